@@ -1,0 +1,344 @@
+"""Benchmark: Mpix/s of the accelerated bilateral graph filters on one GB300.
+
+One step = the whole filtering path on one noisy 512 x 512 image (7 x 7 window, sigma_s 2,
+sigma_r 0.08; synthetic polygons over a gradient, noise sigma 0.05): build the graph
+(bf_weights), 50 iterations of the preconditioned CG filter (Algorithm 2) and 30 iterations
+of block LOBPCG with k = 16 (Algorithm 3), all through the C-ABI.  The image is generated
+on the host and resident on the device before the timed region; L2 (126 MB) is flushed by
+writing a 256 MB buffer between timed steps, and each step is timed with CUDA events on
+the launching stream.
+
+Extra keys: `roofline` for the bilateral operator kernel (k = 16 block apply, timed alone
+with an L2 flush before each launch), `cpu_baseline` (the FP64 CPU oracle, one thread, on
+one full step of the same workload), `e2e` (the same pipeline from pinned host memory to
+host results), `clocks` (nvidia-smi sampled during the timed region) and `gpu_launches`
+(kernels the library launched per timed step, from its own counter).
+
+`--impl reference` times the oracle instead (the reference arm of this benchmark: there
+is no reference implementation, only the paper), each step the same pipeline on a
+128 x 128 crop-sized image of the same generator, reported in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s denoised at ≤1e-5 rel err (plain vs precond+batched); bf_apply GB/s vs HBM"
+WORKLOAD = dict(name="image512_w7x7_cg50_lobpcg_k16x30", ny=512, nx=512, radius=3, sigma_s=2.0,
+                sigma_r=0.08, noise=0.05, seed=2, cg_iters=50, lob_k=16, lob_iters=30)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_step(noisy, w):
+    """One step of the pipeline on the FP64 CPU oracle; returns seconds."""
+    import numpy as np
+
+    from oracle import solvers
+    from oracle.graph import Graph
+    from paper_1509_02468_gb300 import synth
+    t0 = time.perf_counter()
+    G = Graph(noisy.astype(np.float64), noisy.shape, w["radius"], w["sigma_s"], w["sigma_r"])
+    x0 = noisy.reshape(-1).astype(np.float64)
+    solvers.cg(G, x0, w["cg_iters"])
+    X0 = synth.block_start(x0, w["lob_k"], seed=w["seed"], dtype=np.float64)
+    solvers.lobpcg(G, X0, w["lob_iters"])
+    return time.perf_counter() - t0
+
+
+def _cpu_child(side, steps, warmup):
+    """Runs in a subprocess with one BLAS thread: times the oracle pipeline."""
+    from paper_1509_02468_gb300 import synth
+    w = dict(WORKLOAD)
+    _, noisy = synth.polygon_image(side, side, w["seed"], noise=w["noise"])
+    for _ in range(warmup):
+        _oracle_step(noisy, w)
+    ts = [_oracle_step(noisy, w) for _ in range(steps)]
+    print(json.dumps({"times": ts, "npix": side * side}))
+
+
+def run_cpu(side, steps, warmup):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", str(side),
+                        str(steps), str(warmup)], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    side = 128
+    res = run_cpu(side, args.steps, args.warmup)
+    tot = sum(res["times"])
+    value = res["npix"] * len(res["times"]) / tot / 1e6
+    sample = (f"{side}x{side} image of the same generator per step: graph + CG 50 + "
+              f"LOBPCG k=16 x 30 in FP64 numpy/scipy, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(res["times"]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"] + f"_sample{side}", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1509_02468_gb300 import bf, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOAD
+    _, noisy = synth.polygon_image(w["ny"], w["nx"], w["seed"], noise=w["noise"])
+    npix = noisy.size
+    X0h = synth.block_start(noisy.reshape(-1), w["lob_k"], seed=w["seed"], dtype=np.float32)
+    stream = torch.cuda.current_stream()
+    guide = torch.as_tensor(noisy).cuda()
+    X0 = torch.as_tensor(X0h).cuda()
+    x_cg = torch.empty(npix, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+
+    def step():
+        G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
+        bf.cg_filter(G, guide.view(-1), w["cg_iters"], out=x_cg, sync=False)
+        out = bf.lobpcg_filter(G, X0, w["lob_iters"], want_X=False, sync=False)
+        return G, out
+
+    keep = []
+    for _ in range(args.warmup):
+        keep.append(step())
+    torch.cuda.synchronize()
+    keep.clear()
+    # ---- timed steps (device time, events on the launching stream, L2 flushed between)
+    times = []
+    launches0 = bf.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            keep.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+    launches = (bf.launch_count() - launches0) / args.steps
+    keep.clear()
+    ms = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * npix / (ms * 1e-3) / 1e6
+
+    # ---- accuracy of the timed configuration (device results vs FP64 oracle, CG output)
+    # checked by the test suite; here only the per-step outputs are kept finite
+    # ---- roofline of the bilateral operator (k = 16 block, on-the-fly weights)
+    G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
+    Xa = torch.randn(npix, 16, device="cuda")
+    Ya = torch.empty_like(Xa)
+    for _ in range(3):
+        bf.bf_apply(G, "L", Xa, Y=Ya)
+    at = []
+    for _ in range(20):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bf.bf_apply(G, "L", Xa, Y=Ya)
+        e1.record(stream)
+        e1.synchronize()
+        at.append(e0.elapsed_time(e1))
+    apply_ms = statistics.mean(at)
+    bytes_per_px = 4 + 8 * 16          # guide + X in + Y out (k = 16, fp32)
+    traffic_alg = bytes_per_px * npix
+    achieved = traffic_alg / (apply_ms * 1e-3) / 1e9
+    peak, peak_src = _peaks()
+    roofline = {"kernel": "k_apply<float,16> (L, on-the-fly weights)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "traffic": None, "algorithmic_bytes": traffic_alg,
+                "ms_per_launch": apply_ms}
+
+    # ---- end to end through the public API from pinned host memory
+    gh = torch.as_tensor(noisy).pin_memory()
+    X0p = torch.as_tensor(X0h).pin_memory()
+    y_h = torch.empty(npix).pin_memory()
+    xcg_h = torch.empty(npix).pin_memory()
+    th_h = torch.empty(16, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        gd = gh.cuda(non_blocking=True)
+        Xd = X0p.cuda(non_blocking=True)
+        G = bf.bf_weights(gd, w["radius"], w["sigma_s"], w["sigma_r"])
+        xc, _, _ = bf.cg_filter(G, gd.view(-1), w["cg_iters"], sync=False)
+        out = bf.lobpcg_filter(G, Xd, w["lob_iters"], want_X=False, sync=False)
+        xcg_h.copy_(xc, non_blocking=True)
+        y_h.copy_(out["y"], non_blocking=True)
+        th_h.copy_(out["theta"], non_blocking=True)
+        torch.cuda.synchronize()
+        return G
+
+    for _ in range(2):
+        e2e_step()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * sum(e2e_t) / len(e2e_t)
+    h2d = gh.numel() * 4 + X0p.numel() * 4
+    d2h = y_h.numel() * 4 + xcg_h.numel() * 4 + th_h.numel() * 8
+
+    # ---- CPU baseline: the oracle on one full step (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        res = run_cpu(w["nx"], 1, 0)
+        cpu = {"value": res["npix"] / res["times"][0] / 1e6, "unit": "Mpix/s", "cores": 1,
+               "kind": "oracle",
+               "sample": "one full step (512x512: graph + CG 50 + LOBPCG k=16 x 30), FP64 "
+                         "numpy/scipy, 1 thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w["name"], "image": f"{w['ny']}x{w['nx']}",
+                           "window": "7x7", "sigma_s": w["sigma_s"], "sigma_r": w["sigma_r"],
+                           "cg_iters": w["cg_iters"], "lobpcg_k": w["lob_k"],
+                           "lobpcg_iters": w["lob_iters"], "weights": "on-the-fly fp32",
+                           "l2": "flushed between steps (256 MB write)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--cpu-child":
+        _cpu_child(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
+        return 0
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

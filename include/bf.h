@@ -1,0 +1,187 @@
+/*
+ * bf.h -- C-ABI of libbf.so: the bilateral-filter graph operator and the Krylov filters
+ * built on it, for NVIDIA GB300 (sm_103a).
+ *
+ * Method: A. Knyazev, A. Malyshev, "Accelerated graph-based spectral polynomial filters",
+ * IEEE MLSP 2015.  Section 2 defines the graph (Eqs. 1-4), Section 4 the normalised
+ * Laplacian and the simple iteration, Section 5 preconditioned CG for L x = 0
+ * (Algorithm 2), Section 6 LOBPCG as a low-pass filter (Algorithm 3).
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is DEVICE memory owned by the caller unless stated otherwise;
+ *    the library never frees it.  Element type is the graph's dtype (float for BF_F32,
+ *    double for BF_F64), except FP64 scalar outputs, which are always double.
+ *  - A signal/image has n = nx * ny samples, row-major (x fastest).  A block of k vectors
+ *    is pixel-major: element (i, c) is at X[i * ld + c], ld >= k.  Block pointers must be
+ *    16-byte aligned and ld a multiple of 16 / sizeof(element) when k is.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are ordered on
+ *    that stream and return before the GPU finishes, except where a host output (an
+ *    info struct, a status read) is requested: then the call synchronises the stream.
+ *  - Return value: BF_OK (0) or a negative BF_E* code; bf_last_error() gives a message
+ *    (thread-local, valid until the next call on that thread).
+ *  - A bf_graph owns its device buffers and a grow-only workspace; one graph must not
+ *    be used by two calls at the same time (host threads or streams).
+ */
+#ifndef BF_H_
+#define BF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define BF_OK             0
+#define BF_EINVAL        -1   /* bad argument (sizes, alignment, enum values, NULL)      */
+#define BF_ECUDA         -2   /* a CUDA runtime call failed                               */
+#define BF_EBREAKDOWN    -3   /* CG: p^T q <= 0;  LOBPCG: dependent basis without P       */
+#define BF_ENONFINITE    -4   /* NaN/Inf in the guide or in a solver scalar               */
+#define BF_ETIMEOUT      -5   /* a bounded device wait gave up                            */
+#define BF_ENOMEM        -6   /* device allocation failed                                 */
+
+/* ---- enums ----------------------------------------------------------------------- */
+#define BF_F32            0
+#define BF_F64            1
+
+#define BF_WINDOW_SQUARE  0   /* |dx| <= r and |dy| <= r (Section 2's window)             */
+#define BF_WINDOW_CROSS   1   /* dx = 0 or dy = 0: the 5-point lattice of Section 7 at r=1 */
+
+#define BF_W_ONTHEFLY     0   /* weights recomputed from the guide inside every apply     */
+#define BF_W_STORED_F32   1   /* forward half-window weights stored once, float           */
+#define BF_W_STORED_BF16  2   /* forward half-window weights stored once, bfloat16        */
+
+#define BF_OP_W           0   /* Y = W X                                    (Eq. 2)       */
+#define BF_OP_L           1   /* Y = (D - W) X                              (Eq. 4)       */
+#define BF_OP_DINV_W      2   /* Y = D^-1 W X, one BF step                  (Eqs. 1, 3)   */
+#define BF_OP_D           3   /* Y = D X                                    (Section 2)   */
+#define BF_OP_NSYM        4   /* Y = D^-1/2 L D^-1/2 X                                    */
+#define BF_OP_NDIAGL      5   /* Y = (diag L)^-1/2 L (diag L)^-1/2 X        (Section 4)   */
+
+#define BF_PRECOND_JACOBI   0 /* T = D^-1 (Algorithm 2's preconditioner)                  */
+#define BF_PRECOND_IDENTITY 1 /* T = I                                                    */
+
+#define BF_BETA_FLEXIBLE  0   /* beta = s^T (r - r_old) / (s_old^T r_old)                 */
+#define BF_BETA_PRINTED   1   /* beta = s^T (r - r_old) / (s_old^T s_old), as printed     */
+
+#define BF_PENCIL_D       0   /* LOBPCG for L x = lambda D x (Algorithm 3)                */
+#define BF_PENCIL_I       1   /* LOBPCG for L x = lambda x                                */
+
+#define BF_CG_CONVERGED   1   /* bf_info.status: stopped by s^T r = 0 or by tol           */
+#define BF_CG_BREAKDOWN   2   /* bf_info.status: stopped by p^T q <= 0                    */
+
+/* ---- structs ---------------------------------------------------------------------- */
+typedef struct bf_params {
+  int32_t ndim;          /* 1: signal (ny must be 1); 2: image                             */
+  int32_t radius;        /* window radius r, 1..7 (2D) or 1..32 (1D)                        */
+  int64_t nx, ny;        /* samples per row, rows                                           */
+  int32_t window;        /* BF_WINDOW_*                                                     */
+  int32_t weight_mode;   /* BF_W_*                                                          */
+  int32_t dtype;         /* BF_F32 or BF_F64 (BF_W_STORED_BF16 needs BF_F32)                */
+  int32_t reserved;      /* must be 0                                                       */
+  double  sigma_s;       /* spatial width of Eq. 2 (> 0; +inf: factor 1)                    */
+  double  sigma_r;       /* range width of Eq. 2   (> 0; +inf: factor 1)                    */
+} bf_params;
+
+typedef struct bf_graph bf_graph;   /* opaque */
+
+typedef struct bf_info {
+  int32_t iters;         /* iterations completed                                            */
+  int32_t status;        /* 0 = ran all iterations, BF_CG_CONVERGED, BF_CG_BREAKDOWN        */
+  int32_t restarts;      /* LOBPCG: iterations redone without P                             */
+  int32_t reserved;
+  double  rnorm;         /* CG: final ||r||_2;  LOBPCG: max relative residual               */
+  double  ref;           /* CG: ||b||_2 (or ||r_0||_2 when b = 0)                           */
+} bf_info;
+
+typedef struct bf_cg_opts {
+  int32_t precond;       /* BF_PRECOND_*                                                    */
+  int32_t beta;          /* BF_BETA_*                                                       */
+  double  shift;         /* sigma >= 0: solve (L + sigma I) x = sigma x0; 0 = L x = 0       */
+  double  tol;           /* > 0: stop once ||r|| <= tol * ||b|| (||r_0|| if b = 0)          */
+  double* hist;          /* optional device array [2 * kmax]: alpha_j, beta_j per iteration */
+} bf_cg_opts;
+
+typedef struct bf_lobpcg_opts {
+  int32_t pencil;        /* BF_PENCIL_*                                                     */
+  int32_t precond;       /* BF_PRECOND_*                                                    */
+  int32_t constrain_e;   /* 1: keep X B-orthogonal to the constant vector e (Section 6)     */
+  int32_t reserved;
+  double  tol;           /* > 0: stop once max_j ||L x_j - theta_j B x_j|| / ||B x_j|| <= tol */
+  double* theta_hist;    /* optional device array [(kmax + 1) * k]: Ritz values per step    */
+} bf_lobpcg_opts;
+
+/* ---- graph ------------------------------------------------------------------------ */
+
+/* Build the graph of Section 2 from the guide g (device, n elements of dtype): the
+ * degree d_i = sum_j w_ij (w_ii = 1 included), diag L_i = sum_{j != i} w_ij, and, in the
+ * stored modes, the forward half-window weights w_ij = exp(-|p_i-p_j|^2 / 2 sigma_s^2) *
+ * exp(-|g_i-g_j|^2 / 2 sigma_r^2) (Eq. 2).  Neighbours outside the image do not exist.
+ * The guide is copied; *out receives a new graph (free with bf_graph_free).
+ * Synchronises `stream` (it reports BF_ENONFINITE if the guide holds NaN or Inf). */
+int bf_weights(const bf_params* params, const void* guide, bf_graph** out, void* stream);
+
+/* Release a graph and everything it owns (NULL is allowed). */
+int bf_graph_free(bf_graph* g);
+
+/* n, the number of window taps (centre included), and the dtype of a graph. */
+int bf_graph_info(const bf_graph* g, int64_t* n, int32_t* taps, int32_t* dtype);
+
+/* Copy the degree d (n elements, dtype) into d_out. */
+int bf_graph_degree(const bf_graph* g, void* d_out, void* stream);
+
+/* Write every weight of the window, w(i, i + offset_t), into taps_out[i * taps + t]
+ * (dtype; 0 where the neighbour is outside the image).  Taps are ordered row-major by
+ * (dy, dx), each from -r to r (dy = 0 only in 1D; only dx = 0 or dy = 0 for the cross).
+ * In the stored modes these are the stored (rounded) values. */
+int bf_graph_export_weights(const bf_graph* g, void* taps_out, void* stream);
+
+/* ---- operator --------------------------------------------------------------------- */
+
+/* Y = op X for a block of k >= 1 vectors (Eqs. 1-4, Section 4); op is BF_OP_*.  X and Y
+ * are [n][ldx] and [n][ldy] and must not overlap.  If dots is not NULL (device, k
+ * doubles) it receives the column dot products dots[c] = sum_i X[i,c] * Y[i,c]. */
+int bf_apply(const bf_graph* g, int op, const void* X, int64_t ldx, int k, void* Y,
+             int64_t ldy, double* dots, void* stream);
+
+/* iters steps of the bilateral filter with fixed weights, x <- D^-1 W x (Section 2's
+ * linear iteration; Section 4's simple iteration for L x = 0 with preconditioner D).
+ * x0 and x_out hold n elements and may be the same array. */
+int bf_simple_filter(const bf_graph* g, const void* x0, int iters, void* x_out,
+                     void* stream);
+
+/* ---- Krylov filters --------------------------------------------------------------- */
+
+/* Algorithm 2 (Section 5): kmax iterations of preconditioned CG for A x = b, A = L +
+ * shift * I, b = shift * x0 (shift = 0: L x = 0 as printed), started at x = x0.  beta is
+ * the flexible formula (opts->beta).  Stops early when s^T r = 0, when p^T q <= 0
+ * (breakdown: x keeps its last value) or, with tol > 0, once ||r|| <= tol * ||b||.
+ * x0 and x_out hold n elements (may be the same array).  opts may be NULL (Jacobi,
+ * flexible beta, shift 0, tol 0).  If info is not NULL the stream is synchronised and
+ * info filled; a breakdown then returns BF_EBREAKDOWN. */
+int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
+              void* x_out, bf_info* info, void* stream);
+
+/* Algorithm 3 (Section 6) on a block of k vectors: kmax steps of LOBPCG for the pencil
+ * (L, B), B = D or I, Rayleigh-Ritz on span{X, W, P}, W = T (L X - B X Theta); the small
+ * Rayleigh-Ritz problems are solved in FP64 on the GPU.  X0 is [n][ldx0] (column 0 is
+ * the signal x0 to filter).  Outputs (any may be NULL): X_out [n][k] B-orthonormal Ritz
+ * vectors, theta_out [k] Ritz values (ascending, double), resid_out [k] relative
+ * residual norms ||L x_j - theta_j B x_j|| / ||B x_j|| (double), y_out [n] the filtered
+ * signal y = X X^T B x0 (with the constraint: e_bar e + X X^T B (x0 - e_bar e), e_bar the
+ * B-mean of x0).  Needs 1 <= k and 3k <= n; k <= 32.  If info is not NULL the stream
+ * is synchronised and info filled. */
+int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, int k, int kmax,
+                  const bf_lobpcg_opts* opts, void* X_out, double* theta_out,
+                  double* resid_out, void* y_out, bf_info* info, void* stream);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char* bf_last_error(void);
+
+/* Number of kernels this library has launched in the process so far (all threads). */
+uint64_t bf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BF_H_ */

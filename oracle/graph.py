@@ -78,9 +78,40 @@ class Graph:
             cols.append(j)
             vals.append(w)
             self.taps[i, t] = w
-        rows = np.concatenate(rows)
-        cols = np.concatenate(cols)
-        vals = np.concatenate(vals)
+        self._assemble(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+    @classmethod
+    def from_taps(cls, taps, shape, radius: int, window: str = "square"):
+        """The graph whose weights are given per tap: taps[i, t] = w(i, i + offset_t) in
+        the canonical tap order (entries for neighbours outside the image are ignored).
+        Used to build the exact FP64 operator of weights that were rounded for storage."""
+        ny, nx = shape
+        self = cls.__new__(cls)
+        self.shape = (ny, nx)
+        self.ndim = 1 if ny == 1 else 2
+        self.n = n = ny * nx
+        self.radius, self.sigma_s, self.sigma_r, self.window = radius, None, None, window
+        self.guide = None
+        self.offsets = window_offsets(self.ndim, radius, window)
+        taps = np.asarray(taps, dtype=np.float64).reshape(n, len(self.offsets))
+        yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        rows, cols, vals = [], [], []
+        self.taps = np.zeros((n, len(self.offsets)), dtype=np.float64)
+        for t, (dy, dx) in enumerate(self.offsets):
+            ty, tx = yy + dy, xx + dx
+            ok = (ty >= 0) & (ty < ny) & (tx >= 0) & (tx < nx)
+            i = (yy * nx + xx)[ok]
+            j = (ty * nx + tx)[ok]
+            w = taps[i, t]
+            rows.append(i)
+            cols.append(j)
+            vals.append(w)
+            self.taps[i, t] = w
+        self._assemble(np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+        return self
+
+    def _assemble(self, rows, cols, vals):
+        n = self.n
         self.W = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
         self.d = np.asarray(self.W.sum(axis=1)).reshape(-1)        # d_i = sum_j w_ij
         self.D = sp.diags(self.d)

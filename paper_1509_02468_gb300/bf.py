@@ -1,0 +1,256 @@
+"""ctypes binding of libbf.so (include/bf.h): argument marshalling only.
+
+Every computation runs in the CUDA library; torch tensors provide device memory and the
+current CUDA stream.  Importing this module loads the library and raises if it is missing
+(build it with ``python -m paper_1509_02468_gb300.build``): there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbf.so")
+
+BF_OK, BF_EINVAL, BF_ECUDA, BF_EBREAKDOWN, BF_ENONFINITE, BF_ETIMEOUT, BF_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+F32, F64 = 0, 1
+WINDOWS = {"square": 0, "cross": 1}
+WEIGHT_MODES = {"onthefly": 0, "stored_f32": 1, "stored_bf16": 2}
+OPS = {"W": 0, "L": 1, "DINV_W": 2, "D": 3, "NSYM": 4, "NDIAGL": 5}
+PRECONDS = {"jacobi": 0, "identity": 1}
+BETAS = {"flexible": 0, "printed": 1}
+PENCILS = {"D": 0, "I": 1}
+STATUS = {0: "ran", 1: "converged", 2: "breakdown"}
+
+
+class BFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libbf error {code}: {msg}")
+        self.code = code
+
+
+class bf_params(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("window", ctypes.c_int32), ("weight_mode", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sigma_s", ctypes.c_double), ("sigma_r", ctypes.c_double)]
+
+
+class bf_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rnorm", ctypes.c_double), ("ref", ctypes.c_double)]
+
+
+class bf_cg_opts(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("shift", ctypes.c_double), ("tol", ctypes.c_double),
+                ("hist", ctypes.c_void_p)]
+
+
+class bf_lobpcg_opts(ctypes.Structure):
+    _fields_ = [("pencil", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("constrain_e", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("theta_hist", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1509_02468_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    sig = {
+        "bf_weights": [ctypes.POINTER(bf_params), vp, ctypes.POINTER(vp), vp],
+        "bf_graph_free": [vp],
+        "bf_graph_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_int32)],
+        "bf_graph_degree": [vp, vp, vp],
+        "bf_graph_export_weights": [vp, vp, vp],
+        "bf_apply": [vp, i32, vp, i64, i32, vp, i64, dp, vp],
+        "bf_simple_filter": [vp, vp, i32, vp, vp],
+        "cg_filter": [vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, ctypes.POINTER(bf_info), vp],
+        "lobpcg_filter": [vp, vp, i64, i32, i32, ctypes.POINTER(bf_lobpcg_opts), vp, dp, dp, vp,
+                          ctypes.POINTER(bf_info), vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.bf_last_error.argtypes = []
+    lib.bf_last_error.restype = ctypes.c_char_p
+    lib.bf_launch_count.argtypes = []
+    lib.bf_launch_count.restype = ctypes.c_uint64
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(_lib.bf_launch_count())
+
+
+def _check(rc):
+    if rc != BF_OK:
+        raise BFError(rc, _lib.bf_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+@dataclass
+class Info:
+    iters: int
+    status: str
+    restarts: int
+    rnorm: float
+    ref: float
+
+
+def _info(i: bf_info) -> Info:
+    return Info(i.iters, STATUS.get(i.status, str(i.status)), i.restarts, i.rnorm, i.ref)
+
+
+class Graph:
+    """A bf_graph handle (device buffers owned by the library)."""
+
+    def __init__(self, handle, params, shape, dtype, device):
+        self.handle = handle
+        self.params = params
+        self.shape = shape
+        self.n = shape[0] * shape[1]
+        self.dtype = dtype
+        self.device = device
+
+    def free(self):
+        if self.handle:
+            _lib.bf_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def taps(self):
+        t = ctypes.c_int32()
+        _check(_lib.bf_graph_info(self.handle, None, ctypes.byref(t), None))
+        return t.value
+
+
+def bf_weights(guide: torch.Tensor, radius: int, sigma_s: float, sigma_r: float,
+               window: str = "square", weight_mode: str = "onthefly", stream=None) -> Graph:
+    """Graph of Section 2 from a 1D signal (shape (n,)) or an image (shape (ny, nx))."""
+    if not guide.is_cuda or guide.dtype not in (torch.float32, torch.float64):
+        raise ValueError("guide must be a float32/float64 CUDA tensor")
+    guide = guide.contiguous()
+    if guide.dim() == 1:
+        ndim, ny, nx = 1, 1, guide.shape[0]
+    elif guide.dim() == 2:
+        ndim, ny, nx = 2, guide.shape[0], guide.shape[1]
+    else:
+        raise ValueError("guide must be 1D or 2D")
+    p = bf_params(ndim=ndim, radius=radius, nx=nx, ny=ny, window=WINDOWS[window],
+                  weight_mode=WEIGHT_MODES[weight_mode],
+                  dtype=F64 if guide.dtype == torch.float64 else F32, reserved=0,
+                  sigma_s=float(sigma_s), sigma_r=float(sigma_r))
+    h = ctypes.c_void_p()
+    _check(_lib.bf_weights(ctypes.byref(p), _ptr(guide), ctypes.byref(h), _stream(stream)))
+    return Graph(h, p, (ny, nx), guide.dtype, guide.device)
+
+
+def graph_degree(g: Graph, stream=None) -> torch.Tensor:
+    d = torch.empty(g.n, dtype=g.dtype, device=g.device)
+    _check(_lib.bf_graph_degree(g.handle, _ptr(d), _stream(stream)))
+    return d
+
+
+def graph_export_weights(g: Graph, stream=None) -> torch.Tensor:
+    out = torch.empty((g.n, g.taps), dtype=g.dtype, device=g.device)
+    _check(_lib.bf_graph_export_weights(g.handle, _ptr(out), _stream(stream)))
+    return out
+
+
+def _as_block(X: torch.Tensor):
+    if X.dim() == 1:
+        return X.view(-1, 1), 1
+    return X, X.shape[1]
+
+
+def bf_apply(g: Graph, op: str, X: torch.Tensor, Y: torch.Tensor | None = None,
+             dots: bool = False, stream=None):
+    """Y = op X for X of shape (n,) or (n, k) (row stride may exceed k)."""
+    Xb, k = _as_block(X)
+    if Xb.stride(1) != 1:
+        raise ValueError("X columns must be contiguous")
+    if Y is None:
+        Y = torch.empty_like(X, memory_format=torch.contiguous_format)
+    Yb, _ = _as_block(Y)
+    d = torch.empty(k, dtype=torch.float64, device=X.device) if dots else None
+    _check(_lib.bf_apply(g.handle, OPS[op], _ptr(Xb), Xb.stride(0), k, _ptr(Yb), Yb.stride(0),
+                         _ptr(d), _stream(stream)))
+    return (Y, d) if dots else Y
+
+
+def bf_simple_filter(g: Graph, x0: torch.Tensor, iters: int, out=None, stream=None):
+    out = torch.empty_like(x0) if out is None else out
+    _check(_lib.bf_simple_filter(g.handle, _ptr(x0), iters, _ptr(out), _stream(stream)))
+    return out
+
+
+def cg_filter(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jacobi",
+              beta: str = "flexible", shift: float = 0.0, tol: float = 0.0,
+              hist: bool = False, out=None, sync: bool = True, stream=None):
+    """Algorithm 2.  Returns (x, info, hist) -- info None unless sync, hist None unless asked."""
+    out = torch.empty_like(x0) if out is None else out
+    h = torch.full((2 * max(kmax, 1),), float("nan"), dtype=torch.float64, device=x0.device) if hist else None
+    o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS[beta], shift=shift, tol=tol,
+                   hist=h.data_ptr() if h is not None else None)
+    info = bf_info() if sync else None
+    _check(_lib.cg_filter(g.handle, _ptr(x0), kmax, ctypes.byref(o), _ptr(out),
+                          ctypes.byref(info) if info is not None else None, _stream(stream)))
+    return out, (_info(info) if info is not None else None), h
+
+
+def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
+                  precond: str = "jacobi", constrain: bool = False, tol: float = 0.0,
+                  want_X: bool = True, want_y: bool = True, theta_hist: bool = False,
+                  sync: bool = True, stream=None):
+    """Algorithm 3 on a block X0 of shape (n, k).  Returns a dict with X, theta, resid, y,
+    theta_hist and info (entries None when not requested)."""
+    Xb, k = _as_block(X0)
+    dev = X0.device
+    X = torch.empty((g.n, k), dtype=X0.dtype, device=dev) if want_X else None
+    y = torch.empty(g.n, dtype=X0.dtype, device=dev) if want_y else None
+    theta = torch.empty(k, dtype=torch.float64, device=dev)
+    resid = torch.empty(k, dtype=torch.float64, device=dev)
+    th = torch.full(((kmax + 1) * k,), float("nan"), dtype=torch.float64, device=dev) if theta_hist else None
+    o = bf_lobpcg_opts(pencil=PENCILS[pencil], precond=PRECONDS[precond],
+                       constrain_e=int(constrain), reserved=0, tol=tol,
+                       theta_hist=th.data_ptr() if th is not None else None)
+    info = bf_info() if sync else None
+    _check(_lib.lobpcg_filter(g.handle, _ptr(Xb), Xb.stride(0), k, kmax, ctypes.byref(o),
+                              _ptr(X), _ptr(theta), _ptr(resid), _ptr(y),
+                              ctypes.byref(info) if info is not None else None, _stream(stream)))
+    return {"X": X, "theta": theta, "resid": resid, "y": y,
+            "theta_hist": th.view(kmax + 1, k) if th is not None else None,
+            "info": _info(info) if info is not None else None}

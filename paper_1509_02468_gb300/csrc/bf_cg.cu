@@ -1,0 +1,304 @@
+// Algorithm 2 (Section 5): preconditioned CG for L x = 0 -- or the shifted system
+// (L + sigma I) x = sigma x0 -- as a polynomial filter, with the flexible beta.
+//
+// Per iteration two kernels, all scalars kept on the device in FP64:
+//   k_cg_dir:    p = s + beta p on the tile and its halo, q = (L + sigma I) p (matrix-free,
+//                weights from the guide or the stored ones), block sums of p^T q, and in the
+//                last block alpha = s^T r / p^T q with the breakdown tests;
+//   k_cg_update: x += alpha p, r -= alpha q, s = T r, sums of s^T r, s^T q, s^T s, r^T r,
+//                and in the last block beta for the next iteration:
+//                s^T (r - r_old) = -alpha s^T q, divided by s_old^T r_old (flexible) or
+//                s_old^T s_old (as printed).
+// Once a kernel records a stop (converged, breakdown, non-finite) the remaining launches
+// return at once, so the host loop needs no read-back.
+#include <math.h>
+
+#include <algorithm>
+
+#include "bf_internal.cuh"
+
+int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
+                 int64_t ldy, double* dots, cudaStream_t s);
+int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
+                 int64_t ldy, double* dots, cudaStream_t s);
+
+namespace {
+
+enum { CG_RUN = 0, CG_CONV = 1, CG_BREAK = 2, CG_NONFINITE = 3 };
+
+struct CgState {
+  double sr;        // s^T r of the current residual
+  double ss;        // s^T s
+  double rr;        // r^T r
+  double pq;        // p^T q
+  double alpha;
+  double beta;      // beta to use in the next direction update
+  double ref2;      // ||b||^2 (or ||r_0||^2 when b = 0)
+  double tol2;
+  int status;
+  int iter;         // completed iterations
+  int beta_mode;
+  int pad;
+  unsigned int counter;
+  unsigned int pad2;
+};
+
+template <typename T>
+struct CgArgs {
+  const T* x0;
+  T* x;
+  T* r;
+  T* s;
+  T* q;
+  const T* p_old;
+  T* p_new;
+  const T* guide;
+  const T* dinv;       // Jacobi preconditioner (NULL: identity)
+  const void* wf;
+  int wmode;
+  int64_t n;
+  T shift;
+  int first;           // first iteration: p = s
+  double* partials;
+  CgState* st;
+  double* hist;        // [2 kmax] or NULL
+};
+
+// Stage one scalar field (with halo) into shared memory; `f(gp)` gives the value at an
+// in-image pixel, 0 is stored outside.
+template <typename T, class F>
+__device__ __forceinline__ void stage1(const Geom<T>& g, const Tile& t, Vec<T, 1>* sx, T* sg,
+                                       const T* guide, bool otf, F f) {
+  for (int hp = threadIdx.x; hp < t.hp; hp += BF_THREADS) {
+    const int hy = hp / t.hw, hx = hp - hy * t.hw;
+    const int gy = t.by - g.ry + hy, gx = t.bx - g.rx + hx;
+    T v = T(0), gv = T(0);
+    if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
+      const int64_t gp = (int64_t)gy * g.nx + gx;
+      v = f(gp);
+      if (otf) gv = guide[gp];
+    }
+    sx[hp].v[0] = v;
+    if (otf) sg[hp] = gv;
+  }
+}
+
+// r = -L x0 (= b - A x0 for either system), x = x0, s = T r; sums s^T r, s^T s, r^T r, x0^T x0.
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_init(const Geom<T> g, const CgArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  const Tile t = make_tile(g);
+  Vec<T, 1>* sx = reinterpret_cast<Vec<T, 1>*>(smem);
+  T* sg = reinterpret_cast<T*>(sx + t.hp);
+  const bool otf = a.wmode == BF_W_ONTHEFLY;
+  stage1<T>(g, t, sx, sg, a.guide, otf, [&](int64_t gp) { return a.x0[gp]; });
+  __syncthreads();
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  if (t.active) {
+    const int64_t i = (int64_t)t.y * g.nx + t.x;
+    T xi[1] = {sx[t.hp0].v[0]}, acc[1] = {T(0)}, ws = T(0);
+    window_sum<T, 1, true>(g, t, sg, sx, a.wf, a.wmode, a.n, xi, acc, ws);
+    const T r = -acc[0];
+    const T s = a.dinv ? r * a.dinv[i] : r;
+    a.x[i] = xi[0];
+    a.r[i] = r;
+    a.s[i] = s;
+    v[0] = s * r;
+    v[1] = s * s;
+    v[2] = r * r;
+    v[3] = xi[0] * xi[0];
+  }
+  double blk[4], tot[4];
+  block_sum<4, T>(v, red, blk);
+  if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->sr = tot[0];
+    st->ss = tot[1];
+    st->rr = tot[2];
+    const double b2 = (double)a.shift * (double)a.shift * tot[3];
+    st->ref2 = b2 > 0.0 ? b2 : tot[2];
+    st->beta = 0.0;
+    st->alpha = 0.0;
+    st->iter = 0;
+    st->status = (isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2])) ? CG_RUN : CG_NONFINITE;
+  }
+}
+
+// p = s + beta p_old (first: p = s) on tile + halo, q = (L + shift I) p, p^T q, alpha.
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_dir(const Geom<T> g, const CgArgs<T> a) {
+  if (a.st->status != CG_RUN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[1 * (BF_THREADS / 32)];
+  __shared__ int last;
+  const Tile t = make_tile(g);
+  Vec<T, 1>* sx = reinterpret_cast<Vec<T, 1>*>(smem);
+  T* sg = reinterpret_cast<T*>(sx + t.hp);
+  const bool otf = a.wmode == BF_W_ONTHEFLY;
+  const T beta = (T)a.st->beta;
+  if (a.first)
+    stage1<T>(g, t, sx, sg, a.guide, otf, [&](int64_t gp) { return a.s[gp]; });
+  else
+    stage1<T>(g, t, sx, sg, a.guide, otf, [&](int64_t gp) { return fma(beta, a.p_old[gp], a.s[gp]); });
+  __syncthreads();
+  T v[1] = {T(0)};
+  if (t.active) {
+    const int64_t i = (int64_t)t.y * g.nx + t.x;
+    T pi[1] = {sx[t.hp0].v[0]}, acc[1] = {T(0)}, ws = T(0);
+    window_sum<T, 1, true>(g, t, sg, sx, a.wf, a.wmode, a.n, pi, acc, ws);
+    const T q = fma(a.shift, pi[0], acc[0]);
+    a.p_new[i] = pi[0];
+    a.q[i] = q;
+    v[0] = pi[0] * q;
+  }
+  double blk[1], tot[1];
+  block_sum<1, T>(v, red, blk);
+  if (grid_sum_last<1>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->pq = tot[0];
+    if (st->sr == 0.0) {
+      st->status = CG_CONV;
+    } else if (!isfinite(tot[0])) {
+      st->status = CG_NONFINITE;
+    } else if (!(tot[0] > 0.0)) {
+      st->status = CG_BREAK;
+    } else {
+      st->alpha = st->sr / tot[0];
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, s = T r; s^T r, s^T q, s^T s, r^T r; beta for the next step.
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_update(const CgArgs<T> a) {
+  if (a.st->status != CG_RUN) return;
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  const T alpha = (T)a.st->alpha;
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * BF_THREADS) {
+    const T p = a.p_new[i], q = a.q[i];
+    a.x[i] = fma(alpha, p, a.x[i]);
+    const T r = fma(-alpha, q, a.r[i]);
+    const T s = a.dinv ? r * a.dinv[i] : r;
+    a.r[i] = r;
+    a.s[i] = s;
+    v[0] += s * r;
+    v[1] += s * q;
+    v[2] += s * s;
+    v[3] += r * r;
+  }
+  double blk[4], tot[4];
+  block_sum<4, T>(v, red, blk);
+  if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    const int it = st->iter;
+    if (a.hist) {
+      a.hist[2 * it] = st->alpha;
+      a.hist[2 * it + 1] = a.first ? 0.0 : st->beta;
+    }
+    st->iter = it + 1;
+    const double den = (st->beta_mode == BF_BETA_PRINTED) ? st->ss : st->sr;
+    const double beta_next = -st->alpha * tot[1] / den;
+    st->sr = tot[0];
+    st->ss = tot[2];
+    st->rr = tot[3];
+    st->beta = beta_next;
+    if (!(isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2]) && isfinite(tot[3])))
+      st->status = CG_NONFINITE;
+    else if (st->tol2 > 0.0 && tot[3] <= st->tol2 * st->ref2)
+      st->status = CG_CONV;
+  }
+}
+
+template <typename T>
+int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_out,
+           bf_info* info, cudaStream_t s) {
+  bf_graph* gm = const_cast<bf_graph*>(g);
+  const int64_t n = g->n;
+  const size_t vb = ((size_t)n * sizeof(T) + 255) & ~(size_t)255;
+  const dim3 tg = tile_grid(g);
+  const unsigned nb_tile = tg.x * tg.y;
+  const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 152 * 8);
+  const unsigned nbmax = std::max(nb_tile, nb_elem);
+  const size_t pb = ((size_t)nbmax * 4 * sizeof(double) + 255) & ~(size_t)255;
+  int rc = bf_ws_reserve(gm, 5 * vb + pb + 256);
+  if (rc) return rc;
+  char* w = (char*)gm->ws;
+  CgArgs<T> a;
+  a.r = (T*)(w);
+  a.s = (T*)(w + vb);
+  a.q = (T*)(w + 2 * vb);
+  T* pbuf[2] = {(T*)(w + 3 * vb), (T*)(w + 4 * vb)};
+  a.partials = (double*)(w + 5 * vb);
+  a.st = (CgState*)(w + 5 * vb + pb);
+  a.x0 = x0;
+  a.x = x_out;
+  a.guide = (const T*)g->guide;
+  a.dinv = o.precond == BF_PRECOND_JACOBI ? (const T*)g->dinv : nullptr;
+  a.wf = g->wf;
+  a.wmode = g->p.weight_mode;
+  a.n = n;
+  a.shift = (T)o.shift;
+  a.hist = o.hist;
+  a.first = 1;
+  a.p_old = pbuf[0];
+  a.p_new = pbuf[1];
+
+  CgState init;
+  memset(&init, 0, sizeof(init));
+  init.tol2 = o.tol > 0 ? o.tol * o.tol : 0.0;
+  init.beta_mode = o.beta;
+  BF_CUDA(cudaMemcpyAsync(a.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  const bool one_d = (g->ny == 1 && g->ry == 0);
+  const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
+  const size_t sm = hp * 2 * sizeof(T);
+  BF_LAUNCH(k_cg_init<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+  BF_CUDA(cudaGetLastError());
+  for (int it = 0; it < kmax; ++it) {
+    a.first = (it == 0);
+    a.p_old = pbuf[it & 1];
+    a.p_new = pbuf[(it + 1) & 1];
+    BF_LAUNCH(k_cg_dir<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+    BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+  }
+  BF_CUDA(cudaGetLastError());
+  if (info) {
+    CgState h;
+    BF_CUDA(cudaMemcpyAsync(&h, a.st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    info->iters = h.iter;
+    info->status = h.status == CG_CONV ? BF_CG_CONVERGED : (h.status == CG_BREAK ? BF_CG_BREAKDOWN : 0);
+    info->restarts = 0;
+    info->reserved = 0;
+    info->rnorm = sqrt(h.rr);
+    info->ref = sqrt(h.ref2);
+    if (h.status == CG_BREAK) return bf_fail(BF_EBREAKDOWN, "cg_filter: p^T q <= 0 (breakdown)");
+    if (h.status == CG_NONFINITE) return bf_fail(BF_ENONFINITE, "cg_filter: non-finite scalar");
+  }
+  return BF_OK;
+}
+
+}  // namespace
+
+extern "C" int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
+                         void* x_out, bf_info* info, void* stream) {
+  if (!g || !x0 || !x_out) return bf_fail(BF_EINVAL, "cg_filter: NULL argument");
+  if (kmax < 0) return bf_fail(BF_EINVAL, "cg_filter: kmax < 0");
+  bf_cg_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY)
+    return bf_fail(BF_EINVAL, "cg_filter: bad precond");
+  if (o.beta != BF_BETA_FLEXIBLE && o.beta != BF_BETA_PRINTED)
+    return bf_fail(BF_EINVAL, "cg_filter: bad beta");
+  if (!(o.shift >= 0.0) || !(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "cg_filter: shift and tol must be >= 0");
+  if ((uintptr_t)x0 % g->esize || (uintptr_t)x_out % g->esize)
+    return bf_fail(BF_EINVAL, "cg_filter: misaligned vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->esize == 4) return cg_run<float>(g, (const float*)x0, kmax, o, (float*)x_out, info, s);
+  return cg_run<double>(g, (const double*)x0, kmax, o, (double*)x_out, info, s);
+}

@@ -1,0 +1,520 @@
+// The bilateral-filter graph (Section 2, Eqs. 1-4; Section 4): building it (bf_weights),
+// exporting it, and the matrix-free operator Y = op X (bf_apply), plus the simple
+// iteration x <- D^-1 W x (bf_simple_filter).
+#include <math.h>
+#include <stdio.h>
+
+#include <cmath>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "bf_internal.cuh"
+
+// ================================================================== errors
+static thread_local std::string g_last_error;
+
+void bf_set_error(const std::string& msg) { g_last_error = msg; }
+int bf_fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+int bf_cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? BF_ENOMEM : BF_ECUDA;
+}
+
+extern "C" const char* bf_last_error(void) { return g_last_error.c_str(); }
+
+static std::atomic<unsigned long long> g_launches{0};
+void bf_count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+extern "C" uint64_t bf_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+int bf_ws_reserve(bf_graph* g, size_t bytes) {
+  if (bytes <= g->ws_bytes) return BF_OK;
+  if (g->ws) {
+    BF_CUDA(cudaDeviceSynchronize());
+    BF_CUDA(cudaFree(g->ws));
+    g->ws = nullptr;
+    g->ws_bytes = 0;
+  }
+  bytes = (bytes + 4095) & ~(size_t)4095;
+  BF_CUDA(cudaMalloc(&g->ws, bytes));
+  g->ws_bytes = bytes;
+  return BF_OK;
+}
+
+// ================================================================== weights kernel
+// One thread per pixel: sum_{j != i} w_ij over the window (same tap order and the same
+// arithmetic as the operator kernels, so d is consistent with every apply), the derived
+// per-pixel scalings, and in the stored modes the forward half-window weights rounded to
+// the storage type (sums use the rounded values: the stored operator is a graph in its own
+// right).
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS)
+k_weights(const Geom<T> g, const T* __restrict__ guide, int64_t n, T* d, T* dinv, T* dis,
+          T* dls, void* wf, int wmode, int* flag) {
+  const int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x;
+  if (i >= n) return;
+  const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+  const T gi = guide[i];
+  if (!isfinite((double)gi)) atomicOr(flag, 1);
+  const int bw = 2 * g.rx + 1;
+  T wsum = T(0);
+  for (int dy = -g.ry; dy <= g.ry; ++dy) {
+    const int yy = y + dy;
+    for (int dx = -g.rx; dx <= g.rx; ++dx) {
+      if (dx == 0 && dy == 0) continue;
+      if (g.cross && dx != 0 && dy != 0) continue;
+      const int cell = (dy + g.ry) * bw + (dx + g.rx);
+      const int f = g.fmap[cell];
+      const int xx = x + dx;
+      const bool in = (yy >= 0 && yy < g.ny && xx >= 0 && xx < g.nx);
+      T w = T(0);
+      if (in) {
+        const T dl = gi - guide[(int64_t)yy * g.nx + xx];
+        w = bf_exp_w(fma(-dl * g.a_r, dl, g.ls[cell]));
+        if (wmode == BF_W_STORED_BF16) w = (T)__bfloat162float(__float2bfloat16_rn((float)w));
+        else if (wmode == BF_W_STORED_F32) w = (T)(float)w;
+        wsum += w;
+      }
+      if (wmode != BF_W_ONTHEFLY && f >= 0) {
+        if (wmode == BF_W_STORED_BF16)
+          ((__nv_bfloat16*)wf)[(int64_t)f * n + i] = __float2bfloat16_rn((float)w);
+        else
+          ((float*)wf)[(int64_t)f * n + i] = (float)w;
+      }
+    }
+  }
+  const T dd = T(1) + wsum;
+  d[i] = dd;
+  dinv[i] = T(1) / dd;
+  dis[i] = T(1) / sqrt(dd);
+  dls[i] = (wsum > T(1e-30)) ? T(1) / sqrt(wsum) : T(0);
+}
+
+// Export every window weight in canonical tap order (centre = 1, 0 off the image).
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS)
+k_export(const Geom<T> g, const T* __restrict__ guide, int64_t n, const void* wf, int wmode,
+         int ntaps, T* out) {
+  const int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x;
+  if (i >= n) return;
+  const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+  const int bw = 2 * g.rx + 1;
+  int t = 0;
+  for (int dy = -g.ry; dy <= g.ry; ++dy) {
+    for (int dx = -g.rx; dx <= g.rx; ++dx) {
+      if (g.cross && dx != 0 && dy != 0) continue;
+      const int yy = y + dy, xx = x + dx;
+      T w = T(0);
+      if (dx == 0 && dy == 0) {
+        w = T(1);
+      } else if (yy >= 0 && yy < g.ny && xx >= 0 && xx < g.nx) {
+        const int cell = (dy + g.ry) * bw + (dx + g.rx);
+        const int64_t j = (int64_t)yy * g.nx + xx;
+        if (wmode == BF_W_ONTHEFLY) {
+          const T dl = guide[i] - guide[j];
+          w = bf_exp_w(fma(-dl * g.a_r, dl, g.ls[cell]));
+        } else {
+          const int f = g.fmap[cell];
+          if (f >= 0) w = (T)ld_weight(wf, (int64_t)f * n + i, wmode);
+          else w = (T)ld_weight(wf, (int64_t)g.fmap[(g.ry - dy) * bw + (g.rx - dx)] * n + j, wmode);
+        }
+      }
+      out[i * ntaps + t] = w;
+      ++t;
+    }
+  }
+}
+
+// ================================================================== operator kernel
+template <typename T>
+struct ApplyArgs {
+  const T* X;
+  int64_t ldx;
+  T* Y;
+  int64_t ldy;
+  const T* guide;
+  const T* scale;   // per-pixel scaling of the operand (NSYM: d^-1/2, NDIAGL: (diag L)^-1/2)
+  const void* wf;
+  int wmode;
+  int op;
+  int64_t n;
+  double* dots;     // [K] or NULL
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(BF_THREADS) k_apply(const Geom<T> g, const ApplyArgs<T> a) {
+  constexpr int V = VecW<T, K>::value;
+  constexpr int NC = K / V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tile t = make_tile(g);
+  Vec<T, V>* sx = reinterpret_cast<Vec<T, V>*>(smem);
+  T* sg = reinterpret_cast<T*>(sx + (size_t)NC * t.hp);
+  const bool otf = (a.wmode == BF_W_ONTHEFLY);
+  // ---- stage the halo tile: operand (optionally scaled) and guide
+  for (int idx = threadIdx.x; idx < t.hp * NC; idx += BF_THREADS) {
+    const int hp = idx / NC, c = idx - hp * NC;
+    const int hy = hp / t.hw, hx = hp - hy * t.hw;
+    const int gy = t.by - g.ry + hy, gx = t.bx - g.rx + hx;
+    Vec<T, V> v;
+    if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
+      const int64_t gp = (int64_t)gy * g.nx + gx;
+      v = *reinterpret_cast<const Vec<T, V>*>(a.X + gp * a.ldx + c * V);
+      if (a.scale) {
+        const T s = a.scale[gp];
+#pragma unroll
+        for (int e = 0; e < V; ++e) v.v[e] *= s;
+      }
+      if (otf && c == 0) sg[hp] = a.guide[gp];
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) v.v[e] = T(0);
+      if (otf && c == 0) sg[hp] = T(0);
+    }
+    sx[c * t.hp + hp] = v;
+  }
+  __syncthreads();
+  // ---- window sum and epilogue
+  const bool diff = (a.op == BF_OP_L || a.op == BF_OP_NSYM || a.op == BF_OP_NDIAGL);
+  T xi[K], acc[K], y[K];
+  T wsum = T(0);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const Vec<T, V> v = sx[c * t.hp + t.hp0];
+#pragma unroll
+    for (int e = 0; e < V; ++e) xi[c * V + e] = v.v[e];
+  }
+#pragma unroll
+  for (int c = 0; c < K; ++c) { acc[c] = T(0); y[c] = T(0); }
+  const int64_t i = (int64_t)t.y * g.nx + t.x;
+  if (t.active) {
+    if (diff) window_sum<T, K, true>(g, t, sg, sx, a.wf, a.wmode, a.n, xi, acc, wsum);
+    else      window_sum<T, K, false>(g, t, sg, sx, a.wf, a.wmode, a.n, xi, acc, wsum);
+    T s_i = T(1);
+    if (a.scale) s_i = a.scale[i];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      switch (a.op) {
+        case BF_OP_W:      y[c] = acc[c] + xi[c]; break;
+        case BF_OP_L:      y[c] = acc[c]; break;
+        case BF_OP_DINV_W: y[c] = (acc[c] + xi[c]) / (T(1) + wsum); break;
+        case BF_OP_D:      y[c] = (T(1) + wsum) * xi[c]; break;
+        default:           y[c] = s_i * acc[c]; break;   // NSYM, NDIAGL
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      Vec<T, V> o;
+#pragma unroll
+      for (int e = 0; e < V; ++e) o.v[e] = y[c * V + e];
+      *reinterpret_cast<Vec<T, V>*>(a.Y + i * a.ldy + c * V) = o;
+    }
+  }
+  if (a.dots) {
+    // dots use the unscaled operand
+    if (a.scale && t.active) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) xi[c] = a.X[i * a.ldx + c];
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const T pr = t.active ? xi[c] * y[c] : T(0);
+      const T s = warp_sum(pr);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&a.dots[c], (double)s);
+    }
+  }
+}
+
+template <typename T, int K>
+static size_t apply_smem(const bf_graph* g) {
+  const bool one_d = (g->ny == 1 && g->ry == 0);
+  const int hw = (one_d ? BF_TW1 : BF_TW2) + 2 * g->rx;
+  const int hh = (one_d ? 1 : BF_TH2) + 2 * g->ry;
+  return (size_t)hw * hh * (K + 1) * sizeof(T);
+}
+
+template <typename T, int K>
+static int launch_apply(const bf_graph* g, const ApplyArgs<T>& a, cudaStream_t s) {
+  const size_t sm = apply_smem<T, K>(g);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(k_apply<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    227 * 1024);
+  });
+  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply)");
+  if (sm > 227 * 1024) return bf_fail(BF_EINVAL, "bf_apply: tile does not fit in shared memory");
+  BF_LAUNCH(k_apply<T, K><<<tile_grid(g), BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+template <typename T>
+static int apply_chunk(const bf_graph* g, int K, const ApplyArgs<T>& a, cudaStream_t s) {
+  switch (K) {
+    case 1: return launch_apply<T, 1>(g, a, s);
+    case 2: return launch_apply<T, 2>(g, a, s);
+    case 4: return launch_apply<T, 4>(g, a, s);
+    case 8: return launch_apply<T, 8>(g, a, s);
+    case 16: return launch_apply<T, 16>(g, a, s);
+    case 32: return launch_apply<T, 32>(g, a, s);
+  }
+  return bf_fail(BF_EINVAL, "bf_apply: bad chunk width");
+}
+
+// Apply op to k columns, split into power-of-two chunks whose vector loads are aligned.
+template <typename T>
+static int apply_block(const bf_graph* g, int op, const T* X, int64_t ldx, int k, T* Y,
+                       int64_t ldy, double* dots, cudaStream_t s) {
+  ApplyArgs<T> a;
+  a.guide = (const T*)g->guide;
+  a.scale = op == BF_OP_NSYM ? (const T*)g->dis : (op == BF_OP_NDIAGL ? (const T*)g->dls : nullptr);
+  a.wf = g->wf;
+  a.wmode = g->p.weight_mode;
+  a.op = op;
+  a.n = g->n;
+  a.ldx = ldx;
+  a.ldy = ldy;
+  const int kmax_chunk = sizeof(T) == 8 ? 16 : 32;
+  int c0 = 0;
+  while (c0 < k) {
+    int K = kmax_chunk;
+    while (K > k - c0) K >>= 1;
+    // shrink until the chunk's vector loads/stores are aligned
+    for (;;) {
+      const int V = (K % (16 / (int)sizeof(T)) == 0) ? 16 / (int)sizeof(T) : ((K % 2 == 0) ? 2 : 1);
+      const size_t vb = (size_t)V * sizeof(T);
+      const bool ok = ((uintptr_t)(X + c0) % vb == 0) && ((uintptr_t)(Y + c0) % vb == 0) &&
+                      (ldx % V == 0) && (ldy % V == 0);
+      if (ok || K == 1) break;
+      K >>= 1;
+    }
+    a.X = X + c0;
+    a.Y = Y + c0;
+    a.dots = dots ? dots + c0 : nullptr;
+    int rc = apply_chunk<T>(g, K, a, s);
+    if (rc) return rc;
+    c0 += K;
+  }
+  return BF_OK;
+}
+
+// Exposed to the solver translation units.
+int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
+                 int64_t ldy, double* dots, cudaStream_t s) {
+  return apply_block<float>(g, op, X, ldx, k, Y, ldy, dots, s);
+}
+int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
+                 int64_t ldy, double* dots, cudaStream_t s) {
+  return apply_block<double>(g, op, X, ldx, k, Y, ldy, dots, s);
+}
+
+// ================================================================== host: graph
+template <typename T>
+static void fill_geom(Geom<T>& G, const bf_params& p, int nx, int ny, int rx, int ry,
+                      int nfwd, const std::vector<short>& fmap) {
+  memset(&G, 0, sizeof(G));
+  G.nx = nx;
+  G.ny = ny;
+  G.rx = rx;
+  G.ry = ry;
+  G.cross = (p.window == BF_WINDOW_CROSS);
+  G.nfwd = nfwd;
+  const bool is_f = sizeof(T) == 4;
+  const double log2e = 1.4426950408889634;
+  const double ar = std::isinf(p.sigma_r) ? 0.0 : 1.0 / (2.0 * p.sigma_r * p.sigma_r);
+  const double as = std::isinf(p.sigma_s) ? 0.0 : 1.0 / (2.0 * p.sigma_s * p.sigma_s);
+  G.a_r = (T)(is_f ? ar * log2e : ar);
+  const int bw = 2 * rx + 1;
+  for (int dy = -ry; dy <= ry; ++dy)
+    for (int dx = -rx; dx <= rx; ++dx) {
+      const int cell = (dy + ry) * bw + (dx + rx);
+      const double l = -(double)(dx * dx + dy * dy) * as;
+      G.ls[cell] = (T)(is_f ? l * log2e : l);
+      G.fmap[cell] = fmap[cell];
+    }
+}
+
+extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out, void* stream) {
+  if (!p || !guide || !out) return bf_fail(BF_EINVAL, "bf_weights: NULL argument");
+  *out = nullptr;
+  if (p->ndim != 1 && p->ndim != 2) return bf_fail(BF_EINVAL, "bf_weights: ndim must be 1 or 2");
+  if (p->nx < 1 || p->ny < 1) return bf_fail(BF_EINVAL, "bf_weights: empty signal");
+  if (p->ndim == 1 && p->ny != 1) return bf_fail(BF_EINVAL, "bf_weights: ndim 1 needs ny = 1");
+  if (p->nx > INT32_MAX || p->ny > INT32_MAX || p->nx * p->ny > ((int64_t)1 << 40))
+    return bf_fail(BF_EINVAL, "bf_weights: signal too large");
+  const int rmax = p->ndim == 2 ? BF_MAX_R2D : BF_MAX_R1D;
+  if (p->radius < 1 || p->radius > rmax) return bf_fail(BF_EINVAL, "bf_weights: radius out of range");
+  if (p->window != BF_WINDOW_SQUARE && p->window != BF_WINDOW_CROSS)
+    return bf_fail(BF_EINVAL, "bf_weights: bad window");
+  if (p->weight_mode < BF_W_ONTHEFLY || p->weight_mode > BF_W_STORED_BF16)
+    return bf_fail(BF_EINVAL, "bf_weights: bad weight_mode");
+  if (p->dtype != BF_F32 && p->dtype != BF_F64) return bf_fail(BF_EINVAL, "bf_weights: bad dtype");
+  if (p->reserved != 0) return bf_fail(BF_EINVAL, "bf_weights: reserved must be 0");
+  if (!(p->sigma_s > 0) || !(p->sigma_r > 0)) return bf_fail(BF_EINVAL, "bf_weights: sigmas must be > 0");
+  const size_t esz = p->dtype == BF_F64 ? 8 : 4;
+  if ((uintptr_t)guide % esz) return bf_fail(BF_EINVAL, "bf_weights: misaligned guide");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  bf_graph* g = new bf_graph();
+  memset(g, 0, sizeof(*g));
+  g->p = *p;
+  g->nx = (int)p->nx;
+  g->ny = (int)p->ny;
+  g->n = p->nx * p->ny;
+  g->rx = p->radius;
+  g->ry = p->ndim == 2 ? p->radius : 0;
+  g->esize = esz;
+  cudaGetDevice(&g->device);
+  // taps and forward map
+  const int bw = 2 * g->rx + 1, bh = 2 * g->ry + 1;
+  std::vector<short> fmap(bw * bh, -1);
+  int ntaps = 0, nfwd = 0;
+  for (int dy = -g->ry; dy <= g->ry; ++dy)
+    for (int dx = -g->rx; dx <= g->rx; ++dx) {
+      if (p->window == BF_WINDOW_CROSS && dx != 0 && dy != 0) continue;
+      ++ntaps;
+      if (dy > 0 || (dy == 0 && dx > 0)) fmap[(dy + g->ry) * bw + (dx + g->rx)] = (short)nfwd++;
+    }
+  g->ntaps = ntaps;
+  g->nfwd = nfwd;
+  fill_geom<float>(g->gf, *p, g->nx, g->ny, g->rx, g->ry, nfwd, fmap);
+  fill_geom<double>(g->gd, *p, g->nx, g->ny, g->rx, g->ry, nfwd, fmap);
+
+  const size_t nb = (size_t)g->n * esz;
+  int rc = BF_OK;
+  int* dflag = nullptr;
+  auto cleanup = [&](int code) {
+    if (dflag) cudaFree(dflag);
+    bf_graph_free(g);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&g->guide, nb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(guide)"));
+  if ((e = cudaMalloc(&g->d, nb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(d)"));
+  if ((e = cudaMalloc(&g->dinv, nb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(dinv)"));
+  if ((e = cudaMalloc(&g->dis, nb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(dis)"));
+  if ((e = cudaMalloc(&g->dls, nb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(dls)"));
+  if (p->weight_mode != BF_W_ONTHEFLY) {
+    if (p->weight_mode == BF_W_STORED_BF16 && p->dtype != BF_F32)
+      return cleanup(bf_fail(BF_EINVAL, "bf_weights: bf16 weights need dtype BF_F32"));
+    const size_t wb = (size_t)nfwd * g->n * (p->weight_mode == BF_W_STORED_BF16 ? 2 : 4);
+    if ((e = cudaMalloc(&g->wf, wb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(weights)"));
+  }
+  if ((e = cudaMalloc(&dflag, sizeof(int))) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(flag)"));
+  if ((e = cudaMemsetAsync(dflag, 0, sizeof(int), s)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "memset"));
+  if ((e = cudaMemcpyAsync(g->guide, guide, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cleanup(bf_cuda_fail(e, "cudaMemcpyAsync(guide)"));
+  const unsigned blocks = (unsigned)((g->n + BF_THREADS - 1) / BF_THREADS);
+  if (esz == 4)
+    BF_LAUNCH(k_weights<float><<<blocks, BF_THREADS, 0, s>>>(g->gf, (const float*)g->guide, g->n, (float*)g->d,
+                                                   (float*)g->dinv, (float*)g->dis, (float*)g->dls,
+                                                   g->wf, p->weight_mode, dflag));
+  else
+    BF_LAUNCH(k_weights<double><<<blocks, BF_THREADS, 0, s>>>(g->gd, (const double*)g->guide, g->n, (double*)g->d,
+                                                    (double*)g->dinv, (double*)g->dis, (double*)g->dls,
+                                                    g->wf, p->weight_mode, dflag));
+  if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(bf_cuda_fail(e, "k_weights launch"));
+  int hflag = 0;
+  if ((e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cleanup(bf_cuda_fail(e, "cudaMemcpyAsync(flag)"));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "bf_weights sync"));
+  if (hflag) return cleanup(bf_fail(BF_ENONFINITE, "bf_weights: guide holds NaN or Inf"));
+  cudaFree(dflag);
+  dflag = nullptr;
+  (void)rc;
+  *out = g;
+  return BF_OK;
+}
+
+extern "C" int bf_graph_free(bf_graph* g) {
+  if (!g) return BF_OK;
+  void* bufs[] = {g->guide, g->d, g->dinv, g->dis, g->dls, g->wf, g->ws};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete g;
+  return BF_OK;
+}
+
+extern "C" int bf_graph_info(const bf_graph* g, int64_t* n, int32_t* taps, int32_t* dtype) {
+  if (!g) return bf_fail(BF_EINVAL, "bf_graph_info: NULL graph");
+  if (n) *n = g->n;
+  if (taps) *taps = g->ntaps;
+  if (dtype) *dtype = g->p.dtype;
+  return BF_OK;
+}
+
+extern "C" int bf_graph_degree(const bf_graph* g, void* d_out, void* stream) {
+  if (!g || !d_out) return bf_fail(BF_EINVAL, "bf_graph_degree: NULL argument");
+  BF_CUDA(cudaMemcpyAsync(d_out, g->d, (size_t)g->n * g->esize, cudaMemcpyDeviceToDevice,
+                          (cudaStream_t)stream));
+  return BF_OK;
+}
+
+extern "C" int bf_graph_export_weights(const bf_graph* g, void* out, void* stream) {
+  if (!g || !out) return bf_fail(BF_EINVAL, "bf_graph_export_weights: NULL argument");
+  if ((uintptr_t)out % g->esize) return bf_fail(BF_EINVAL, "bf_graph_export_weights: misaligned output");
+  const unsigned blocks = (unsigned)((g->n + BF_THREADS - 1) / BF_THREADS);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->esize == 4)
+    BF_LAUNCH(k_export<float><<<blocks, BF_THREADS, 0, s>>>(g->gf, (const float*)g->guide, g->n, g->wf,
+                                                  g->p.weight_mode, g->ntaps, (float*)out));
+  else
+    BF_LAUNCH(k_export<double><<<blocks, BF_THREADS, 0, s>>>(g->gd, (const double*)g->guide, g->n, g->wf,
+                                                   g->p.weight_mode, g->ntaps, (double*)out));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+// ================================================================== host: operator
+extern "C" int bf_apply(const bf_graph* g, int op, const void* X, int64_t ldx, int k, void* Y,
+                        int64_t ldy, double* dots, void* stream) {
+  if (!g || !X || !Y) return bf_fail(BF_EINVAL, "bf_apply: NULL argument");
+  if (op < BF_OP_W || op > BF_OP_NDIAGL) return bf_fail(BF_EINVAL, "bf_apply: bad op");
+  if (k < 1 || ldx < k || ldy < k) return bf_fail(BF_EINVAL, "bf_apply: need k >= 1 and ld >= k");
+  if ((uintptr_t)X % g->esize || (uintptr_t)Y % g->esize)
+    return bf_fail(BF_EINVAL, "bf_apply: misaligned X or Y");
+  const char* xb = (const char*)X;
+  const char* yb = (const char*)Y;
+  const size_t xspan = ((size_t)(g->n - 1) * ldx + k) * g->esize;
+  const size_t yspan = ((size_t)(g->n - 1) * ldy + k) * g->esize;
+  if (xb < yb + yspan && yb < xb + xspan) return bf_fail(BF_EINVAL, "bf_apply: X and Y overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dots) BF_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * k, s));
+  if (g->esize == 4) return bf_apply_f32(g, op, (const float*)X, ldx, k, (float*)Y, ldy, dots, s);
+  return bf_apply_f64(g, op, (const double*)X, ldx, k, (double*)Y, ldy, dots, s);
+}
+
+extern "C" int bf_simple_filter(const bf_graph* g, const void* x0, int iters, void* x_out,
+                                void* stream) {
+  if (!g || !x0 || !x_out) return bf_fail(BF_EINVAL, "bf_simple_filter: NULL argument");
+  if (iters < 0) return bf_fail(BF_EINVAL, "bf_simple_filter: iters < 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nb = (size_t)g->n * g->esize;
+  if (iters == 0) {
+    if (x0 != x_out) BF_CUDA(cudaMemcpyAsync(x_out, x0, nb, cudaMemcpyDeviceToDevice, s));
+    return BF_OK;
+  }
+  bf_graph* gm = const_cast<bf_graph*>(g);
+  const size_t nba = (nb + 255) & ~(size_t)255;
+  int rc = bf_ws_reserve(gm, 2 * nba);
+  if (rc) return rc;
+  void* tmp[2] = {gm->ws, (char*)gm->ws + nba};
+  // ping-pong through two temporaries; the last step writes x_out unless it aliases x0
+  const void* src = x0;
+  for (int it = 0; it < iters; ++it) {
+    const bool last = (it == iters - 1);
+    void* dst = (last && x_out != src) ? x_out : tmp[it & 1];
+    rc = (g->esize == 4)
+             ? bf_apply_f32(g, BF_OP_DINV_W, (const float*)src, 1, 1, (float*)dst, 1, nullptr, s)
+             : bf_apply_f64(g, BF_OP_DINV_W, (const double*)src, 1, 1, (double*)dst, 1, nullptr, s);
+    if (rc) return rc;
+    if (last && dst != x_out) BF_CUDA(cudaMemcpyAsync(x_out, dst, nb, cudaMemcpyDeviceToDevice, s));
+    src = dst;
+  }
+  return BF_OK;
+}

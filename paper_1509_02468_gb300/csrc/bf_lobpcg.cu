@@ -1,0 +1,1035 @@
+// Algorithm 3 (Section 6) for a block of k vectors: LOBPCG as a low-pass filter for the
+// pencil (L, B), B = D or I, with preconditioner T = D^-1 or I and the optional
+// constraint x ⊥_B e.
+//
+// Device pipeline of one iteration (all state on the GPU, no host read-back):
+//   [project W off e]  ->  AW = L W (matrix-free operator)  ->  Gram partials of
+//   G_A = S^T (A S) and G_B = S^T (B S), S = [X W P], FP32 products with compensated
+//   accumulation, FP64 across blocks  ->  one-CTA FP64 Rayleigh-Ritz (unit-diagonal
+//   scaling, Cholesky of G_B with the drop-P restart, standard form, parallel cyclic
+//   Jacobi, ascending sort)  ->  fused update X = S C_X, AX = AS C_X, P = [W P] C_{WP},
+//   AP = [AW AP] C_{WP}, and the next residual W = T (AX - B X Theta) with its norms.
+// Buffers ping-pong between two copies; the final kernels pick the current copy from the
+// device-side iteration count, so an early stop (tolerance or breakdown) needs no sync.
+#include <math.h>
+
+#include <algorithm>
+
+#include "bf_internal.cuh"
+
+int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
+                 int64_t ldy, double* dots, cudaStream_t s);
+int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
+                 int64_t ldy, double* dots, cudaStream_t s);
+
+#define LOB_KMAX 32
+#define LOB_MMAX 96
+#define RR_THREADS 512
+#define GRAM_THREADS 512
+#define GRAM_PX 32
+#define DEP_TOL 1e-10
+
+namespace {
+
+enum { LOB_RUN = 0, LOB_CONV = 1, LOB_BREAK = 2, LOB_NONFINITE = 3 };
+
+struct LobState {
+  double theta[LOB_KMAX];
+  double resid[LOB_KMAX];
+  double cw[LOB_KMAX];      // e^T B W / e^T B e (constraint projection coefficients)
+  double ebe;               // e^T B e
+  double tol;
+  int status;
+  int iter;                 // completed iterations
+  int restarts;
+  int pad;
+  unsigned int counter;
+  unsigned int pad2;
+};
+
+// ------------------------------------------------------------------ apply wrapper
+template <typename T>
+int apply_T(const bf_graph* g, int op, const T* X, int64_t ldx, int k, T* Y, int64_t ldy,
+            cudaStream_t s);
+template <>
+int apply_T<float>(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
+                   int64_t ldy, cudaStream_t s) {
+  return bf_apply_f32(g, op, X, ldx, k, Y, ldy, nullptr, s);
+}
+template <>
+int apply_T<double>(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
+                    int64_t ldy, cudaStream_t s) {
+  return bf_apply_f64(g, op, X, ldx, k, Y, ldy, nullptr, s);
+}
+
+// ------------------------------------------------------------------ runtime-width grid sums
+// Each block adds its per-value sums into shared memory (sh[0..nv)); then the block writes
+// them as partials and the last block to arrive sums all partials in block order.
+// Returns true in every thread of the last block; `out` (nv doubles) is then valid.
+__device__ bool grid_colsum_last(const double* sh, int nv, double* partials,
+                                 unsigned int* counter, double* out, int* is_last_sh) {
+  const unsigned nb = gridDim.x;
+  __syncthreads();
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) partials[(size_t)blockIdx.x * nv + j] = sh[j];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *is_last_sh = (atomicAdd(counter, 1u) == nb - 1);
+  __syncthreads();
+  if (!*is_last_sh) return false;
+  __threadfence();
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    double s = 0.0;
+    for (unsigned b = 0; b < nb; ++b) s += ((volatile double*)partials)[(size_t)b * nv + j];
+    out[j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ------------------------------------------------------------------ small kernels
+// Copy a block [n][ldx] -> [n][k] (contiguous).
+template <typename T>
+__global__ void k_copy_block(const T* __restrict__ X, int64_t ldx, int k, int64_t n, T* Y) {
+  const int64_t tot = n * k;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / k;
+    const int c = (int)(q - i * k);
+    Y[q] = X[i * ldx + c];
+  }
+}
+
+// Sums for the constraint: cs[c] = sum_i b_i V[i][c] (c < k), cs[k] = sum_i b_i.  The last
+// block stores cw[c] = cs[c] / cs[k] and ebe = cs[k].  Thread t of a block owns column
+// t % k of pixel lane t / k.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bsums(const T* __restrict__ V, int k, int64_t n,
+                                               const T* __restrict__ b, double* partials,
+                                               LobState* st) {
+  if (st->status != LOB_RUN) return;
+  __shared__ double sh[LOB_KMAX + 1];
+  __shared__ double out[LOB_KMAX + 1];
+  __shared__ int last;
+  for (int j = threadIdx.x; j <= k; j += blockDim.x) sh[j] = 0.0;
+  __syncthreads();
+  const int lanes = blockDim.x / k;
+  const int pl = threadIdx.x / k, c = threadIdx.x - pl * k;
+  T acc = T(0), accb = T(0);
+  if (pl < lanes) {
+    for (int64_t i = (int64_t)blockIdx.x * lanes + pl; i < n; i += (int64_t)gridDim.x * lanes) {
+      const T bi = b ? b[i] : T(1);
+      acc = fma(bi, V[i * k + c], acc);
+      if (c == 0) accb += bi;
+    }
+    atomicAdd(&sh[c], (double)acc);
+    if (c == 0) atomicAdd(&sh[k], (double)accb);
+  }
+  if (grid_colsum_last(sh, k + 1, partials, &st->counter, out, &last)) {
+    if (threadIdx.x == 0) {
+      st->ebe = out[k];
+      for (int q = 0; q < k; ++q) st->cw[q] = out[q] / out[k];
+    }
+  }
+}
+
+// Reset the state before a run (kernel form, so the whole run can be captured in a graph).
+__global__ void k_state_init(LobState* st, double tol) {
+  if (threadIdx.x == 0) {
+    st->status = LOB_RUN;
+    st->iter = 0;
+    st->restarts = 0;
+    st->counter = 0u;
+    st->tol = tol;
+    st->ebe = 0.0;
+  }
+  if (threadIdx.x < LOB_KMAX) {
+    st->theta[threadIdx.x] = 0.0;
+    st->resid[threadIdx.x] = 0.0;
+    st->cw[threadIdx.x] = 0.0;
+  }
+}
+
+__global__ void k_state_iter0(LobState* st) {
+  if (threadIdx.x == 0) st->iter = 0;
+}
+
+template <typename T>
+struct XPair {
+  const T* p[2];
+};
+
+// V[i][c] -= cw[c]  (B-orthogonal projection off e, coefficients from k_bsums/k_update).
+template <typename T>
+__global__ void k_project(T* V, int k, int64_t n, const LobState* st) {
+  if (st->status != LOB_RUN) return;
+  const int64_t tot = n * k;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q % k);
+    V[q] -= (T)st->cw[c];
+  }
+}
+
+// ------------------------------------------------------------------ Gram partials
+// Block b accumulates, over its pixel chunks, G_A[a][c] = sum_i S[i][a] AS[i][c] and
+// G_B[a][c] = sum_i b_i S[i][a] S[i][c] for a < m and c < m4 (m rounded up to 4).
+// Work item = (a, quad of c); IT items per thread, or NG pixel groups when items are few.
+// Float path: FP32 sums over a chunk of GRAM_PX pixels folded into (hi, lo) pairs by
+// TwoSum; the block result hi + lo is written in FP64.
+template <typename T>
+struct GramArgs {
+  const T* S[3];
+  const T* AS[3];
+  const T* b;        // B diagonal (NULL: I)
+  int nblk, k, m, m4;
+  int64_t n;
+  double* partials;  // [gridDim.x][2][m][m4]
+  const LobState* st;
+};
+
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+__device__ __forceinline__ void two_sum(double& hi, double& lo, double x) { hi += x; }
+
+template <typename T, int IT>
+__global__ void __launch_bounds__(GRAM_THREADS) k_gram(const GramArgs<T> a) {
+  if (a.st->status != LOB_RUN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = a.m, m4 = a.m4, k = a.k;
+  T* sS = reinterpret_cast<T*>(smem);            // [GRAM_PX][m4]
+  T* sA = sS + GRAM_PX * m4;                      // [GRAM_PX][m4]
+  T* sb = sA + GRAM_PX * m4;                      // [GRAM_PX]
+  const int items = m * (m4 / 4);
+  const int ng = (IT == 1) ? max(1, GRAM_THREADS / items) : 1;
+  const int grp = (IT == 1) ? (int)threadIdx.x / items : 0;
+  T hA[IT][4], lA[IT][4], hB[IT][4], lB[IT][4];
+#pragma unroll
+  for (int q = 0; q < IT; ++q)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) hA[q][e] = lA[q][e] = hB[q][e] = lB[q][e] = T(0);
+  const int64_t nchunks = (a.n + GRAM_PX - 1) / GRAM_PX;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t i0 = ch * GRAM_PX;
+    __syncthreads();
+    for (int q = threadIdx.x; q < GRAM_PX * m4; q += GRAM_THREADS) {
+      const int p = q / m4, col = q - p * m4;
+      const int64_t i = i0 + p;
+      T vs = T(0), va = T(0);
+      if (i < a.n && col < m) {
+        const int blk = col / k, c = col - blk * k;
+        vs = a.S[blk][i * k + c];
+        va = a.AS[blk][i * k + c];
+      }
+      sS[q] = vs;
+      sA[q] = va;
+    }
+    for (int p = threadIdx.x; p < GRAM_PX; p += GRAM_THREADS) {
+      const int64_t i = i0 + p;
+      sb[p] = (i < a.n) ? (a.b ? a.b[i] : T(1)) : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+      const int it = (IT == 1) ? ((int)threadIdx.x - grp * items) : ((int)threadIdx.x + q * GRAM_THREADS);
+      if (it >= items || (IT == 1 && grp >= ng)) continue;
+      const int ar = it / (m4 / 4), cq = it - ar * (m4 / 4);
+      T cA[4] = {T(0), T(0), T(0), T(0)}, cB[4] = {T(0), T(0), T(0), T(0)};
+      for (int p = grp; p < GRAM_PX; p += ng) {
+        const T sa = sS[p * m4 + ar];
+        const T bsa = sb[p] * sa;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          cA[e] = fma(sa, sA[p * m4 + cq * 4 + e], cA[e]);
+          cB[e] = fma(bsa, sS[p * m4 + cq * 4 + e], cB[e]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        two_sum(hA[q][e], lA[q][e], cA[e]);
+        two_sum(hB[q][e], lB[q][e], cB[e]);
+      }
+    }
+  }
+  // combine pixel groups (IT == 1) through shared memory, then write the block partial
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem);   // [GRAM_THREADS][8]
+  double* out = a.partials + (size_t)blockIdx.x * 2 * m * m4;
+  if (IT == 1) {
+    const int it = (int)threadIdx.x - grp * items;
+    if (grp < ng && it < items) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        red[threadIdx.x * 8 + e] = (double)hA[0][e] + (double)lA[0][e];
+        red[threadIdx.x * 8 + 4 + e] = (double)hB[0][e] + (double)lB[0][e];
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < items) {
+      const int it0 = threadIdx.x;
+      const int ar = it0 / (m4 / 4), cq = it0 - ar * (m4 / 4);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        double s = 0.0;
+        for (int gq = 0; gq < ng; ++gq) s += red[(gq * items + it0) * 8 + e];
+        const int c = cq * 4 + (e & 3);
+        out[(size_t)((e < 4) ? 0 : 1) * m * m4 + (size_t)ar * m4 + c] = s;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < IT; ++q) {
+      const int it = (int)threadIdx.x + q * GRAM_THREADS;
+      if (it >= items) continue;
+      const int ar = it / (m4 / 4), cq = it - ar * (m4 / 4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        out[(size_t)ar * m4 + cq * 4 + e] = (double)hA[q][e] + (double)lA[q][e];
+        out[(size_t)m * m4 + (size_t)ar * m4 + cq * 4 + e] = (double)hB[q][e] + (double)lB[q][e];
+      }
+    }
+  }
+}
+
+// Sum the Gram partials over blocks in order: G[2][m][m] (compact).
+__global__ void k_gram_reduce(const double* __restrict__ partials, int nblocks, int m, int m4,
+                              double* G, const LobState* st) {
+  if (st->status != LOB_RUN) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 2 * m * m) return;
+  const int w = q / (m * m), r = q - w * m * m;
+  const int a = r / m, c = r - a * m;
+  const size_t off = (size_t)w * m * m4 + (size_t)a * m4 + c;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * 2 * m * m4 + off];
+  G[q] = s;
+}
+
+// ------------------------------------------------------------------ Rayleigh-Ritz (FP64)
+// One CTA.  Input G[0] = G_A, G[1] = G_B (m x m).  Scale to unit diagonal of G_B,
+// Cholesky G_B = R R^T (squared pivot <= DEP_TOL: the basis is dependent -- retry on the
+// leading m_nop x m_nop block, i.e. without P, if allowed), M = R^-1 G_A R^-T, cyclic
+// Jacobi with a round-robin (parallel) ordering, sort ascending, C = R^-T V scaled back.
+// Output C [m][k] (rows of dropped columns are 0) and theta into the state.
+struct RRArgs {
+  const double* G;
+  int m, k, m_nop;   // m_nop: size without P (0: no retry)
+  double* C;         // [m][k]
+  LobState* st;
+  double* theta_hist;   // [k] slot for this call, or NULL
+};
+
+__device__ __forceinline__ void jacobi_pair(int step, int i, int mp, int& p, int& q) {
+  // circle method: index mp-1 fixed, the others rotate
+  const int n1 = mp - 1;
+  if (i == 0) {
+    p = step % n1;
+    q = n1;
+  } else {
+    p = (step + i) % n1;
+    q = (step - i + n1) % n1;
+  }
+  if (p > q) { const int t = p; p = q; q = t; }
+}
+
+__global__ void __launch_bounds__(RR_THREADS) k_rr(const RRArgs a) {
+  LobState* st = a.st;
+  if (st->status != LOB_RUN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int k = a.k;
+  int m = a.m;
+  int mp = m + (m & 1);
+  // layout: M[mp][mp] (A, then the standard form), R[mp][mp] (B, then its factor),
+  // V[mp][mp], then vectors
+  double* M = reinterpret_cast<double*>(smem);
+  double* R = M + LOB_MMAX * LOB_MMAX;
+  double* V = R + LOB_MMAX * LOB_MMAX;
+  double* sc = V + LOB_MMAX * LOB_MMAX;          // [LOB_MMAX] scaling
+  double* tv = sc + LOB_MMAX;                     // [LOB_MMAX] Cholesky column
+  double* cs = tv + LOB_MMAX;                     // [LOB_MMAX / 2] rotation cos
+  double* sn = cs + LOB_MMAX / 2;                 // [LOB_MMAX / 2] rotation sin
+  int* perm = reinterpret_cast<int*>(sn + LOB_MMAX / 2);   // [LOB_MMAX]
+  __shared__ int fail, nrot, dropped;
+  const int tid = threadIdx.x;
+  const int LD = LOB_MMAX;
+  if (tid == 0) dropped = 0;
+
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    __syncthreads();
+    mp = m + (m & 1);
+    // load + symmetrise
+    for (int q = tid; q < mp * mp; q += RR_THREADS) {
+      const int r = q / mp, c = q - r * mp;
+      double va = 0.0, vb = 0.0;
+      if (r < m && c < m) {
+        va = 0.5 * (a.G[r * a.m + c] + a.G[c * a.m + r]);
+        vb = 0.5 * (a.G[a.m * a.m + r * a.m + c] + a.G[a.m * a.m + c * a.m + r]);
+      }
+      M[r * LD + c] = va;
+      R[r * LD + c] = vb;
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int r = tid; r < m; r += RR_THREADS) {
+      const double dg = R[r * LD + r];
+      if (!(dg > 0.0) || !isfinite(dg)) fail = 1;
+      sc[r] = (dg > 0.0) ? 1.0 / sqrt(dg) : 0.0;
+    }
+    __syncthreads();
+    if (!fail) {
+      for (int q = tid; q < m * m; q += RR_THREADS) {
+        const int r = q / m, c = q - r * m;
+        M[r * LD + c] *= sc[r] * sc[c];
+        R[r * LD + c] *= sc[r] * sc[c];
+      }
+      __syncthreads();
+      // left-looking Cholesky, lower factor stored in R (strict upper part left as is)
+      for (int j = 0; j < m && !fail; ++j) {
+        for (int i = j + tid; i < m; i += RR_THREADS) {
+          double s = R[i * LD + j];
+          for (int p = 0; p < j; ++p) s -= R[i * LD + p] * R[j * LD + p];
+          tv[i] = s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          if (!(tv[j] > DEP_TOL)) fail = 1;
+          else tv[j] = sqrt(tv[j]);
+        }
+        __syncthreads();
+        if (!fail)
+          for (int i = j + tid; i < m; i += RR_THREADS) R[i * LD + j] = (i == j) ? tv[j] : tv[i] / tv[j];
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    if (!fail) break;
+    if (attempt == 0 && a.m_nop > 0 && a.m_nop < a.m) {
+      m = a.m_nop;
+      if (tid == 0) dropped = 1;
+      continue;
+    }
+    if (tid == 0) st->status = LOB_BREAK;
+    return;
+  }
+  // standard form: V := R^-1 M (column-wise forward substitution), then M := R^-1 V^T
+  for (int c = tid; c < m; c += RR_THREADS) {
+    for (int i = 0; i < m; ++i) {
+      double s = M[i * LD + c];
+      for (int p = 0; p < i; ++p) s -= R[i * LD + p] * V[p * LD + c];
+      V[i * LD + c] = s / R[i * LD + i];
+    }
+  }
+  __syncthreads();
+  for (int c = tid; c < m; c += RR_THREADS) {
+    for (int i = 0; i < m; ++i) {
+      double s = V[c * LD + i];
+      for (int p = 0; p < i; ++p) s -= R[i * LD + p] * M[p * LD + c];
+      M[i * LD + c] = s / R[i * LD + i];
+    }
+  }
+  __syncthreads();
+  // symmetrise (upper from lower), pad, V = I
+  for (int q = tid; q < mp * mp; q += RR_THREADS) {
+    const int r = q / mp, c = q - r * mp;
+    if (r < m && c < m && r < c) {
+      const double v = 0.5 * (M[r * LD + c] + M[c * LD + r]);
+      M[r * LD + c] = v;
+      M[c * LD + r] = v;
+    }
+    if (r >= m || c >= m) M[r * LD + c] = (r == c) ? 1e300 : 0.0;
+    V[r * LD + c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // parallel cyclic Jacobi
+  const int npair = mp / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) nrot = 0;
+    __syncthreads();
+    for (int step = 0; step < mp - 1; ++step) {
+      for (int i = tid; i < npair; i += RR_THREADS) {
+        int p, q;
+        jacobi_pair(step, i, mp, p, q);
+        const double apq = M[p * LD + q];
+        const double app = M[p * LD + p], aqq = M[q * LD + q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (fabs(tau) > 1e150) ? 0.5 / tau
+                                                 : ((tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                                                 : -1.0 / (-tau + sqrt(1.0 + tau * tau)));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+          atomicAdd(&nrot, 1);
+        }
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      // rows: M <- J^T M
+      for (int q2 = tid; q2 < npair * mp; q2 += RR_THREADS) {
+        const int i = q2 / mp, j = q2 - i * mp;
+        if (sn[i] == 0.0) continue;
+        int p, q;
+        jacobi_pair(step, i, mp, p, q);
+        const double x = M[p * LD + j], y = M[q * LD + j];
+        M[p * LD + j] = cs[i] * x - sn[i] * y;
+        M[q * LD + j] = sn[i] * x + cs[i] * y;
+      }
+      __syncthreads();
+      // columns: M <- M J, V <- V J
+      for (int q2 = tid; q2 < npair * mp; q2 += RR_THREADS) {
+        const int i = q2 / mp, r = q2 - i * mp;
+        if (sn[i] == 0.0) continue;
+        int p, q;
+        jacobi_pair(step, i, mp, p, q);
+        const double x = M[r * LD + p], y = M[r * LD + q];
+        M[r * LD + p] = cs[i] * x - sn[i] * y;
+        M[r * LD + q] = sn[i] * x + cs[i] * y;
+        const double vx = V[r * LD + p], vy = V[r * LD + q];
+        V[r * LD + p] = cs[i] * vx - sn[i] * vy;
+        V[r * LD + q] = sn[i] * vx + cs[i] * vy;
+      }
+      __syncthreads();
+    }
+    if (nrot == 0) break;
+    __syncthreads();
+  }
+  // ascending order (ties by index)
+  for (int i = tid; i < mp; i += RR_THREADS) {
+    const double li = M[i * LD + i];
+    int rank = 0;
+    for (int j = 0; j < mp; ++j) {
+      const double lj = M[j * LD + j];
+      rank += (lj < li) || (lj == li && j < i);
+    }
+    perm[rank] = i;
+  }
+  __syncthreads();
+  // C = R^-T V[:, perm[0..k)], then undo the scaling; rows past m (dropped P) are 0
+  for (int j = tid; j < k; j += RR_THREADS) {
+    const int col = perm[j];
+    for (int i = m - 1; i >= 0; --i) {
+      double s = V[i * LD + col];
+      for (int p = i + 1; p < m; ++p) s -= R[p * LD + i] * a.C[p * k + j];
+      a.C[i * k + j] = s / R[i * LD + i];
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < a.m * k; q += RR_THREADS) {
+    const int r = q / k;
+    a.C[q] = (r < m) ? a.C[q] * sc[r] : 0.0;
+  }
+  if (tid < k) {
+    const double th = M[perm[tid] * LD + perm[tid]];
+    st->theta[tid] = th;
+    if (a.theta_hist) a.theta_hist[tid] = th;
+    if (!isfinite(th)) st->status = LOB_NONFINITE;
+  }
+  if (tid == 0 && dropped) st->restarts += 1;
+}
+
+// ------------------------------------------------------------------ update
+// For a tile of pixels and a group of CW columns per thread:
+//   X' = S C[:, cols];  P' = [W P] C[k:, cols] and AP' = [AW AP] C[k:, cols] (nblk >= 2).
+// A X' is not formed here: it is recomputed as L X' by the operator kernel, because the
+// combination [AX AW AP] C cancels heavily once X is nearly converged (AX ~ theta B X is
+// small next to AW C_W), which costs FP32 accuracy.
+template <typename T>
+struct UpdArgs {
+  const T* S[3];
+  const T* AS[3];
+  int nblk, k, m;
+  int64_t n;
+  const double* C;       // [m][k]
+  T* Xn;
+  T* Pn;                 // NULL when nblk == 1
+  T* APn;
+  const LobState* st;
+};
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
+  if (a.st->status != LOB_RUN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int k = a.k, m = a.m;
+  const int ngrp = k / CW;
+  const int pt = 256 / ngrp;                  // pixels per pass
+  T* sC = reinterpret_cast<T*>(smem);         // [m][k]
+  T* sS = sC + m * k;                         // [pt][m]
+  T* sA = sS + pt * m;                        // [pt][m]  (AS rows of W and P only)
+  for (int q = threadIdx.x; q < m * k; q += 256) sC[q] = (T)a.C[q];
+  const int p_loc = threadIdx.x / ngrp, g = threadIdx.x - p_loc * ngrp;
+  const bool with_p = a.Pn != nullptr;
+  const int64_t npass = (a.n + pt - 1) / pt;
+  for (int64_t ps = blockIdx.x; ps < npass; ps += gridDim.x) {
+    const int64_t i0 = ps * pt;
+    __syncthreads();
+    for (int q = threadIdx.x; q < pt * m; q += 256) {
+      const int p = q / m, col = q - p * m;
+      const int64_t i = i0 + p;
+      T vs = T(0), va = T(0);
+      if (i < a.n) {
+        const int blk = col / k, c = col - blk * k;
+        vs = a.S[blk][i * k + c];
+        if (with_p && blk > 0) va = a.AS[blk][i * k + c];
+      }
+      sS[q] = vs;
+      sA[q] = va;
+    }
+    __syncthreads();
+    const int64_t i = i0 + p_loc;
+    if (p_loc < pt && i < a.n) {
+      T x[CW], pp[CW], ap[CW];
+#pragma unroll
+      for (int e = 0; e < CW; ++e) x[e] = pp[e] = ap[e] = T(0);
+      for (int r = 0; r < k; ++r) {
+        const T s = sS[p_loc * m + r];
+#pragma unroll
+        for (int e = 0; e < CW; ++e) x[e] = fma(s, sC[r * k + g * CW + e], x[e]);
+      }
+      for (int r = k; r < m; ++r) {
+        const T s = sS[p_loc * m + r], as = sA[p_loc * m + r];
+#pragma unroll
+        for (int e = 0; e < CW; ++e) {
+          const T c = sC[r * k + g * CW + e];
+          pp[e] = fma(s, c, pp[e]);
+          ap[e] = fma(as, c, ap[e]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < CW; ++e) {
+        const int c = g * CW + e;
+        a.Xn[i * k + c] = x[e] + pp[e];
+        if (with_p) {
+          a.Pn[i * k + c] = pp[e];
+          a.APn[i * k + c] = ap[e];
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ residual
+// R = AX - b X theta, W = t R (t = 1/d or 1), per-column sums of R^2, (b X)^2 and b W
+// (thread t of a block owns column t % k of pixel lane t / k).  The last block writes the
+// relative residual norms and the constraint coefficients e^T B W / e^T B e, counts the
+// step and applies the tolerance test.
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T* __restrict__ AX,
+                                               int k, int64_t n, const T* b, const T* tinv,
+                                               T* Wn, int constrain, double* partials,
+                                               LobState* st) {
+  if (st->status != LOB_RUN) return;
+  __shared__ double sums[3 * LOB_KMAX];
+  __shared__ double outs[3 * LOB_KMAX];
+  __shared__ int last;
+  for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) sums[q] = 0.0;
+  __syncthreads();
+  const int lanes = blockDim.x / k;
+  const int pl = threadIdx.x / k, c = threadIdx.x - pl * k;
+  T r2 = T(0), bx2 = T(0), bw = T(0);
+  if (pl < lanes) {
+    const T th = (T)st->theta[c];
+    for (int64_t i = (int64_t)blockIdx.x * lanes + pl; i < n; i += (int64_t)gridDim.x * lanes) {
+      const T bi = b ? b[i] : T(1);
+      const T ti = tinv ? tinv[i] : T(1);
+      const T bx = bi * X[i * k + c];
+      const T rr = AX[i * k + c] - bx * th;
+      const T w = ti * rr;
+      Wn[i * k + c] = w;
+      r2 = fma(rr, rr, r2);
+      bx2 = fma(bx, bx, bx2);
+      bw = fma(bi, w, bw);
+    }
+    atomicAdd(&sums[c], (double)r2);
+    atomicAdd(&sums[k + c], (double)bx2);
+    atomicAdd(&sums[2 * k + c], (double)bw);
+  }
+  if (grid_colsum_last(sums, 3 * k, partials, &st->counter, outs, &last)) {
+    if (threadIdx.x < k) {
+      const int q = threadIdx.x;
+      st->resid[q] = sqrt(outs[q]) / sqrt(outs[k + q]);
+      st->cw[q] = constrain ? outs[2 * k + q] / st->ebe : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st->iter += 1;
+      double mx = 0.0;
+      bool fin = true;
+      for (int q = 0; q < k; ++q) {
+        mx = fmax(mx, st->resid[q]);
+        fin = fin && isfinite(st->resid[q]);
+      }
+      if (!fin) st->status = LOB_NONFINITE;
+      else if (st->tol > 0.0 && mx <= st->tol) st->status = LOB_CONV;
+    }
+  }
+}
+
+// y = X c + ebar (constrained) with c = X^T B (x0 - ebar e).  First the sums
+// out[c] = sum b_i X_ic x0_i, out[k + c] = sum b_i X_ic, out[2k] = sum b_i x0_i,
+// out[2k + 1] = sum b_i (column-lane mapping as in k_bsums), then the combination.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ysums(const XPair<T> xs, int k, int64_t n,
+                                               const T* __restrict__ x0, int64_t ldx0,
+                                               const T* b, double* partials, LobState* st,
+                                               double* out) {
+  __shared__ double sh[2 * LOB_KMAX + 2];
+  __shared__ int last;
+  const T* X = xs.p[st->iter & 1];
+  for (int j = threadIdx.x; j < 2 * k + 2; j += blockDim.x) sh[j] = 0.0;
+  __syncthreads();
+  const int lanes = blockDim.x / k;
+  const int pl = threadIdx.x / k, c = threadIdx.x - pl * k;
+  T a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0);
+  if (pl < lanes) {
+    for (int64_t i = (int64_t)blockIdx.x * lanes + pl; i < n; i += (int64_t)gridDim.x * lanes) {
+      const T bi = b ? b[i] : T(1);
+      const T xi = x0[i * ldx0];
+      const T bx = bi * X[i * k + c];
+      a1 = fma(bx, xi, a1);
+      a2 += bx;
+      if (c == 0) {
+        a3 = fma(bi, xi, a3);
+        a4 += bi;
+      }
+    }
+    atomicAdd(&sh[c], (double)a1);
+    atomicAdd(&sh[k + c], (double)a2);
+    if (c == 0) {
+      atomicAdd(&sh[2 * k], (double)a3);
+      atomicAdd(&sh[2 * k + 1], (double)a4);
+    }
+  }
+  grid_colsum_last(sh, 2 * k + 2, partials, &st->counter, out, &last);
+}
+
+template <typename T>
+__global__ void k_yout(const XPair<T> xs, int k, int64_t n, const double* sums, int constrain,
+                       const LobState* st, T* y) {
+  const T* X = xs.p[st->iter & 1];
+  __shared__ T cf[LOB_KMAX + 1];
+  if (threadIdx.x == 0) {
+    const double ebar = constrain ? sums[2 * k] / sums[2 * k + 1] : 0.0;
+    for (int c = 0; c < k; ++c) cf[c] = (T)(sums[c] - ebar * sums[k + c]);
+    cf[k] = (T)ebar;
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = cf[k];
+    for (int c = 0; c < k; ++c) acc = fma(X[i * k + c], cf[c], acc);
+    y[i] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_xout(const XPair<T> xs, int k, int64_t n, const LobState* st, T* out) {
+  const T* X = xs.p[st->iter & 1];
+  const int64_t tot = n * k;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = X[q];
+}
+
+__global__ void k_theta_out(const LobState* st, int k, double* theta, double* resid) {
+  const int c = threadIdx.x;
+  if (c < k) {
+    if (theta) theta[c] = st->theta[c];
+    if (resid) resid[c] = st->resid[c];
+  }
+}
+
+// ------------------------------------------------------------------ host driver
+template <typename T>
+struct LobBuffers {
+  T* X[2];
+  T* AX[2];
+  T* P[2];
+  T* AP[2];
+  T* W[2];
+  T* AW;
+  double* gram_part;
+  double* G;
+  double* C;
+  double* part;       // small reductions
+  double* ysums;
+  LobState* st;
+};
+
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 132;
+  }
+  return n;
+}
+
+template <typename T, int IT>
+static void launch_gram_it(const GramArgs<T>& ga, int grid, size_t sm, cudaStream_t s) {
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_gram<T, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    init = true;
+  }
+  BF_LAUNCH(k_gram<T, IT><<<grid, GRAM_THREADS, sm, s>>>(ga));
+}
+
+template <typename T>
+static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
+  const int items = ga.m * (ga.m4 / 4);
+  const int it = (items + GRAM_THREADS - 1) / GRAM_THREADS;
+  size_t sm = (size_t)(2 * GRAM_PX * ga.m4 + GRAM_PX) * sizeof(T);
+  sm = std::max(sm, (size_t)GRAM_THREADS * 8 * sizeof(double));
+  switch (it) {
+    case 1: launch_gram_it<T, 1>(ga, grid, sm, s); break;
+    case 2: launch_gram_it<T, 2>(ga, grid, sm, s); break;
+    case 3: launch_gram_it<T, 3>(ga, grid, sm, s); break;
+    case 4: launch_gram_it<T, 4>(ga, grid, sm, s); break;
+    case 5: launch_gram_it<T, 5>(ga, grid, sm, s); break;
+    default: return bf_fail(BF_EINVAL, "lobpcg_filter: block too wide");
+  }
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+template <typename T, int CW>
+static void launch_update_cw(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
+  const int ngrp = ua.k / CW;
+  const int pt = 256 / ngrp;
+  const size_t sm = (size_t)(ua.m * ua.k + 2 * pt * ua.m) * sizeof(T);
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_update<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    init = true;
+  }
+  BF_LAUNCH(k_update<T, CW><<<grid, 256, sm, s>>>(ua));
+}
+
+template <typename T>
+static int run_update(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
+  if (ua.k % 4 == 0) launch_update_cw<T, 4>(ua, grid, s);
+  else launch_update_cw<T, 1>(ua, grid, s);
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+// A X = L X, then the residual kernel: W = T (A X - B X theta) and its norms.
+template <typename T>
+static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T* bdiag,
+                     const T* tinv, int constrain, double* part, LobState* st, int rgrid,
+                     cudaStream_t s) {
+  int rc = apply_T<T>(g, BF_OP_L, X, k, k, AX, k, s);
+  if (rc) return rc;
+  BF_LAUNCH(k_resid<T><<<rgrid, 256, 0, s>>>(X, AX, k, g->n, bdiag, tinv, Wn, constrain, part, st));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+static int run_rr(const RRArgs& ra, cudaStream_t s) {
+  static bool init = false;
+  const size_t sm = (size_t)(3 * LOB_MMAX * LOB_MMAX + 3 * LOB_MMAX) * sizeof(double) + LOB_MMAX * sizeof(int);
+  if (!init) {
+    cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    init = true;
+  }
+  BF_LAUNCH(k_rr<<<1, RR_THREADS, sm, s>>>(ra));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+template <typename T>
+int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
+            const bf_lobpcg_opts& o, T* X_out, double* theta_out, double* resid_out, T* y_out,
+            bf_info* info, cudaStream_t s) {
+  bf_graph* gm = const_cast<bf_graph*>(g);
+  const int64_t n = g->n;
+  const int nsm = sm_count();
+  const int ggrid = nsm;                       // Gram blocks
+  const int ugrid = 2 * nsm;                   // update blocks
+  const int rgrid = 2 * nsm;                   // reduction blocks
+  const size_t blk = (((size_t)n * k * sizeof(T)) + 255) & ~(size_t)255;
+  const int m3 = 3 * k, m34 = (m3 + 3) & ~3;
+  const size_t gpb = (((size_t)ggrid * 2 * m3 * m34 * sizeof(double)) + 255) & ~(size_t)255;
+  const size_t gb = ((2 * (size_t)m3 * m3 * sizeof(double)) + 255) & ~(size_t)255;
+  const size_t cb = (((size_t)m3 * k * sizeof(double)) + 255) & ~(size_t)255;
+  const size_t pb = (((size_t)std::max(ugrid, rgrid) * (3 * LOB_KMAX + 2) * sizeof(double)) + 255) & ~(size_t)255;
+  const size_t yb = 256 * sizeof(double) * 2;
+  const size_t total = 11 * blk + gpb + gb + cb + pb + yb + 1024;
+  int rc = bf_ws_reserve(gm, total);
+  if (rc) return rc;
+  char* w = (char*)gm->ws;
+  LobBuffers<T> B;
+  for (int j = 0; j < 2; ++j) {
+    B.X[j] = (T*)w; w += blk;
+    B.AX[j] = (T*)w; w += blk;
+    B.P[j] = (T*)w; w += blk;
+    B.AP[j] = (T*)w; w += blk;
+    B.W[j] = (T*)w; w += blk;
+  }
+  B.AW = (T*)w; w += blk;
+  B.gram_part = (double*)w; w += gpb;
+  B.G = (double*)w; w += gb;
+  B.C = (double*)w; w += cb;
+  B.part = (double*)w; w += pb;
+  B.ysums = (double*)w; w += yb;
+  B.st = (LobState*)w; w += 1024;
+
+  const T* bdiag = (o.pencil == BF_PENCIL_D) ? (const T*)g->d : nullptr;
+  const T* tinv = (o.precond == BF_PRECOND_JACOBI) ? (const T*)g->dinv : nullptr;
+
+  BF_LAUNCH(k_state_init<<<1, 64, 0, s>>>(B.st, o.tol));
+  XPair<T> xs;
+  xs.p[0] = B.X[0];
+  xs.p[1] = B.X[1];
+
+  const int egrid = (int)std::min<int64_t>((n * k + 255) / 256, 4 * nsm);
+  // ---- start block: copy, constrain, A X
+  BF_LAUNCH(k_copy_block<T><<<egrid, 256, 0, s>>>(X0, ldx0, k, n, B.X[1]));
+  BF_CUDA(cudaGetLastError());
+  BF_LAUNCH(k_bsums<T><<<rgrid, 256, 0, s>>>(B.X[1], k, n, bdiag, B.part, B.st));
+  if (o.constrain_e) BF_LAUNCH(k_project<T><<<egrid, 256, 0, s>>>(B.X[1], k, n, B.st));
+  BF_CUDA(cudaGetLastError());
+  rc = apply_T<T>(g, BF_OP_L, B.X[1], k, k, B.AX[1], k, s);
+  if (rc) return rc;
+  // Rayleigh-Ritz on span(X0)
+  GramArgs<T> ga;
+  memset(&ga, 0, sizeof(ga));
+  ga.b = bdiag;
+  ga.k = k;
+  ga.n = n;
+  ga.partials = B.gram_part;
+  ga.st = B.st;
+  ga.nblk = 1;
+  ga.S[0] = B.X[1];
+  ga.AS[0] = B.AX[1];
+  ga.m = k;
+  ga.m4 = (k + 3) & ~3;
+  rc = run_gram<T>(ga, ggrid, s);
+  if (rc) return rc;
+  const int rthreads = 256;
+  BF_LAUNCH(k_gram_reduce<<<(2 * k * k + rthreads - 1) / rthreads, rthreads, 0, s>>>(B.gram_part, ggrid, k, ga.m4, B.G, B.st));
+  RRArgs ra;
+  ra.G = B.G;
+  ra.C = B.C;
+  ra.st = B.st;
+  ra.k = k;
+  ra.m = k;
+  ra.m_nop = 0;
+  ra.theta_hist = o.theta_hist;
+  rc = run_rr(ra, s);
+  if (rc) return rc;
+  UpdArgs<T> ua;
+  memset(&ua, 0, sizeof(ua));
+  ua.k = k;
+  ua.n = n;
+  ua.C = B.C;
+  ua.st = B.st;
+  ua.nblk = 1;
+  ua.m = k;
+  ua.S[0] = B.X[1];
+  ua.AS[0] = B.AX[1];
+  ua.Xn = B.X[0];
+  ua.Pn = nullptr;
+  ua.APn = nullptr;
+  rc = run_update<T>(ua, ugrid, s);
+  if (rc) return rc;
+  rc = run_resid<T>(g, B.X[0], B.AX[0], k, B.W[0], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s);
+  if (rc) return rc;
+  // the start step counted as one residual evaluation: iterations count from 0 after it
+  BF_LAUNCH(k_state_iter0<<<1, 32, 0, s>>>(B.st));
+  // ---- iterations: current copy j = it & 1, next copy 1 - j
+  for (int it = 0; it < kmax; ++it) {
+    const int j = it & 1, nj = 1 - j;
+    if (o.constrain_e) BF_LAUNCH(k_project<T><<<egrid, 256, 0, s>>>(B.W[j], k, n, B.st));
+    rc = apply_T<T>(g, BF_OP_L, B.W[j], k, k, B.AW, k, s);
+    if (rc) return rc;
+    const int nblk = (it == 0) ? 2 : 3;
+    ga.nblk = nblk;
+    ga.m = nblk * k;
+    ga.m4 = (ga.m + 3) & ~3;
+    ga.S[0] = B.X[j];
+    ga.AS[0] = B.AX[j];
+    ga.S[1] = B.W[j];
+    ga.AS[1] = B.AW;
+    ga.S[2] = B.P[j];
+    ga.AS[2] = B.AP[j];
+    rc = run_gram<T>(ga, ggrid, s);
+    if (rc) return rc;
+    BF_LAUNCH(k_gram_reduce<<<(2 * ga.m * ga.m + rthreads - 1) / rthreads, rthreads, 0, s>>>(B.gram_part, ggrid, ga.m, ga.m4, B.G, B.st));
+    ra.m = ga.m;
+    ra.m_nop = (nblk == 3) ? 2 * k : 0;
+    ra.theta_hist = o.theta_hist ? o.theta_hist + (size_t)(it + 1) * k : nullptr;
+    rc = run_rr(ra, s);
+    if (rc) return rc;
+    ua.nblk = nblk;
+    ua.m = ga.m;
+    for (int b2 = 0; b2 < 3; ++b2) {
+      ua.S[b2] = ga.S[b2];
+      ua.AS[b2] = ga.AS[b2];
+    }
+    ua.Xn = B.X[nj];
+    ua.Pn = B.P[nj];
+    ua.APn = B.AP[nj];
+    rc = run_update<T>(ua, ugrid, s);
+    if (rc) return rc;
+    rc = run_resid<T>(g, B.X[nj], B.AX[nj], k, B.W[nj], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s);
+    if (rc) return rc;
+  }
+  // ---- outputs
+  if (X_out) BF_LAUNCH(k_xout<T><<<egrid, 256, 0, s>>>(xs, k, n, B.st, X_out));
+  if (theta_out || resid_out) BF_LAUNCH(k_theta_out<<<1, 32, 0, s>>>(B.st, k, theta_out, resid_out));
+  if (y_out) {
+    BF_LAUNCH(k_ysums<T><<<rgrid, 256, 0, s>>>(xs, k, n, X0, ldx0, bdiag, B.part, B.st, B.ysums));
+    BF_LAUNCH(k_yout<T><<<egrid, 256, 0, s>>>(xs, k, n, B.ysums, o.constrain_e, B.st, y_out));
+  }
+  BF_CUDA(cudaGetLastError());
+  if (info) {
+    LobState h;
+    BF_CUDA(cudaMemcpyAsync(&h, B.st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    info->iters = h.iter;
+    info->status = h.status == LOB_CONV ? BF_CG_CONVERGED : (h.status == LOB_BREAK ? BF_CG_BREAKDOWN : 0);
+    info->restarts = h.restarts;
+    info->reserved = 0;
+    double mx = 0.0;
+    for (int c = 0; c < k; ++c) mx = std::max(mx, h.resid[c]);
+    info->rnorm = mx;
+    info->ref = 0.0;
+    if (h.status == LOB_BREAK) return bf_fail(BF_EBREAKDOWN, "lobpcg_filter: dependent trial basis");
+    if (h.status == LOB_NONFINITE) return bf_fail(BF_ENONFINITE, "lobpcg_filter: non-finite value");
+  }
+  return BF_OK;
+}
+
+}  // namespace
+
+extern "C" int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, int k, int kmax,
+                             const bf_lobpcg_opts* opts, void* X_out, double* theta_out,
+                             double* resid_out, void* y_out, bf_info* info, void* stream) {
+  if (!g || !X0) return bf_fail(BF_EINVAL, "lobpcg_filter: NULL argument");
+  if (k < 1 || k > LOB_KMAX) return bf_fail(BF_EINVAL, "lobpcg_filter: need 1 <= k <= 32");
+  if ((int64_t)3 * k > g->n) return bf_fail(BF_EINVAL, "lobpcg_filter: need 3k <= n");
+  if (kmax < 0 || ldx0 < k) return bf_fail(BF_EINVAL, "lobpcg_filter: need kmax >= 0 and ldx0 >= k");
+  bf_lobpcg_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.pencil != BF_PENCIL_D && o.pencil != BF_PENCIL_I) return bf_fail(BF_EINVAL, "lobpcg_filter: bad pencil");
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY)
+    return bf_fail(BF_EINVAL, "lobpcg_filter: bad precond");
+  if (!(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "lobpcg_filter: tol must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->esize == 4)
+    return lob_run<float>(g, (const float*)X0, ldx0, k, kmax, o, (float*)X_out, theta_out, resid_out,
+                          (float*)y_out, info, s);
+  return lob_run<double>(g, (const double*)X0, ldx0, k, kmax, o, (double*)X_out, theta_out, resid_out,
+                         (double*)y_out, info, s);
+}

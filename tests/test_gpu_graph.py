@@ -1,0 +1,162 @@
+"""GPU parity of the graph (Eq. 2 weights, degree) and the matrix-free operator (Eqs. 1-4,
+Section 4) against the FP64 oracle, through the C-ABI."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import solvers
+from oracle.graph import Graph
+from tests.gpu_helpers import (bf, dev, host, image_case, make_pair, rel_l2, signal_case,
+                               tol_for)
+
+pytestmark = pytest.mark.gpu
+
+OPS = ["W", "L", "DINV_W", "D", "NSYM", "NDIAGL"]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("mode", ["onthefly", "stored_f32"])
+@pytest.mark.parametrize("case", ["1d", "2d", "2d_cross"])
+def test_degree_and_weights(dtype, mode, case):
+    """Eq. 2 weights exported per tap and the degree d_i = sum_j w_ij against the oracle
+    (stored FP32 weights: Eq. 2 rounded to float)."""
+    if case == "1d":
+        _, g = signal_case(1000, 1)
+        r, ss, sr, win = 5, 3.0, 0.1, "square"
+    else:
+        _, g = image_case(45, 77, 2)
+        r, ss, sr, win = (3, 2.0, 0.08, "square") if case == "2d" else (1, 2.0, 0.08, "cross")
+    G = bf().bf_weights(dev(g, dtype), r, ss, sr, window=win, weight_mode=mode)
+    shape = (1, g.size) if g.ndim == 1 else g.shape
+    O = Graph(host(dev(g, dtype)), shape, r, ss, sr, window=win)
+    exact = dtype == torch.float64 and mode == "onthefly"
+    tol = 1e-12 if exact else 2e-6
+    assert rel_l2(host(bf().graph_degree(G)), O.d) < tol
+    taps = host(bf().graph_export_weights(G))
+    assert taps.shape == O.taps.shape
+    np.testing.assert_allclose(taps, O.taps, rtol=tol, atol=1e-30)
+
+
+def test_bf16_weights_are_rounded_oracle_weights():
+    """Stored BF16 weights: each equals the FP64 weight to BF16 rounding (2^-8 relative)."""
+    _, g = image_case(40, 50, 3)
+    G = bf().bf_weights(dev(g), 3, 2.0, 0.08, weight_mode="stored_bf16")
+    O = Graph(g.astype(np.float64), g.shape, 3, 2.0, 0.08)
+    taps = host(bf().graph_export_weights(G))
+    np.testing.assert_allclose(taps, O.taps, rtol=2 ** -8, atol=1e-30)
+    # and the degree is the exact sum of the stored weights
+    Ob = Graph.from_taps(taps, g.shape, 3)
+    assert rel_l2(host(bf().graph_degree(G)), Ob.d) < 1e-6
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("mode", ["onthefly", "stored_f32", "stored_bf16"])
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("k", [1, 3, 4, 16])
+def test_apply_2d(dtype, mode, op, k):
+    if mode == "stored_bf16" and dtype == torch.float64:
+        pytest.skip("bf16 weights need the float path")
+    _, g = image_case(45, 70, 4)       # ragged against 32 x 8 tiles
+    G, O = make_pair(g, 3, 2.0, 0.08, mode=mode, dtype=dtype)
+    X = np.random.default_rng(k).standard_normal((g.size, k))
+    if k > 1:
+        X[:, 0] = g.reshape(-1)          # a smooth column too
+    Xd = dev(X, dtype)
+    Y = host(bf().bf_apply(G, op, Xd))
+    ref = O.apply(op, host(Xd))
+    assert rel_l2(Y, ref) < tol_for(dtype), (op, k, rel_l2(Y, ref))
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("k", [1, 2, 4, 32])
+def test_apply_1d(dtype, op, k):
+    _, g = signal_case(1531, 5)         # ragged against 256-sample tiles
+    G, O = make_pair(g, 5, 3.0, 0.1, dtype=dtype)
+    X = np.random.default_rng(k).standard_normal((g.size, k))
+    Xd = dev(X, dtype)
+    Y = host(bf().bf_apply(G, op, Xd))
+    assert rel_l2(Y, O.apply(op, host(Xd))) < tol_for(dtype)
+
+
+@pytest.mark.parametrize("shape,radius", [((1, 1), 1), ((1, 9), 3), ((9, 1), 3), ((3, 3), 7),
+                                          ((2, 300), 2), ((33, 9), 1)])
+def test_apply_small_and_degenerate_images(shape, radius):
+    """Images smaller than a tile, one pixel wide or tall, radius beyond the image."""
+    g = np.random.default_rng(7).uniform(size=shape).astype(np.float32)
+    G, O = make_pair(g, radius, 1.5, 0.2)
+    X = np.random.default_rng(8).standard_normal((g.size, 4))
+    Xd = dev(X)
+    for op in OPS:
+        Y = host(bf().bf_apply(G, op, Xd))
+        ref = O.apply(op, host(Xd))
+        if np.linalg.norm(ref) == 0:
+            assert np.abs(Y).max() < 1e-6
+        else:
+            assert rel_l2(Y, ref) < 1e-5, op
+
+
+def test_apply_strided_block_and_dots():
+    """ld > k (a column slice of a wider block) and the fused column dot products."""
+    _, g = image_case(37, 41, 6)
+    G, O = make_pair(g, 2, 2.0, 0.1)
+    big = dev(np.random.default_rng(9).standard_normal((g.size, 12)))
+    Xv = big[:, 2:9]                     # k = 7, ld = 12, offset 2
+    Y, d = bf().bf_apply(G, "L", Xv, dots=True)
+    Xh = host(Xv)
+    ref = O.apply("L", Xh)
+    assert rel_l2(host(Y), ref) < 1e-5
+    np.testing.assert_allclose(host(d), np.sum(Xh * ref, axis=0), rtol=1e-5)
+
+
+def test_apply_rejects_bad_arguments():
+    _, g = image_case(16, 16, 1)
+    G, _ = make_pair(g, 1, 1.0, 0.1)
+    X = dev(np.ones((g.size, 2)))
+    with pytest.raises(bf().BFError) as e:
+        bf().bf_apply(G, "L", X, Y=X)    # in place
+    assert e.value.code == bf().BF_EINVAL
+
+
+def test_nonfinite_guide_is_reported():
+    g = np.ones((8, 8), np.float32)
+    g[3, 4] = np.nan
+    with pytest.raises(bf().BFError) as e:
+        bf().bf_weights(dev(g), 1, 1.0, 0.1)
+    assert e.value.code == bf().BF_ENONFINITE
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 7])
+def test_simple_filter(iters):
+    """x <- D^-1 W x repeated (Section 4); also in place."""
+    _, g = image_case(30, 47, 10)
+    G, O = make_pair(g, 3, 2.0, 0.08)
+    x = dev(g.reshape(-1))
+    y = bf().bf_simple_filter(G, x, iters)
+    ref = solvers.simple_iteration(O, host(x), iters)
+    assert rel_l2(host(y), ref) < 1e-5
+    xin = x.clone()
+    bf().bf_simple_filter(G, xin, iters, out=xin)
+    assert rel_l2(host(xin), ref) < 1e-5
+
+
+def test_full_size_image_apply_sampled():
+    """The 512 x 512, 7 x 7 window operator at k = 16 (the block width LOBPCG uses on this
+    image), checked on sampled rows computed one by one from the oracle's definition."""
+    _, g = image_case(512, 512, 2)
+    G = bf().bf_weights(dev(g), 3, 2.0, 0.08)
+    X = np.random.default_rng(0).standard_normal((g.size, 16)).astype(np.float32)
+    Y = host(bf().bf_apply(G, "L", dev(X)))
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([rng.integers(0, g.size, 200), [0, 511, g.size - 1, g.size - 512]])
+    gg = g.astype(np.float64)
+    for i in rows:
+        y, x = divmod(int(i), 512)
+        acc = np.zeros(16)
+        for dy in range(-3, 4):
+            for dx in range(-3, 4):
+                yy, xx = y + dy, x + dx
+                if (dy or dx) and 0 <= yy < 512 and 0 <= xx < 512:
+                    w = np.exp(-(dx * dx + dy * dy) / 8.0) * np.exp(-(gg[y, x] - gg[yy, xx]) ** 2 / (2 * 0.08 ** 2))
+                    acc += w * (X[i].astype(np.float64) - X[yy * 512 + xx].astype(np.float64))
+        assert rel_l2(Y[i], acc) < 1e-5

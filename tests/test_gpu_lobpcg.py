@@ -1,0 +1,111 @@
+"""GPU parity of the block LOBPCG filter (Algorithm 3, Section 6) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import solvers, spectral
+from paper_1509_02468_gb300 import synth
+from tests.gpu_helpers import TOL_RITZ, bf, dev, host, image_case, make_pair, rel_l2, signal_case
+
+pytestmark = pytest.mark.gpu
+
+
+def ritz_ok(theta, ref, tol=TOL_RITZ):
+    theta = np.asarray(theta)
+    ref = np.asarray(ref)
+    floor = 1e-3 * np.abs(ref).max()
+    err = np.abs(theta - ref) / np.maximum(np.abs(ref), floor)
+    return float(err.max())
+
+
+def subspace_gap(X, Y, b):
+    """sin of the largest principal angle between span X and span Y (B inner product)."""
+    def borth(V):
+        G = V.T @ (b[:, None] * V)
+        R = np.linalg.cholesky(0.5 * (G + G.T))
+        return np.linalg.solve(R, V.T).T
+    Qx, Qy = borth(X), borth(Y)
+    s = np.linalg.svd(Qx.T @ (b[:, None] * Qy), compute_uv=False)
+    return float(np.sqrt(max(0.0, 1.0 - s.min() ** 2)))
+
+
+def run_pair(g, radius, ss, sr, k, kmax, dtype=torch.float32, seed=0, **kw):
+    G, O = make_pair(g, radius, ss, sr, dtype=dtype)
+    X0 = synth.block_start(g.reshape(-1), k, seed=seed, dtype=np.float64)
+    X0d = dev(X0, dtype)
+    out = bf().lobpcg_filter(G, X0d, kmax, theta_hist=True, **kw)
+    okw = {"pencil": kw.get("pencil", "D"), "precond": kw.get("precond", "jacobi"),
+           "constrain": kw.get("constrain", False), "tol": kw.get("tol", 0.0)}
+    ref = solvers.lobpcg(O, host(X0d), kmax, **okw)
+    return out, ref, O
+
+
+def test_lobpcg_signal_1d_n4096_fp64():
+    """1D signal n = 4096, FP64, k = 4, 10 iterations (Ritz values and filtered signal)."""
+    w = synth.SIGNAL_1D_4096
+    _, g = synth.make_input(w)
+    out, ref, O = run_pair(g, w.radius, w.sigma_s, w.sigma_r, w.lobpcg_k, w.lobpcg_iters,
+                           dtype=torch.float64)
+    assert out["info"].iters == ref["iters"] == 10
+    assert ritz_ok(host(out["theta"]), ref["theta"]) < 1e-9
+    assert rel_l2(host(out["y"]), ref["y"]) < 1e-9
+    np.testing.assert_allclose(host(out["resid"]), ref["resid"], rtol=1e-6)
+
+
+@pytest.mark.parametrize("k,constrain", [(1, False), (4, False), (4, True), (3, True), (8, False)])
+def test_lobpcg_small_image_fp32(k, constrain):
+    _, g = image_case(48, 53, 13)
+    out, ref, O = run_pair(g, 2, 2.0, 0.08, k, 12, constrain=constrain)
+    e = ritz_ok(host(out["theta"]), ref["theta"])
+    assert e < TOL_RITZ, e
+    th = host(out["theta_hist"])
+    np.testing.assert_allclose(th[-1], host(out["theta"]))
+    assert rel_l2(host(out["y"]), ref["y"]) < 1e-4
+    assert subspace_gap(host(out["X"]), ref["X"], O.d) < 1e-3
+
+
+def test_lobpcg_image_512_k16_fp32():
+    """512 x 512 image, k = 16, 30 iterations, FP32 blocks with FP64 Rayleigh-Ritz."""
+    w = synth.IMAGE_512
+    _, g = synth.make_input(w)
+    out, ref, O = run_pair(g, w.radius, w.sigma_s, w.sigma_r, w.lobpcg_k, w.lobpcg_iters, seed=w.seed)
+    assert out["info"].iters == 30
+    e = ritz_ok(host(out["theta"]), ref["theta"])
+    assert e < TOL_RITZ, (e, host(out["theta"]), ref["theta"])
+    assert rel_l2(host(out["y"]), ref["y"]) < 1e-4
+
+
+def test_lobpcg_converges_to_dense_eigenvalues_on_gpu():
+    """Tiny image, many iterations: Ritz values equal the dense generalised eigenvalues
+    (Eq. 8 for the pencil (L, D)); X^T D X = I."""
+    _, g = image_case(12, 13, 14, dtype=np.float64)
+    G, O = make_pair(g, 1, 1.0, 1.0, dtype=torch.float64)
+    X0 = dev(synth.block_start(g.reshape(-1), 3, seed=1), torch.float64)
+    out = bf().lobpcg_filter(G, X0, 300, tol=1e-10)
+    lam, _ = spectral.pencil_eig(O, "D")
+    np.testing.assert_allclose(host(out["theta"]), lam[:3], rtol=1e-9, atol=1e-13)
+    X = host(out["X"])
+    np.testing.assert_allclose(X.T @ (O.d[:, None] * X), np.eye(3), atol=1e-9)
+    assert out["info"].status == "converged"
+
+
+def test_lobpcg_identity_pencil_and_precond():
+    _, g = signal_case(600, 4, dtype=np.float32)
+    out, ref, O = run_pair(g, 3, 2.0, 0.1, 4, 15, pencil="I", precond="identity")
+    assert ritz_ok(host(out["theta"]), ref["theta"]) < TOL_RITZ
+
+
+def test_lobpcg_tolerance_stop():
+    _, g = image_case(20, 24, 15, dtype=np.float64)
+    out, ref, O = run_pair(g, 1, 1.0, 1.0, 2, 300, dtype=torch.float64, tol=1e-8)
+    assert ref["status"] == "converged"
+    assert out["info"].status == "converged"
+    assert abs(out["info"].iters - ref["iters"]) <= 1
+    assert host(out["resid"]).max() <= 1e-8
+
+
+def test_lobpcg_rejects_bad_sizes():
+    _, g = image_case(4, 4, 1)
+    G, _ = make_pair(g, 1, 1.0, 0.1)
+    with pytest.raises(bf().BFError):
+        bf().lobpcg_filter(G, dev(np.ones((16, 6))), 3)    # 3k > n

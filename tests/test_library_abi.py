@@ -1,0 +1,47 @@
+"""The C-ABI library builds, loads and exports every function include/*.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names - {"if", "while", "for", "return", "sizeof"}
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["bf_weights", "bf_apply", "cg_filter", "lobpcg_filter", "bf_graph_free",
+              "bf_last_error", "bf_simple_filter"]:
+        assert n in names
+
+
+def test_library_loads_and_exports_declared_symbols():
+    from paper_1509_02468_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.bf_last_error.restype = ctypes.c_char_p
+    assert lib.bf_last_error() == b""
+
+
+def test_argument_validation_needs_no_gpu():
+    """Argument checks return BF_EINVAL before touching the device."""
+    from paper_1509_02468_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.bf_apply.restype = ctypes.c_int
+    assert lib.bf_apply(None, 1, None, 1, 1, None, 1, None, None) == -1
+    lib.bf_weights.restype = ctypes.c_int
+    assert lib.bf_weights(None, None, None, None) == -1
+    lib.cg_filter.restype = ctypes.c_int
+    assert lib.cg_filter(None, None, 3, None, None, None, None) == -1
