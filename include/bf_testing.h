@@ -1,0 +1,33 @@
+/*
+ * bf_testing.h -- extra entry point of libbf.so that exposes one internal step of
+ * lobpcg_filter for direct testing (see bf.h for the conventions).
+ */
+#ifndef BF_TESTING_H_
+#define BF_TESTING_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The Rayleigh-Ritz step of LOBPCG (Algorithm 3, Section 6: "use the Rayleigh-Ritz method
+ * for the pencil L - lambda D on the trial subspace"), on the GPU in FP64, one CTA.
+ * G (device, 2*m*m doubles): G_A = S^T L S then G_B = S^T B S, row-major, symmetric up
+ * to rounding, G_B positive definite.  Finds the k smallest eigenpairs of
+ * G_A c = theta G_B c:  C (device, m*k doubles, row-major [m][k]) with C^T G_B C = I,
+ * theta (device, k doubles, ascending).  If a squared pivot of the Cholesky factor of the
+ * unit-diagonal-scaled G_B is <= 1e-10 and 0 < m_nop < m, the problem is solved again on
+ * the leading m_nop x m_nop blocks (rows m_nop.. of C are then 0).  Cp (device, m*k
+ * doubles, may be NULL) receives the coefficients of the next search direction P: the
+ * rows of C past the first k, minus C times C^T G_B (those rows), i.e. B-orthogonal to
+ * the Ritz vectors.  flags (device, 2 ints) must hold {0, 0}; on return flags[0] is 2
+ * for a dependent basis that dropping P does not cure, 3 for a non-finite Ritz value,
+ * and flags[1] counts drops of P.  Needs 1 <= k <= m <= 96 and k <= 32.  Asynchronous. */
+int bf_rayleigh_ritz(const double* G, int m, int k, int m_nop, double* C, double* Cp,
+                     double* theta, int* flags, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BF_TESTING_H_ */

@@ -25,6 +25,10 @@ Readings of the text (each listed with its reason in the design notes):
   B-orthogonal projection of x0 on span(X): y = X X^T B x0; with the constraint the
   B-mean e_bar = e^T B x0 / e^T B e is added back: y = e_bar e + X X^T B (x0 - e_bar e).
 * LOBPCG start.  Column 0 of the block is x0; the other columns are given by the caller.
+* LOBPCG search direction.  Algorithm 3 sets p_k+1 = w_k + gamma_k p_k.  For a block the
+  raw P drifts into span X as columns converge and S^T B S becomes ill-conditioned; P is
+  therefore kept B-orthogonal to X after each update (the same trial subspaces, see
+  ``lobpcg``), as in the basis selection of Hetmaniuk and Lehoucq (2006).
 * Rayleigh-Ritz.  The small pencil (S^T A S, S^T B S) is scaled to unit diagonal, reduced
   with the Cholesky factor of the scaled S^T B S, solved as a symmetric eigenproblem and
   sorted ascending.  If that Cholesky factor has a squared pivot <= ``DEP_TOL`` (the
@@ -152,13 +156,20 @@ def rayleigh_ritz(GA, GB, k):
 
 # ---------------------------------------------------------------- Algorithm 3 (block)
 def lobpcg(G, X0, kmax: int, pencil: str = "D", precond="jacobi", constrain: bool = False,
-           tol: float = 0.0, x0=None):
+           tol: float = 0.0, x0=None, p_ortho: bool = True):
     """Block LOBPCG as a low-pass filter (Algorithm 3 with a block of k vectors).
 
     A = L, B = D (pencil "D") or I (pencil "I").  Returns a dict with theta (k Ritz values,
     ascending), X (B-orthonormal Ritz vectors [n][k]), resid (||L x_j - theta_j B x_j|| /
     ||B x_j||), y (the filtered signal), the Ritz values of every iteration, the number of
-    iterations, the number of restarts without P and a status string."""
+    iterations, the number of restarts without P and a status string.
+
+    p_ortho: after every update P is made B-orthogonal to the new X (P -= X X^T B P).
+    A X and A P are recomputed with the operator after every update (not carried as
+    linear combinations), so S^T A S is always consistent with the vectors in S.
+    span{X_t+1, P_t+1} = span{X_t+1, X_t} either way, so every trial subspace -- and hence
+    every Ritz pair -- is the same as with the raw P = [W P] C_WP; only the conditioning of
+    S^T B S changes (raw P drifts into span X as columns converge)."""
     L = G.L
     n = G.n
     bdiag = G.d.copy() if pencil == "D" else np.ones(n)
@@ -225,11 +236,12 @@ def lobpcg(G, X0, kmax: int, pencil: str = "D", precond="jacobi", constrain: boo
         if theta_new is None:
             break
         theta = theta_new
-        Xn = S @ C
-        AXn = AS @ C
+        X = S @ C
         P = S[:, k:] @ C[k:, :]
-        AP = AS[:, k:] @ C[k:, :]
-        X, AX = Xn, AXn
+        if p_ortho:
+            P = P - X @ (X.T @ B(P))
+        AX = np.asarray(L @ X)        # products with A are always fresh operator applies
+        AP = np.asarray(L @ P)
         it += 1
         hist.append(theta.copy())
     R = AX - B(X) * theta[None, :]

@@ -76,6 +76,7 @@ def _load():
         "cg_filter": [vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, ctypes.POINTER(bf_info), vp],
         "lobpcg_filter": [vp, vp, i64, i32, i32, ctypes.POINTER(bf_lobpcg_opts), vp, dp, dp, vp,
                           ctypes.POINTER(bf_info), vp],
+        "bf_rayleigh_ritz": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -254,3 +255,20 @@ def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
     return {"X": X, "theta": theta, "resid": resid, "y": y,
             "theta_hist": th.view(kmax + 1, k) if th is not None else None,
             "info": _info(info) if info is not None else None}
+
+
+def rayleigh_ritz(GA: torch.Tensor, GB: torch.Tensor, k: int, m_nop: int = 0,
+                  want_cp: bool = False, stream=None):
+    """The LOBPCG Rayleigh-Ritz step on the GPU (include/bf_testing.h).  Returns
+    (C, theta, Cp or None, status, restarts)."""
+    m = GA.shape[0]
+    dev = GA.device
+    G = torch.stack([GA, GB]).to(torch.float64).contiguous()
+    C = torch.empty((m, k), dtype=torch.float64, device=dev)
+    Cp = torch.empty((m, k), dtype=torch.float64, device=dev) if want_cp else None
+    theta = torch.empty(k, dtype=torch.float64, device=dev)
+    flags = torch.zeros(2, dtype=torch.int32, device=dev)
+    _check(_lib.bf_rayleigh_ritz(_ptr(G), m, k, m_nop, _ptr(C), _ptr(Cp), _ptr(theta),
+                                 _ptr(flags), _stream(stream)))
+    f = flags.cpu().tolist()
+    return C, theta, Cp, f[0], f[1]

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libbf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["bf_graph.cu", "bf_cg.cu", "bf_lobpcg.cu"]
+SOURCES = ["bf_graph.cu", "bf_cg.cu", "bf_lobpcg.cu", "bf_rr.cu"]
 
 
 def nvcc() -> str:
@@ -39,8 +39,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "bf_internal.cuh"), os.path.join(ROOT, "include", "bf.h"),
-                   os.path.abspath(__file__)]
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + \
+        [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))] + \
+        [os.path.abspath(__file__)]
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):
         return LIB

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "bf_internal.cuh"
+#include "bf_rr.cuh"
 
 int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
@@ -23,11 +24,8 @@ int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k,
                  int64_t ldy, double* dots, cudaStream_t s);
 
 #define LOB_KMAX 32
-#define LOB_MMAX 96
-#define RR_THREADS 512
 #define GRAM_THREADS 512
 #define GRAM_PX 32
-#define DEP_TOL 1e-10
 
 namespace {
 
@@ -310,245 +308,21 @@ __global__ void k_gram_reduce(const double* __restrict__ partials, int nblocks, 
   G[q] = s;
 }
 
-// ------------------------------------------------------------------ Rayleigh-Ritz (FP64)
-// One CTA.  Input G[0] = G_A, G[1] = G_B (m x m).  Scale to unit diagonal of G_B,
-// Cholesky G_B = R R^T (squared pivot <= DEP_TOL: the basis is dependent -- retry on the
-// leading m_nop x m_nop block, i.e. without P, if allowed), M = R^-1 G_A R^-T, cyclic
-// Jacobi with a round-robin (parallel) ordering, sort ascending, C = R^-T V scaled back.
-// Output C [m][k] (rows of dropped columns are 0) and theta into the state.
-struct RRArgs {
-  const double* G;
-  int m, k, m_nop;   // m_nop: size without P (0: no retry)
-  double* C;         // [m][k]
-  LobState* st;
-  double* theta_hist;   // [k] slot for this call, or NULL
-};
-
-__device__ __forceinline__ void jacobi_pair(int step, int i, int mp, int& p, int& q) {
-  // circle method: index mp-1 fixed, the others rotate
-  const int n1 = mp - 1;
-  if (i == 0) {
-    p = step % n1;
-    q = n1;
-  } else {
-    p = (step + i) % n1;
-    q = (step - i + n1) % n1;
-  }
-  if (p > q) { const int t = p; p = q; q = t; }
-}
-
-__global__ void __launch_bounds__(RR_THREADS) k_rr(const RRArgs a) {
-  LobState* st = a.st;
-  if (st->status != LOB_RUN) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int k = a.k;
-  int m = a.m;
-  int mp = m + (m & 1);
-  // layout: M[mp][mp] (A, then the standard form), R[mp][mp] (B, then its factor),
-  // V[mp][mp], then vectors
-  double* M = reinterpret_cast<double*>(smem);
-  double* R = M + LOB_MMAX * LOB_MMAX;
-  double* V = R + LOB_MMAX * LOB_MMAX;
-  double* sc = V + LOB_MMAX * LOB_MMAX;          // [LOB_MMAX] scaling
-  double* tv = sc + LOB_MMAX;                     // [LOB_MMAX] Cholesky column
-  double* cs = tv + LOB_MMAX;                     // [LOB_MMAX / 2] rotation cos
-  double* sn = cs + LOB_MMAX / 2;                 // [LOB_MMAX / 2] rotation sin
-  int* perm = reinterpret_cast<int*>(sn + LOB_MMAX / 2);   // [LOB_MMAX]
-  __shared__ int fail, nrot, dropped;
-  const int tid = threadIdx.x;
-  const int LD = LOB_MMAX;
-  if (tid == 0) dropped = 0;
-
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    __syncthreads();
-    mp = m + (m & 1);
-    // load + symmetrise
-    for (int q = tid; q < mp * mp; q += RR_THREADS) {
-      const int r = q / mp, c = q - r * mp;
-      double va = 0.0, vb = 0.0;
-      if (r < m && c < m) {
-        va = 0.5 * (a.G[r * a.m + c] + a.G[c * a.m + r]);
-        vb = 0.5 * (a.G[a.m * a.m + r * a.m + c] + a.G[a.m * a.m + c * a.m + r]);
-      }
-      M[r * LD + c] = va;
-      R[r * LD + c] = vb;
-    }
-    if (tid == 0) fail = 0;
-    __syncthreads();
-    for (int r = tid; r < m; r += RR_THREADS) {
-      const double dg = R[r * LD + r];
-      if (!(dg > 0.0) || !isfinite(dg)) fail = 1;
-      sc[r] = (dg > 0.0) ? 1.0 / sqrt(dg) : 0.0;
-    }
-    __syncthreads();
-    if (!fail) {
-      for (int q = tid; q < m * m; q += RR_THREADS) {
-        const int r = q / m, c = q - r * m;
-        M[r * LD + c] *= sc[r] * sc[c];
-        R[r * LD + c] *= sc[r] * sc[c];
-      }
-      __syncthreads();
-      // left-looking Cholesky, lower factor stored in R (strict upper part left as is)
-      for (int j = 0; j < m && !fail; ++j) {
-        for (int i = j + tid; i < m; i += RR_THREADS) {
-          double s = R[i * LD + j];
-          for (int p = 0; p < j; ++p) s -= R[i * LD + p] * R[j * LD + p];
-          tv[i] = s;
-        }
-        __syncthreads();
-        if (tid == 0) {
-          if (!(tv[j] > DEP_TOL)) fail = 1;
-          else tv[j] = sqrt(tv[j]);
-        }
-        __syncthreads();
-        if (!fail)
-          for (int i = j + tid; i < m; i += RR_THREADS) R[i * LD + j] = (i == j) ? tv[j] : tv[i] / tv[j];
-        __syncthreads();
-      }
-    }
-    __syncthreads();
-    if (!fail) break;
-    if (attempt == 0 && a.m_nop > 0 && a.m_nop < a.m) {
-      m = a.m_nop;
-      if (tid == 0) dropped = 1;
-      continue;
-    }
-    if (tid == 0) st->status = LOB_BREAK;
-    return;
-  }
-  // standard form: V := R^-1 M (column-wise forward substitution), then M := R^-1 V^T
-  for (int c = tid; c < m; c += RR_THREADS) {
-    for (int i = 0; i < m; ++i) {
-      double s = M[i * LD + c];
-      for (int p = 0; p < i; ++p) s -= R[i * LD + p] * V[p * LD + c];
-      V[i * LD + c] = s / R[i * LD + i];
-    }
-  }
-  __syncthreads();
-  for (int c = tid; c < m; c += RR_THREADS) {
-    for (int i = 0; i < m; ++i) {
-      double s = V[c * LD + i];
-      for (int p = 0; p < i; ++p) s -= R[i * LD + p] * M[p * LD + c];
-      M[i * LD + c] = s / R[i * LD + i];
-    }
-  }
-  __syncthreads();
-  // symmetrise (upper from lower), pad, V = I
-  for (int q = tid; q < mp * mp; q += RR_THREADS) {
-    const int r = q / mp, c = q - r * mp;
-    if (r < m && c < m && r < c) {
-      const double v = 0.5 * (M[r * LD + c] + M[c * LD + r]);
-      M[r * LD + c] = v;
-      M[c * LD + r] = v;
-    }
-    if (r >= m || c >= m) M[r * LD + c] = (r == c) ? 1e300 : 0.0;
-    V[r * LD + c] = (r == c) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  // parallel cyclic Jacobi
-  const int npair = mp / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) nrot = 0;
-    __syncthreads();
-    for (int step = 0; step < mp - 1; ++step) {
-      for (int i = tid; i < npair; i += RR_THREADS) {
-        int p, q;
-        jacobi_pair(step, i, mp, p, q);
-        const double apq = M[p * LD + q];
-        const double app = M[p * LD + p], aqq = M[q * LD + q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t = (fabs(tau) > 1e150) ? 0.5 / tau
-                                                 : ((tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                                                 : -1.0 / (-tau + sqrt(1.0 + tau * tau)));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
-          atomicAdd(&nrot, 1);
-        }
-        cs[i] = c;
-        sn[i] = s;
-      }
-      __syncthreads();
-      // rows: M <- J^T M
-      for (int q2 = tid; q2 < npair * mp; q2 += RR_THREADS) {
-        const int i = q2 / mp, j = q2 - i * mp;
-        if (sn[i] == 0.0) continue;
-        int p, q;
-        jacobi_pair(step, i, mp, p, q);
-        const double x = M[p * LD + j], y = M[q * LD + j];
-        M[p * LD + j] = cs[i] * x - sn[i] * y;
-        M[q * LD + j] = sn[i] * x + cs[i] * y;
-      }
-      __syncthreads();
-      // columns: M <- M J, V <- V J
-      for (int q2 = tid; q2 < npair * mp; q2 += RR_THREADS) {
-        const int i = q2 / mp, r = q2 - i * mp;
-        if (sn[i] == 0.0) continue;
-        int p, q;
-        jacobi_pair(step, i, mp, p, q);
-        const double x = M[r * LD + p], y = M[r * LD + q];
-        M[r * LD + p] = cs[i] * x - sn[i] * y;
-        M[r * LD + q] = sn[i] * x + cs[i] * y;
-        const double vx = V[r * LD + p], vy = V[r * LD + q];
-        V[r * LD + p] = cs[i] * vx - sn[i] * vy;
-        V[r * LD + q] = sn[i] * vx + cs[i] * vy;
-      }
-      __syncthreads();
-    }
-    if (nrot == 0) break;
-    __syncthreads();
-  }
-  // ascending order (ties by index)
-  for (int i = tid; i < mp; i += RR_THREADS) {
-    const double li = M[i * LD + i];
-    int rank = 0;
-    for (int j = 0; j < mp; ++j) {
-      const double lj = M[j * LD + j];
-      rank += (lj < li) || (lj == li && j < i);
-    }
-    perm[rank] = i;
-  }
-  __syncthreads();
-  // C = R^-T V[:, perm[0..k)], then undo the scaling; rows past m (dropped P) are 0
-  for (int j = tid; j < k; j += RR_THREADS) {
-    const int col = perm[j];
-    for (int i = m - 1; i >= 0; --i) {
-      double s = V[i * LD + col];
-      for (int p = i + 1; p < m; ++p) s -= R[p * LD + i] * a.C[p * k + j];
-      a.C[i * k + j] = s / R[i * LD + i];
-    }
-  }
-  __syncthreads();
-  for (int q = tid; q < a.m * k; q += RR_THREADS) {
-    const int r = q / k;
-    a.C[q] = (r < m) ? a.C[q] * sc[r] : 0.0;
-  }
-  if (tid < k) {
-    const double th = M[perm[tid] * LD + perm[tid]];
-    st->theta[tid] = th;
-    if (a.theta_hist) a.theta_hist[tid] = th;
-    if (!isfinite(th)) st->status = LOB_NONFINITE;
-  }
-  if (tid == 0 && dropped) st->restarts += 1;
-}
-
 // ------------------------------------------------------------------ update
 // For a tile of pixels and a group of CW columns per thread:
-//   X' = S C[:, cols];  P' = [W P] C[k:, cols] and AP' = [AW AP] C[k:, cols] (nblk >= 2).
-// A X' is not formed here: it is recomputed as L X' by the operator kernel, because the
-// combination [AX AW AP] C cancels heavily once X is nearly converged (AX ~ theta B X is
-// small next to AW C_W), which costs FP32 accuracy.
+//   X' = S C[:, cols]  and  P' = S Cp[:, cols]  (Cp: the next P, B-orthogonal to X').
+// A X' and A P' are not formed here: they are recomputed by the operator kernel, which
+// keeps S^T A S consistent with S (linear combinations of [AX AW AP] cancel heavily once
+// X is nearly converged).
 template <typename T>
 struct UpdArgs {
   const T* S[3];
-  const T* AS[3];
   int nblk, k, m;
   int64_t n;
   const double* C;       // [m][k]
+  const double* Cp;      // [m][k] or NULL
   T* Xn;
-  T* Pn;                 // NULL when nblk == 1
-  T* APn;
+  T* Pn;                 // NULL when Cp is NULL
   const LobState* st;
 };
 
@@ -559,12 +333,15 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
   const int k = a.k, m = a.m;
   const int ngrp = k / CW;
   const int pt = 256 / ngrp;                  // pixels per pass
-  T* sC = reinterpret_cast<T*>(smem);         // [m][k]
-  T* sS = sC + m * k;                         // [pt][m]
-  T* sA = sS + pt * m;                        // [pt][m]  (AS rows of W and P only)
-  for (int q = threadIdx.x; q < m * k; q += 256) sC[q] = (T)a.C[q];
-  const int p_loc = threadIdx.x / ngrp, g = threadIdx.x - p_loc * ngrp;
   const bool with_p = a.Pn != nullptr;
+  T* sC = reinterpret_cast<T*>(smem);         // [m][k]
+  T* sCp = sC + m * k;                        // [m][k]
+  T* sS = sCp + m * k;                        // [pt][m]
+  for (int q = threadIdx.x; q < m * k; q += 256) {
+    sC[q] = (T)a.C[q];
+    sCp[q] = with_p ? (T)a.Cp[q] : T(0);
+  }
+  const int p_loc = threadIdx.x / ngrp, g = threadIdx.x - p_loc * ngrp;
   const int64_t npass = (a.n + pt - 1) / pt;
   for (int64_t ps = blockIdx.x; ps < npass; ps += gridDim.x) {
     const int64_t i0 = ps * pt;
@@ -572,43 +349,32 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
     for (int q = threadIdx.x; q < pt * m; q += 256) {
       const int p = q / m, col = q - p * m;
       const int64_t i = i0 + p;
-      T vs = T(0), va = T(0);
+      T vs = T(0);
       if (i < a.n) {
         const int blk = col / k, c = col - blk * k;
         vs = a.S[blk][i * k + c];
-        if (with_p && blk > 0) va = a.AS[blk][i * k + c];
       }
       sS[q] = vs;
-      sA[q] = va;
     }
     __syncthreads();
     const int64_t i = i0 + p_loc;
     if (p_loc < pt && i < a.n) {
-      T x[CW], pp[CW], ap[CW];
+      T x[CW], pp[CW];
 #pragma unroll
-      for (int e = 0; e < CW; ++e) x[e] = pp[e] = ap[e] = T(0);
-      for (int r = 0; r < k; ++r) {
+      for (int e = 0; e < CW; ++e) x[e] = pp[e] = T(0);
+      for (int r = 0; r < m; ++r) {
         const T s = sS[p_loc * m + r];
 #pragma unroll
-        for (int e = 0; e < CW; ++e) x[e] = fma(s, sC[r * k + g * CW + e], x[e]);
-      }
-      for (int r = k; r < m; ++r) {
-        const T s = sS[p_loc * m + r], as = sA[p_loc * m + r];
-#pragma unroll
         for (int e = 0; e < CW; ++e) {
-          const T c = sC[r * k + g * CW + e];
-          pp[e] = fma(s, c, pp[e]);
-          ap[e] = fma(as, c, ap[e]);
+          x[e] = fma(s, sC[r * k + g * CW + e], x[e]);
+          if (with_p) pp[e] = fma(s, sCp[r * k + g * CW + e], pp[e]);
         }
       }
 #pragma unroll
       for (int e = 0; e < CW; ++e) {
         const int c = g * CW + e;
-        a.Xn[i * k + c] = x[e] + pp[e];
-        if (with_p) {
-          a.Pn[i * k + c] = pp[e];
-          a.APn[i * k + c] = ap[e];
-        }
+        a.Xn[i * k + c] = x[e];
+        if (with_p) a.Pn[i * k + c] = pp[e];
       }
     }
   }
@@ -757,6 +523,7 @@ struct LobBuffers {
   double* gram_part;
   double* G;
   double* C;
+  double* Cp;
   double* part;       // small reductions
   double* ysums;
   LobState* st;
@@ -805,7 +572,7 @@ template <typename T, int CW>
 static void launch_update_cw(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
   const int ngrp = ua.k / CW;
   const int pt = 256 / ngrp;
-  const size_t sm = (size_t)(ua.m * ua.k + 2 * pt * ua.m) * sizeof(T);
+  const size_t sm = (size_t)(2 * ua.m * ua.k + pt * ua.m) * sizeof(T);
   static bool init = false;
   if (!init) {
     cudaFuncSetAttribute(k_update<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -834,18 +601,6 @@ static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T
   return BF_OK;
 }
 
-static int run_rr(const RRArgs& ra, cudaStream_t s) {
-  static bool init = false;
-  const size_t sm = (size_t)(3 * LOB_MMAX * LOB_MMAX + 3 * LOB_MMAX) * sizeof(double) + LOB_MMAX * sizeof(int);
-  if (!init) {
-    cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    init = true;
-  }
-  BF_LAUNCH(k_rr<<<1, RR_THREADS, sm, s>>>(ra));
-  BF_CUDA(cudaGetLastError());
-  return BF_OK;
-}
-
 template <typename T>
 int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
             const bf_lobpcg_opts& o, T* X_out, double* theta_out, double* resid_out, T* y_out,
@@ -863,7 +618,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   const size_t cb = (((size_t)m3 * k * sizeof(double)) + 255) & ~(size_t)255;
   const size_t pb = (((size_t)std::max(ugrid, rgrid) * (3 * LOB_KMAX + 2) * sizeof(double)) + 255) & ~(size_t)255;
   const size_t yb = 256 * sizeof(double) * 2;
-  const size_t total = 11 * blk + gpb + gb + cb + pb + yb + 1024;
+  const size_t total = 11 * blk + gpb + gb + 2 * cb + pb + yb + 1024;
   int rc = bf_ws_reserve(gm, total);
   if (rc) return rc;
   char* w = (char*)gm->ws;
@@ -879,6 +634,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   B.gram_part = (double*)w; w += gpb;
   B.G = (double*)w; w += gb;
   B.C = (double*)w; w += cb;
+  B.Cp = (double*)w; w += cb;
   B.part = (double*)w; w += pb;
   B.ysums = (double*)w; w += yb;
   B.st = (LobState*)w; w += 1024;
@@ -894,7 +650,6 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   const int egrid = (int)std::min<int64_t>((n * k + 255) / 256, 4 * nsm);
   // ---- start block: copy, constrain, A X
   BF_LAUNCH(k_copy_block<T><<<egrid, 256, 0, s>>>(X0, ldx0, k, n, B.X[1]));
-  BF_CUDA(cudaGetLastError());
   BF_LAUNCH(k_bsums<T><<<rgrid, 256, 0, s>>>(B.X[1], k, n, bdiag, B.part, B.st));
   if (o.constrain_e) BF_LAUNCH(k_project<T><<<egrid, 256, 0, s>>>(B.X[1], k, n, B.st));
   BF_CUDA(cudaGetLastError());
@@ -917,29 +672,31 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   if (rc) return rc;
   const int rthreads = 256;
   BF_LAUNCH(k_gram_reduce<<<(2 * k * k + rthreads - 1) / rthreads, rthreads, 0, s>>>(B.gram_part, ggrid, k, ga.m4, B.G, B.st));
-  RRArgs ra;
+  RRParams ra;
   ra.G = B.G;
   ra.C = B.C;
-  ra.st = B.st;
+  ra.Cp = nullptr;
+  ra.theta = B.st->theta;
+  ra.status = &B.st->status;
+  ra.restarts = &B.st->restarts;
   ra.k = k;
   ra.m = k;
   ra.m_nop = 0;
   ra.theta_hist = o.theta_hist;
-  rc = run_rr(ra, s);
+  rc = bf_rr_launch(ra, s);
   if (rc) return rc;
   UpdArgs<T> ua;
   memset(&ua, 0, sizeof(ua));
   ua.k = k;
   ua.n = n;
   ua.C = B.C;
+  ua.Cp = nullptr;
   ua.st = B.st;
   ua.nblk = 1;
   ua.m = k;
   ua.S[0] = B.X[1];
-  ua.AS[0] = B.AX[1];
   ua.Xn = B.X[0];
   ua.Pn = nullptr;
-  ua.APn = nullptr;
   rc = run_update<T>(ua, ugrid, s);
   if (rc) return rc;
   rc = run_resid<T>(g, B.X[0], B.AX[0], k, B.W[0], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s);
@@ -967,19 +724,19 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
     BF_LAUNCH(k_gram_reduce<<<(2 * ga.m * ga.m + rthreads - 1) / rthreads, rthreads, 0, s>>>(B.gram_part, ggrid, ga.m, ga.m4, B.G, B.st));
     ra.m = ga.m;
     ra.m_nop = (nblk == 3) ? 2 * k : 0;
+    ra.Cp = B.Cp;
     ra.theta_hist = o.theta_hist ? o.theta_hist + (size_t)(it + 1) * k : nullptr;
-    rc = run_rr(ra, s);
+    rc = bf_rr_launch(ra, s);
     if (rc) return rc;
     ua.nblk = nblk;
     ua.m = ga.m;
-    for (int b2 = 0; b2 < 3; ++b2) {
-      ua.S[b2] = ga.S[b2];
-      ua.AS[b2] = ga.AS[b2];
-    }
+    for (int b2 = 0; b2 < 3; ++b2) ua.S[b2] = ga.S[b2];
+    ua.Cp = B.Cp;
     ua.Xn = B.X[nj];
     ua.Pn = B.P[nj];
-    ua.APn = B.AP[nj];
     rc = run_update<T>(ua, ugrid, s);
+    if (rc) return rc;
+    rc = apply_T<T>(g, BF_OP_L, B.P[nj], k, k, B.AP[nj], k, s);
     if (rc) return rc;
     rc = run_resid<T>(g, B.X[nj], B.AX[nj], k, B.W[nj], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s);
     if (rc) return rc;

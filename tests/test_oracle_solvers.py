@@ -237,3 +237,14 @@ def test_filters_denoise_polygon_image():
     p0 = synth.psnr(clean.reshape(-1), x0)
     xcg = solvers.cg(G, x0, 20)["x"]
     assert synth.psnr(clean.reshape(-1), xcg) > p0 + 0.5
+
+
+def test_lobpcg_orthogonal_p_spans_the_same_subspaces():
+    """span{X_t+1, P_t+1} = span{X_t+1, X_t}: keeping P B-orthogonal to X changes no Ritz
+    pair (raw P = [W P] C_WP as in Algorithm 3 gives the same trajectory)."""
+    G, x0 = _graph_2d(ny=14, nx=15, seed=16)
+    X0 = synth.block_start(x0, 3, seed=16)
+    a = solvers.lobpcg(G, X0, 25, p_ortho=True)
+    b = solvers.lobpcg(G, X0, 25, p_ortho=False)
+    np.testing.assert_allclose(a["theta_hist"], b["theta_hist"], rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(a["y"], b["y"], rtol=1e-8, atol=1e-10)
