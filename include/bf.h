@@ -175,6 +175,23 @@ int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, int k, int km
                   const bf_lobpcg_opts* opts, void* X_out, double* theta_out,
                   double* resid_out, void* y_out, bf_info* info, void* stream);
 
+/* cg_filter without any device allocation (the paper has no counterpart: this is a
+ * deployment variant).  cg_filter keeps its vectors in the graph's workspace, which grows
+ * with cudaMalloc -- and cudaFree, which synchronises the whole device -- when a larger
+ * problem arrives.  Callers that must not allocate device memory once they are running
+ * (a fixed memory budget owned by another allocator, a loop that cannot take the implicit
+ * device synchronisation) call this instead: same arguments, same kernels and results,
+ * but the scratch lives in a static device array of the library, about 12.6 MB, which
+ * every GPU that loads the library holds until the process exits.  Limits: n <= 262144
+ * samples and at most 65536 operator tiles; larger problems return BF_EINVAL.  The
+ * caller still provides the graph (built beforehand with bf_weights), x0 and x_out.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  Every call
+ * shares the one array, so calls whose GPU work overlaps (other streams, other host
+ * threads) race and must be serialised by the caller. */
+int cg_filter_noalloc(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
+                      void* x_out, bf_info* info, void* stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char* bf_last_error(void);
 

@@ -77,6 +77,7 @@ def _load():
         "lobpcg_filter": [vp, vp, i64, i32, i32, ctypes.POINTER(bf_lobpcg_opts), vp, dp, dp, vp,
                           ctypes.POINTER(bf_info), vp],
         "bf_rayleigh_ritz": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
+        "cg_filter_noalloc": [vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, ctypes.POINTER(bf_info), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -230,6 +231,20 @@ def cg_filter(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jacobi",
     _check(_lib.cg_filter(g.handle, _ptr(x0), kmax, ctypes.byref(o), _ptr(out),
                           ctypes.byref(info) if info is not None else None, _stream(stream)))
     return out, (_info(info) if info is not None else None), h
+
+
+def cg_filter_noalloc(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jacobi",
+                      beta: str = "flexible", shift: float = 0.0, tol: float = 0.0,
+                      out=None, sync: bool = True, stream=None):
+    """cg_filter with its scratch in the library's static device array (no allocation by
+    the library; n <= 262144).  Returns (x, info)."""
+    out = torch.empty_like(x0) if out is None else out
+    o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS[beta], shift=shift, tol=tol, hist=None)
+    info = bf_info() if sync else None
+    _check(_lib.cg_filter_noalloc(g.handle, _ptr(x0), kmax, ctypes.byref(o), _ptr(out),
+                                  ctypes.byref(info) if info is not None else None,
+                                  _stream(stream)))
+    return out, (_info(info) if info is not None else None)
 
 
 def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "bf_internal.cuh"
 
@@ -301,4 +302,133 @@ extern "C" int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_c
   cudaStream_t s = (cudaStream_t)stream;
   if (g->esize == 4) return cg_run<float>(g, (const float*)x0, kmax, o, (float*)x_out, info, s);
   return cg_run<double>(g, (const double*)x0, kmax, o, (double*)x_out, info, s);
+}
+
+// ==================================================================== allocation-free CG
+// cg_filter keeps its vectors in the graph's workspace, which grows with cudaMalloc (and
+// cudaFree, which synchronises the whole device) the first time a larger problem comes
+// along.  Some callers cannot allow that: code that must not allocate device memory at
+// all once it is running (a fixed memory budget owned by another allocator, a loop that
+// cannot afford the implicit device synchronisation).  cg_filter_noalloc runs the same
+// kernels with their scratch in the file-scope array below instead: five n-vectors, the
+// per-block partial sums and the scalar state.  The array is a fixed part of the library
+// image, so every GPU that loads the library holds it until the process exits.
+#define BF_NOALLOC_MAX_N (1 << 18)              // samples (a 512 x 512 image)
+#define BF_NOALLOC_MAX_BLOCKS (1 << 16)         // operator tiles (partial-sum slots)
+#define BF_NOALLOC_VEC_BYTES ((size_t)BF_NOALLOC_MAX_N * sizeof(double))
+#define BF_NOALLOC_BYTES (5 * BF_NOALLOC_VEC_BYTES + (size_t)BF_NOALLOC_MAX_BLOCKS * 4 * sizeof(double) + 256)
+
+static __device__ __align__(256) unsigned char g_cg_noalloc_scratch[BF_NOALLOC_BYTES];
+
+namespace {
+
+// Device address of the scratch array on the current device, looked up once per device.
+// (In host code the array's name is only a host-side stand-in for the symbol.)
+int noalloc_scratch(unsigned char** out) {
+  static std::mutex mu;
+  static unsigned char* addr[256] = {nullptr};
+  int dev = 0;
+  BF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return bf_fail(BF_EINVAL, "cg_filter_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_cg_noalloc_scratch);
+    if (e != cudaSuccess) return bf_cuda_fail(e, "cudaGetSymbolAddress(g_cg_noalloc_scratch)");
+    addr[dev] = (unsigned char*)p;
+  }
+  *out = addr[dev];
+  return BF_OK;
+}
+
+template <typename T>
+int cg_run_noalloc(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_out,
+                   bf_info* info, cudaStream_t s) {
+  const int64_t n = g->n;
+  const dim3 tg = tile_grid(g);
+  const unsigned nb_tile = tg.x * tg.y;
+  const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 152 * 8);
+  if (n > BF_NOALLOC_MAX_N)
+    return bf_fail(BF_EINVAL, "cg_filter_noalloc: n exceeds the static scratch limit of 262144 samples");
+  if (std::max(nb_tile, nb_elem) > BF_NOALLOC_MAX_BLOCKS)
+    return bf_fail(BF_EINVAL, "cg_filter_noalloc: image shape needs more than 65536 operator tiles");
+  unsigned char* w = nullptr;
+  int rc = noalloc_scratch(&w);
+  if (rc) return rc;
+  CgArgs<T> a;
+  a.r = (T*)(w);
+  a.s = (T*)(w + BF_NOALLOC_VEC_BYTES);
+  a.q = (T*)(w + 2 * BF_NOALLOC_VEC_BYTES);
+  T* pbuf[2] = {(T*)(w + 3 * BF_NOALLOC_VEC_BYTES), (T*)(w + 4 * BF_NOALLOC_VEC_BYTES)};
+  a.partials = (double*)(w + 5 * BF_NOALLOC_VEC_BYTES);
+  a.st = (CgState*)(w + 5 * BF_NOALLOC_VEC_BYTES + (size_t)BF_NOALLOC_MAX_BLOCKS * 4 * sizeof(double));
+  a.x0 = x0;
+  a.x = x_out;
+  a.guide = (const T*)g->guide;
+  a.dinv = o.precond == BF_PRECOND_JACOBI ? (const T*)g->dinv : nullptr;
+  a.wf = g->wf;
+  a.wmode = g->p.weight_mode;
+  a.n = n;
+  a.shift = (T)o.shift;
+  a.hist = o.hist;
+  a.first = 1;
+  a.p_old = pbuf[0];
+  a.p_new = pbuf[1];
+  // The array keeps whatever the previous call left: the state (including the block
+  // counter of the grid reductions, which must start at 0) is written in full here.
+  CgState init;
+  memset(&init, 0, sizeof(init));
+  init.tol2 = o.tol > 0 ? o.tol * o.tol : 0.0;
+  init.beta_mode = o.beta;
+  BF_CUDA(cudaMemcpyAsync(a.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  const bool one_d = (g->ny == 1 && g->ry == 0);
+  const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
+  const size_t sm = hp * 2 * sizeof(T);
+  BF_LAUNCH(k_cg_init<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+  BF_CUDA(cudaGetLastError());
+  for (int it = 0; it < kmax; ++it) {
+    a.first = (it == 0);
+    a.p_old = pbuf[it & 1];
+    a.p_new = pbuf[(it + 1) & 1];
+    BF_LAUNCH(k_cg_dir<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+    BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+  }
+  BF_CUDA(cudaGetLastError());
+  if (info) {
+    CgState h;
+    BF_CUDA(cudaMemcpyAsync(&h, a.st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    info->iters = h.iter;
+    info->status = h.status == CG_CONV ? BF_CG_CONVERGED : (h.status == CG_BREAK ? BF_CG_BREAKDOWN : 0);
+    info->restarts = 0;
+    info->reserved = 0;
+    info->rnorm = sqrt(h.rr);
+    info->ref = sqrt(h.ref2);
+    if (h.status == CG_BREAK) return bf_fail(BF_EBREAKDOWN, "cg_filter_noalloc: p^T q <= 0 (breakdown)");
+    if (h.status == CG_NONFINITE) return bf_fail(BF_ENONFINITE, "cg_filter_noalloc: non-finite scalar");
+  }
+  return BF_OK;
+}
+
+}  // namespace
+
+extern "C" int cg_filter_noalloc(const bf_graph* g, const void* x0, int kmax,
+                                 const bf_cg_opts* opts, void* x_out, bf_info* info,
+                                 void* stream) {
+  if (!g || !x0 || !x_out) return bf_fail(BF_EINVAL, "cg_filter_noalloc: NULL argument");
+  if (kmax < 0) return bf_fail(BF_EINVAL, "cg_filter_noalloc: kmax < 0");
+  bf_cg_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY)
+    return bf_fail(BF_EINVAL, "cg_filter_noalloc: bad precond");
+  if (o.beta != BF_BETA_FLEXIBLE && o.beta != BF_BETA_PRINTED)
+    return bf_fail(BF_EINVAL, "cg_filter_noalloc: bad beta");
+  if (!(o.shift >= 0.0) || !(o.tol >= 0.0))
+    return bf_fail(BF_EINVAL, "cg_filter_noalloc: shift and tol must be >= 0");
+  if ((uintptr_t)x0 % g->esize || (uintptr_t)x_out % g->esize)
+    return bf_fail(BF_EINVAL, "cg_filter_noalloc: misaligned vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->esize == 4) return cg_run_noalloc<float>(g, (const float*)x0, kmax, o, (float*)x_out, info, s);
+  return cg_run_noalloc<double>(g, (const double*)x0, kmax, o, (double*)x_out, info, s);
 }
