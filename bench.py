@@ -3,7 +3,8 @@
 One step = the whole filtering path on one noisy 512 x 512 image (7 x 7 window, sigma_s 2,
 sigma_r 0.08; synthetic polygons over a gradient, noise sigma 0.05): build the graph
 (bf_weights), 50 iterations of the preconditioned CG filter (Algorithm 2) and 30 iterations
-of block LOBPCG with k = 16 (Algorithm 3), all through the C-ABI.  The image is generated
+of block LOBPCG with k = 16 (Algorithm 3), all through the C-ABI; the two filters run on
+two streams at once.  The image is generated
 on the host and resident on the device before the timed region; L2 (126 MB) is flushed by
 writing a 256 MB buffer between timed steps, and each step is timed with CUDA events on
 the launching stream.
@@ -194,10 +195,16 @@ def run_gpu(args):
     x_cg = torch.empty(npix, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
 
+    side = torch.cuda.Stream()
+
     def step():
+        # the two filters read the same graph and run concurrently: CG on a side stream,
+        # LOBPCG (whose one-CTA Rayleigh-Ritz leaves most SMs free) on the main stream
         G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
-        bf.cg_filter(G, guide.view(-1), w["cg_iters"], out=x_cg, sync=False)
+        side.wait_stream(stream)
+        bf.cg_filter(G, guide.view(-1), w["cg_iters"], out=x_cg, sync=False, stream=side)
         out = bf.lobpcg_filter(G, X0, w["lob_iters"], want_X=False, sync=False)
+        stream.wait_stream(side)
         return G, out
 
     keep = []
@@ -270,8 +277,10 @@ def run_gpu(args):
         gd = gh.cuda(non_blocking=True)
         Xd = X0p.cuda(non_blocking=True)
         G = bf.bf_weights(gd, w["radius"], w["sigma_s"], w["sigma_r"])
-        xc, _, _ = bf.cg_filter(G, gd.view(-1), w["cg_iters"], sync=False)
+        side.wait_stream(stream)
+        xc, _, _ = bf.cg_filter(G, gd.view(-1), w["cg_iters"], sync=False, stream=side)
         out = bf.lobpcg_filter(G, Xd, w["lob_iters"], want_X=False, sync=False)
+        stream.wait_stream(side)
         xcg_h.copy_(xc, non_blocking=True)
         y_h.copy_(out["y"], non_blocking=True)
         th_h.copy_(out["theta"], non_blocking=True)
@@ -322,6 +331,37 @@ def run_gpu(args):
     return 0
 
 
+def run_case(args):
+    """Launch one kernel family of the timed step a few times on the benchmark workload, for
+    an ncu capture (no timing, no JSON line): `apply` (k = 16 operator), `cg` (the CG
+    filter), `lobpcg` (one LOBPCG run)."""
+    import numpy as np
+    import torch
+
+    from paper_1509_02468_gb300 import bf, synth
+    w = WORKLOAD
+    side = args.case_side or w["nx"]
+    _, noisy = synth.polygon_image(side, side, w["seed"], noise=w["noise"])
+    guide = torch.as_tensor(noisy).cuda()
+    G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
+    if args.case == "apply":
+        X = torch.randn(noisy.size, 16, device="cuda")
+        Y = torch.empty_like(X)
+        for _ in range(args.steps):
+            bf.bf_apply(G, "L", X, Y=Y)
+    elif args.case == "cg":
+        for _ in range(args.steps):
+            bf.cg_filter(G, guide.view(-1), w["cg_iters"], sync=False)
+    elif args.case == "lobpcg":
+        X0 = torch.as_tensor(synth.block_start(noisy.reshape(-1), w["lob_k"], seed=w["seed"],
+                                               dtype=np.float32)).cuda()
+        for _ in range(args.steps):
+            bf.lobpcg_filter(G, X0, w["lob_iters"], want_X=False, sync=False)
+    torch.cuda.synchronize()
+    print(f"case {args.case} side {side}: {bf.launch_count()} launches")
+    return 0
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--cpu-child":
         _cpu_child(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
@@ -332,7 +372,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--case", choices=["apply", "cg", "lobpcg"], default=None,
+                    help="only launch one kernel family (for profiler captures)")
+    ap.add_argument("--case-side", type=int, default=0, help="image side for --case")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

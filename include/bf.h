@@ -19,8 +19,10 @@
  *    info struct, a status read) is requested: then the call synchronises the stream.
  *  - Return value: BF_OK (0) or a negative BF_E* code; bf_last_error() gives a message
  *    (thread-local, valid until the next call on that thread).
- *  - A bf_graph owns its device buffers and a grow-only workspace; one graph must not
- *    be used by two calls at the same time (host threads or streams).
+ *  - A bf_graph owns its device buffers and grow-only workspaces.  cg_filter,
+ *    lobpcg_filter and bf_simple_filter each keep their own workspace, so calls of
+ *    different families may run at the same time on different streams (they only read
+ *    the graph); two calls of the same family on one graph must not overlap.
  */
 #ifndef BF_H_
 #define BF_H_

@@ -226,9 +226,9 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 152 * 8);
   const unsigned nbmax = std::max(nb_tile, nb_elem);
   const size_t pb = ((size_t)nbmax * 4 * sizeof(double) + 255) & ~(size_t)255;
-  int rc = bf_ws_reserve(gm, 5 * vb + pb + 256);
+  int rc = bf_ws_reserve(gm, BF_WS_CG, 5 * vb + pb + 256);
   if (rc) return rc;
-  char* w = (char*)gm->ws;
+  char* w = (char*)gm->ws[BF_WS_CG];
   CgArgs<T> a;
   a.r = (T*)(w);
   a.s = (T*)(w + vb);

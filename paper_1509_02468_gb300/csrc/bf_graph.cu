@@ -32,17 +32,17 @@ static std::atomic<unsigned long long> g_launches{0};
 void bf_count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 extern "C" uint64_t bf_launch_count(void) { return (uint64_t)g_launches.load(); }
 
-int bf_ws_reserve(bf_graph* g, size_t bytes) {
-  if (bytes <= g->ws_bytes) return BF_OK;
-  if (g->ws) {
+int bf_ws_reserve(bf_graph* g, int slot, size_t bytes) {
+  if (bytes <= g->ws_bytes[slot]) return BF_OK;
+  if (g->ws[slot]) {
     BF_CUDA(cudaDeviceSynchronize());
-    BF_CUDA(cudaFree(g->ws));
-    g->ws = nullptr;
-    g->ws_bytes = 0;
+    BF_CUDA(cudaFree(g->ws[slot]));
+    g->ws[slot] = nullptr;
+    g->ws_bytes[slot] = 0;
   }
   bytes = (bytes + 4095) & ~(size_t)4095;
-  BF_CUDA(cudaMalloc(&g->ws, bytes));
-  g->ws_bytes = bytes;
+  BF_CUDA(cudaMalloc(&g->ws[slot], bytes));
+  g->ws_bytes[slot] = bytes;
   return BF_OK;
 }
 
@@ -433,7 +433,7 @@ extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out,
 
 extern "C" int bf_graph_free(bf_graph* g) {
   if (!g) return BF_OK;
-  void* bufs[] = {g->guide, g->d, g->dinv, g->dis, g->dls, g->wf, g->ws};
+  void* bufs[] = {g->guide, g->d, g->dinv, g->dis, g->dls, g->wf, g->ws[0], g->ws[1], g->ws[2]};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete g;
@@ -501,9 +501,9 @@ extern "C" int bf_simple_filter(const bf_graph* g, const void* x0, int iters, vo
   }
   bf_graph* gm = const_cast<bf_graph*>(g);
   const size_t nba = (nb + 255) & ~(size_t)255;
-  int rc = bf_ws_reserve(gm, 2 * nba);
+  int rc = bf_ws_reserve(gm, BF_WS_SIMPLE, 2 * nba);
   if (rc) return rc;
-  void* tmp[2] = {gm->ws, (char*)gm->ws + nba};
+  void* tmp[2] = {gm->ws[BF_WS_SIMPLE], (char*)gm->ws[BF_WS_SIMPLE] + nba};
   // ping-pong through two temporaries; the last step writes x_out unless it aliases x0
   const void* src = x0;
   for (int it = 0; it < iters; ++it) {

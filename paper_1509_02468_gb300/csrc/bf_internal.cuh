@@ -73,12 +73,17 @@ struct bf_graph {
   void* wf;              // [nfwd][n] forward weights (stored modes) or NULL
   Geom<float> gf;
   Geom<double> gd;
-  void* ws;              // grow-only workspace
-  size_t ws_bytes;
+  void* ws[3];           // grow-only workspaces, one per filter family (BF_WS_*)
+  size_t ws_bytes[3];
 };
 
-// Grow the graph's workspace to at least `bytes` (synchronises the device when it grows).
-int bf_ws_reserve(bf_graph* g, size_t bytes);
+// Workspace slots: CG and LOBPCG keep their own, so one call of each may run at the same
+// time on different streams.
+enum { BF_WS_CG = 0, BF_WS_LOB = 1, BF_WS_SIMPLE = 2 };
+
+// Grow workspace `slot` of the graph to at least `bytes` (synchronises the device when it
+// grows).
+int bf_ws_reserve(bf_graph* g, int slot, size_t bytes);
 
 template <typename T> inline const Geom<T>& geom_of(const bf_graph* g);
 template <> inline const Geom<float>& geom_of<float>(const bf_graph* g) { return g->gf; }

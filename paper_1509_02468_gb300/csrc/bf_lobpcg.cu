@@ -24,8 +24,6 @@ int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k,
                  int64_t ldy, double* dots, cudaStream_t s);
 
 #define LOB_KMAX 32
-#define GRAM_THREADS 512
-#define GRAM_PX 32
 
 namespace {
 
@@ -75,10 +73,14 @@ __device__ bool grid_colsum_last(const double* sh, int nv, double* partials,
   __syncthreads();
   if (!*is_last_sh) return false;
   __threadfence();
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+  // one warp per value: lanes take blocks lane, lane + 32, ... in order, then a
+  // fixed shuffle tree (deterministic)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < nv; j += nw) {
     double s = 0.0;
-    for (unsigned b = 0; b < nb; ++b) s += ((volatile double*)partials)[(size_t)b * nv + j];
-    out[j] = s;
+    for (unsigned b = lane; b < nb; b += 32) s += ((volatile double*)partials)[(size_t)b * nv + j];
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
@@ -170,11 +172,17 @@ __global__ void k_project(T* V, int k, int64_t n, const LobState* st) {
 }
 
 // ------------------------------------------------------------------ Gram partials
-// Block b accumulates, over its pixel chunks, G_A[a][c] = sum_i S[i][a] AS[i][c] and
-// G_B[a][c] = sum_i b_i S[i][a] S[i][c] for a < m and c < m4 (m rounded up to 4).
-// Work item = (a, quad of c); IT items per thread, or NG pixel groups when items are few.
-// Float path: FP32 sums over a chunk of GRAM_PX pixels folded into (hi, lo) pairs by
-// TwoSum; the block result hi + lo is written in FP64.
+// G_A = S^T (A S) and G_B = S^T (B S) for S = [X W P] (m = nblk k columns), split over the
+// pixels: each block accumulates its share and writes one partial, summed in order by
+// k_gram_reduce.  Both matrices are symmetric (L and B are), so only the upper-triangle
+// 4 x 4 tiles (ta <= tb) are formed; k_gram_reduce mirrors them.  A thread owns one tile
+// of both matrices (16 + 16 accumulators, the S values of the tile's rows are shared) and
+// one pixel group of the staged chunk.  Float path: FP32 products summed over runs of 16
+// pixels, then folded by TwoSum into (hi, lo) pairs; groups are combined by a tree of
+// TwoSums, and the block partial hi + lo is written in FP64.
+#define GRAM_T 512
+#define GRAM_PXC 64
+
 template <typename T>
 struct GramArgs {
   const T* S[3];
@@ -182,7 +190,7 @@ struct GramArgs {
   const T* b;        // B diagonal (NULL: I)
   int nblk, k, m, m4;
   int64_t n;
-  double* partials;  // [gridDim.x][2][m][m4]
+  double* partials;  // [gridDim.x][2][m][m] (upper tiles only)
   const LobState* st;
 };
 
@@ -195,117 +203,177 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
 }
 __device__ __forceinline__ void two_sum(double& hi, double& lo, double x) { hi += x; }
 
-template <typename T, int IT>
-__global__ void __launch_bounds__(GRAM_THREADS) k_gram(const GramArgs<T> a) {
+template <typename T>
+__global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
   if (a.st->status != LOB_RUN) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = a.m, m4 = a.m4, k = a.k;
-  T* sS = reinterpret_cast<T*>(smem);            // [GRAM_PX][m4]
-  T* sA = sS + GRAM_PX * m4;                      // [GRAM_PX][m4]
-  T* sb = sA + GRAM_PX * m4;                      // [GRAM_PX]
-  const int items = m * (m4 / 4);
-  const int ng = (IT == 1) ? max(1, GRAM_THREADS / items) : 1;
-  const int grp = (IT == 1) ? (int)threadIdx.x / items : 0;
-  T hA[IT][4], lA[IT][4], hB[IT][4], lB[IT][4];
+  const int ta_n = m4 / 4;
+  const int nt = ta_n * (ta_n + 1) / 2;
+  const int ng = GRAM_T / nt;                         // pixel groups (>= 1)
+  const int grp = threadIdx.x / nt, tile = threadIdx.x - grp * nt;
+  const bool act = grp < ng;
+  // tile -> (ta, tb), ta <= tb, row-major over the upper triangle
+  int ta = 0, tb = 0;
+  {
+    int t = act ? tile : 0, row = 0;
+    while (t >= ta_n - row) { t -= ta_n - row; ++row; }
+    ta = row;
+    tb = row + t;
+  }
+  T* sS = reinterpret_cast<T*>(smem);                 // [GRAM_PXC][m4]
+  T* sA = sS + GRAM_PXC * m4;                         // [GRAM_PXC][m4]
+  T* sb = sA + GRAM_PXC * m4;                         // [GRAM_PXC]
+  T cA[16], cB[16], hA[16], lA[16], hB[16], lB[16];
 #pragma unroll
-  for (int q = 0; q < IT; ++q)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) hA[q][e] = lA[q][e] = hB[q][e] = lB[q][e] = T(0);
-  const int64_t nchunks = (a.n + GRAM_PX - 1) / GRAM_PX;
+  for (int e = 0; e < 16; ++e) cA[e] = cB[e] = hA[e] = lA[e] = hB[e] = lB[e] = T(0);
+  int since_fold = 0;
+  const int fold_every = 16;      // FP32 runs of 16 products (64 cost ~5e-7 in Ritz values on small images)
+  const int64_t nchunks = (a.n + GRAM_PXC - 1) / GRAM_PXC;
+  const bool vec = (k % 4 == 0);
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int64_t i0 = ch * GRAM_PX;
+    const int64_t i0 = ch * GRAM_PXC;
     __syncthreads();
-    for (int q = threadIdx.x; q < GRAM_PX * m4; q += GRAM_THREADS) {
-      const int p = q / m4, col = q - p * m4;
-      const int64_t i = i0 + p;
-      T vs = T(0), va = T(0);
-      if (i < a.n && col < m) {
-        const int blk = col / k, c = col - blk * k;
-        vs = a.S[blk][i * k + c];
-        va = a.AS[blk][i * k + c];
+    if (vec) {
+      const int q4 = m4 / 4;
+      for (int q = threadIdx.x; q < GRAM_PXC * q4; q += GRAM_T) {
+        const int p = q / q4, c4 = q - p * q4;
+        const int64_t i = i0 + p;
+        const int col = c4 * 4, blk = col / k, c = col - blk * k;
+        Vec<T, 4> vs, va;
+        if (i < a.n && col < m) {
+          vs = *reinterpret_cast<const Vec<T, 4>*>(a.S[blk] + i * k + c);
+          va = *reinterpret_cast<const Vec<T, 4>*>(a.AS[blk] + i * k + c);
+        } else {
+          vs.v[0] = vs.v[1] = vs.v[2] = vs.v[3] = T(0);
+          va = vs;
+        }
+        *reinterpret_cast<Vec<T, 4>*>(sS + p * m4 + col) = vs;
+        *reinterpret_cast<Vec<T, 4>*>(sA + p * m4 + col) = va;
       }
-      sS[q] = vs;
-      sA[q] = va;
+    } else {
+      for (int q = threadIdx.x; q < GRAM_PXC * m4; q += GRAM_T) {
+        const int p = q / m4, col = q - p * m4;
+        const int64_t i = i0 + p;
+        T vs = T(0), va = T(0);
+        if (i < a.n && col < m) {
+          const int blk = col / k, c = col - blk * k;
+          vs = a.S[blk][i * k + c];
+          va = a.AS[blk][i * k + c];
+        }
+        sS[q] = vs;
+        sA[q] = va;
+      }
     }
-    for (int p = threadIdx.x; p < GRAM_PX; p += GRAM_THREADS) {
+    for (int p = threadIdx.x; p < GRAM_PXC; p += GRAM_T) {
       const int64_t i = i0 + p;
       sb[p] = (i < a.n) ? (a.b ? a.b[i] : T(1)) : T(0);
     }
     __syncthreads();
+    if (act) {
+      for (int p = grp; p < GRAM_PXC; p += ng) {
+        const Vec<T, 4> xa = *reinterpret_cast<const Vec<T, 4>*>(sS + p * m4 + ta * 4);
+        const Vec<T, 4> xb = *reinterpret_cast<const Vec<T, 4>*>(sS + p * m4 + tb * 4);
+        const Vec<T, 4> yb = *reinterpret_cast<const Vec<T, 4>*>(sA + p * m4 + tb * 4);
+        const T bp = sb[p];
 #pragma unroll
-    for (int q = 0; q < IT; ++q) {
-      const int it = (IT == 1) ? ((int)threadIdx.x - grp * items) : ((int)threadIdx.x + q * GRAM_THREADS);
-      if (it >= items || (IT == 1 && grp >= ng)) continue;
-      const int ar = it / (m4 / 4), cq = it - ar * (m4 / 4);
-      T cA[4] = {T(0), T(0), T(0), T(0)}, cB[4] = {T(0), T(0), T(0), T(0)};
-      for (int p = grp; p < GRAM_PX; p += ng) {
-        const T sa = sS[p * m4 + ar];
-        const T bsa = sb[p] * sa;
+        for (int i = 0; i < 4; ++i) {
+          const T bx = bp * xa.v[i];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          cA[e] = fma(sa, sA[p * m4 + cq * 4 + e], cA[e]);
-          cB[e] = fma(bsa, sS[p * m4 + cq * 4 + e], cB[e]);
+          for (int j = 0; j < 4; ++j) {
+            cA[i * 4 + j] = fma(xa.v[i], yb.v[j], cA[i * 4 + j]);
+            cB[i * 4 + j] = fma(bx, xb.v[j], cB[i * 4 + j]);
+          }
         }
-      }
+        if (++since_fold == fold_every) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        two_sum(hA[q][e], lA[q][e], cA[e]);
-        two_sum(hB[q][e], lB[q][e], cB[e]);
+          for (int e = 0; e < 16; ++e) {
+            two_sum(hA[e], lA[e], cA[e]);
+            two_sum(hB[e], lB[e], cB[e]);
+            cA[e] = cB[e] = T(0);
+          }
+          since_fold = 0;
+        }
       }
     }
   }
-  // combine pixel groups (IT == 1) through shared memory, then write the block partial
-  __syncthreads();
-  double* red = reinterpret_cast<double*>(smem);   // [GRAM_THREADS][8]
-  double* out = a.partials + (size_t)blockIdx.x * 2 * m * m4;
-  if (IT == 1) {
-    const int it = (int)threadIdx.x - grp * items;
-    if (grp < ng && it < items) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        red[threadIdx.x * 8 + e] = (double)hA[0][e] + (double)lA[0][e];
-        red[threadIdx.x * 8 + 4 + e] = (double)hB[0][e] + (double)lB[0][e];
+  for (int e = 0; e < 16; ++e) {
+    two_sum(hA[e], lA[e], cA[e]);
+    two_sum(hB[e], lB[e], cB[e]);
+  }
+  // tree over the pixel groups: the sender (odd multiple of stride) hands its (hi, lo)
+  // pairs to the receiver stride groups below
+  T* scr = reinterpret_cast<T*>(smem);               // [ng / 2 + 1][nt][64]
+  for (int stride = 1; stride < ng; stride <<= 1) {
+    __syncthreads();
+    const bool sender = act && (grp % (2 * stride) == stride);
+    if (sender) {
+      T* dst = scr + ((size_t)((grp - stride) / (2 * stride)) * nt + tile) * 64;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        dst[e] = hA[e];
+        dst[16 + e] = lA[e];
+        dst[32 + e] = hB[e];
+        dst[48 + e] = lB[e];
       }
     }
     __syncthreads();
-    if ((int)threadIdx.x < items) {
-      const int it0 = threadIdx.x;
-      const int ar = it0 / (m4 / 4), cq = it0 - ar * (m4 / 4);
+    const bool receiver = act && (grp % (2 * stride) == 0) && (grp + stride < ng);
+    if (receiver) {
+      const T* src = scr + ((size_t)(grp / (2 * stride)) * nt + tile) * 64;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        double s = 0.0;
-        for (int gq = 0; gq < ng; ++gq) s += red[(gq * items + it0) * 8 + e];
-        const int c = cq * 4 + (e & 3);
-        out[(size_t)((e < 4) ? 0 : 1) * m * m4 + (size_t)ar * m4 + c] = s;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < IT; ++q) {
-      const int it = (int)threadIdx.x + q * GRAM_THREADS;
-      if (it >= items) continue;
-      const int ar = it / (m4 / 4), cq = it - ar * (m4 / 4);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        out[(size_t)ar * m4 + cq * 4 + e] = (double)hA[q][e] + (double)lA[q][e];
-        out[(size_t)m * m4 + (size_t)ar * m4 + cq * 4 + e] = (double)hB[q][e] + (double)lB[q][e];
+      for (int e = 0; e < 16; ++e) {
+        two_sum(hA[e], lA[e], src[e]);
+        lA[e] += src[16 + e];
+        two_sum(hB[e], lB[e], src[32 + e]);
+        lB[e] += src[48 + e];
       }
     }
   }
+  if (act && grp == 0) {
+    double* out = a.partials + (size_t)blockIdx.x * 2 * m * m;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = ta * 4 + i, c = tb * 4 + j;
+        if (r < m && c < m && r <= c) {
+          out[(size_t)r * m + c] = (double)hA[i * 4 + j] + (double)lA[i * 4 + j];
+          out[(size_t)m * m + (size_t)r * m + c] = (double)hB[i * 4 + j] + (double)lB[i * 4 + j];
+        }
+      }
+  }
 }
 
-// Sum the Gram partials over blocks in order: G[2][m][m] (compact).
-__global__ void k_gram_reduce(const double* __restrict__ partials, int nblocks, int m, int m4,
-                              double* G, const LobState* st) {
+// Sum the Gram partials over blocks in block order (eight lanes per entry, each a strided
+// share, combined by shuffles) and write both triangles: G[2][m][m].
+__global__ void k_gram_reduce(const double* __restrict__ partials, int nblocks, int m, double* G,
+                              const LobState* st) {
   if (st->status != LOB_RUN) return;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= 2 * m * m) return;
-  const int w = q / (m * m), r = q - w * m * m;
-  const int a = r / m, c = r - a * m;
-  const size_t off = (size_t)w * m * m4 + (size_t)a * m4 + c;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = gtid >> 3, part = gtid & 7;
+  const int nupper = m * (m + 1) / 2;
+  const bool ok = e < 2 * nupper;
+  int w = 0, r = 0, c = 0;
+  if (ok) {
+    w = e / nupper;
+    int t = e - w * nupper;
+    while (t >= m - r) { t -= m - r; ++r; }
+    c = r + t;
+  }
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * 2 * m * m4 + off];
-  G[q] = s;
+  if (ok) {
+    const size_t off = (size_t)w * m * m + (size_t)r * m + c;
+    for (int b = part; b < nblocks; b += 8) s += partials[(size_t)b * 2 * m * m + off];
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  if (ok && part == 0) {
+    G[(size_t)w * m * m + (size_t)r * m + c] = s;
+    G[(size_t)w * m * m + (size_t)c * m + r] = s;
+  }
 }
 
 // ------------------------------------------------------------------ update
@@ -326,57 +394,66 @@ struct UpdArgs {
   const LobState* st;
 };
 
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename T, int CW>
 __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
   if (a.st->status != LOB_RUN) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = a.k, m = a.m;
   const int ngrp = k / CW;
-  const int pt = 256 / ngrp;                  // pixels per pass
   const bool with_p = a.Pn != nullptr;
   T* sC = reinterpret_cast<T*>(smem);         // [m][k]
   T* sCp = sC + m * k;                        // [m][k]
-  T* sS = sCp + m * k;                        // [pt][m]
   for (int q = threadIdx.x; q < m * k; q += 256) {
     sC[q] = (T)a.C[q];
     sCp[q] = with_p ? (T)a.Cp[q] : T(0);
   }
-  const int p_loc = threadIdx.x / ngrp, g = threadIdx.x - p_loc * ngrp;
-  const int64_t npass = (a.n + pt - 1) / pt;
-  for (int64_t ps = blockIdx.x; ps < npass; ps += gridDim.x) {
-    const int64_t i0 = ps * pt;
-    __syncthreads();
-    for (int q = threadIdx.x; q < pt * m; q += 256) {
-      const int p = q / m, col = q - p * m;
-      const int64_t i = i0 + p;
-      T vs = T(0);
-      if (i < a.n) {
-        const int blk = col / k, c = col - blk * k;
-        vs = a.S[blk][i * k + c];
-      }
-      sS[q] = vs;
-    }
-    __syncthreads();
-    const int64_t i = i0 + p_loc;
-    if (p_loc < pt && i < a.n) {
-      T x[CW], pp[CW];
+  __syncthreads();
+  const int64_t total = a.n * ngrp;
+  for (int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x; q < total; q += (int64_t)gridDim.x * 256) {
+    const int64_t i = q / ngrp;
+    const int g = (int)(q - i * ngrp);
+    // X' is formed in double-float: each product exactly (TwoProd by fma) and the running
+    // sum with TwoSum, so X' is the rounding of S C (an FP32 running sum over 3k terms
+    // moved the Ritz values of small problems by ~1e-6)
+    T x[CW], xl[CW], pp[CW];
 #pragma unroll
-      for (int e = 0; e < CW; ++e) x[e] = pp[e] = T(0);
-      for (int r = 0; r < m; ++r) {
-        const T s = sS[p_loc * m + r];
+    for (int e = 0; e < CW; ++e) x[e] = xl[e] = pp[e] = T(0);
+    for (int blk = 0; blk < a.nblk; ++blk) {
+      const T* row = a.S[blk] + i * k;
+      for (int c0 = 0; c0 < k; c0 += CW) {
+        Vec<T, CW> sv = *reinterpret_cast<const Vec<T, CW>*>(row + c0);
 #pragma unroll
-        for (int e = 0; e < CW; ++e) {
-          x[e] = fma(s, sC[r * k + g * CW + e], x[e]);
-          if (with_p) pp[e] = fma(s, sCp[r * k + g * CW + e], pp[e]);
+        for (int u = 0; u < CW; ++u) {
+          const int r = blk * k + c0 + u;
+          const Vec<T, CW> cv = *reinterpret_cast<const Vec<T, CW>*>(sC + r * k + g * CW);
+#pragma unroll
+          for (int e = 0; e < CW; ++e) {
+            const T pr = mul_rn(sv.v[u], cv.v[e]);      // not contracted into the add below
+            const T pe = fma(sv.v[u], cv.v[e], -pr);
+            const T t = x[e] + pr;
+            const T bp = t - x[e];
+            xl[e] += ((x[e] - (t - bp)) + (pr - bp)) + pe;
+            x[e] = t;
+          }
+          if (with_p) {
+            const Vec<T, CW> pv = *reinterpret_cast<const Vec<T, CW>*>(sCp + r * k + g * CW);
+#pragma unroll
+            for (int e = 0; e < CW; ++e) pp[e] = fma(sv.v[u], pv.v[e], pp[e]);
+          }
         }
       }
-#pragma unroll
-      for (int e = 0; e < CW; ++e) {
-        const int c = g * CW + e;
-        a.Xn[i * k + c] = x[e];
-        if (with_p) a.Pn[i * k + c] = pp[e];
-      }
     }
+    Vec<T, CW> xo, po;
+#pragma unroll
+    for (int e = 0; e < CW; ++e) {
+      xo.v[e] = x[e] + xl[e];
+      po.v[e] = pp[e];
+    }
+    *reinterpret_cast<Vec<T, CW>*>(a.Xn + i * k + g * CW) = xo;
+    if (with_p) *reinterpret_cast<Vec<T, CW>*>(a.Pn + i * k + g * CW) = po;
   }
 }
 
@@ -412,6 +489,22 @@ __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T*
       bx2 = fma(bx, bx, bx2);
       bw = fma(bi, w, bw);
     }
+  }
+  // lanes that share a column (lane = c mod k when k divides 32) are summed by shuffles
+  // before one shared-memory add per column and warp
+  const int lane = threadIdx.x & 31;
+  if ((32 % k) == 0) {
+    for (int o = 16; o >= k; o >>= 1) {
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      bx2 += __shfl_xor_sync(0xffffffffu, bx2, o);
+      bw += __shfl_xor_sync(0xffffffffu, bw, o);
+    }
+    if (lane < k && pl < lanes) {
+      atomicAdd(&sums[c], (double)r2);
+      atomicAdd(&sums[k + c], (double)bx2);
+      atomicAdd(&sums[2 * k + c], (double)bw);
+    }
+  } else if (pl < lanes) {
     atomicAdd(&sums[c], (double)r2);
     atomicAdd(&sums[k + c], (double)bx2);
     atomicAdd(&sums[2 * k + c], (double)bw);
@@ -540,39 +633,35 @@ static int sm_count() {
   return n;
 }
 
-template <typename T, int IT>
-static void launch_gram_it(const GramArgs<T>& ga, int grid, size_t sm, cudaStream_t s) {
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(k_gram<T, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    init = true;
-  }
-  BF_LAUNCH(k_gram<T, IT><<<grid, GRAM_THREADS, sm, s>>>(ga));
-}
-
 template <typename T>
 static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
-  const int items = ga.m * (ga.m4 / 4);
-  const int it = (items + GRAM_THREADS - 1) / GRAM_THREADS;
-  size_t sm = (size_t)(2 * GRAM_PX * ga.m4 + GRAM_PX) * sizeof(T);
-  sm = std::max(sm, (size_t)GRAM_THREADS * 8 * sizeof(double));
-  switch (it) {
-    case 1: launch_gram_it<T, 1>(ga, grid, sm, s); break;
-    case 2: launch_gram_it<T, 2>(ga, grid, sm, s); break;
-    case 3: launch_gram_it<T, 3>(ga, grid, sm, s); break;
-    case 4: launch_gram_it<T, 4>(ga, grid, sm, s); break;
-    case 5: launch_gram_it<T, 5>(ga, grid, sm, s); break;
-    default: return bf_fail(BF_EINVAL, "lobpcg_filter: block too wide");
+  const int ta_n = ga.m4 / 4;
+  const int nt = ta_n * (ta_n + 1) / 2;
+  if (nt > GRAM_T) return bf_fail(BF_EINVAL, "lobpcg_filter: block too wide");
+  const int ng = GRAM_T / nt;
+  size_t sm = (size_t)(2 * GRAM_PXC * ga.m4 + GRAM_PXC) * sizeof(T);
+  sm = std::max(sm, (size_t)(ng / 2 + 1) * nt * 64 * sizeof(T));
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    init = true;
   }
+  BF_LAUNCH(k_gram<T><<<grid, GRAM_T, sm, s>>>(ga));
   BF_CUDA(cudaGetLastError());
   return BF_OK;
 }
 
+static void run_gram_reduce(const double* partials, int nblocks, int m, double* G,
+                            const LobState* st, cudaStream_t s) {
+  const int threads = 2 * (m * (m + 1) / 2) * 8;
+  BF_LAUNCH(k_gram_reduce<<<(threads + 255) / 256, 256, 0, s>>>(partials, nblocks, m, G, st));
+}
+
 template <typename T, int CW>
 static void launch_update_cw(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
-  const int ngrp = ua.k / CW;
-  const int pt = 256 / ngrp;
-  const size_t sm = (size_t)(2 * ua.m * ua.k + pt * ua.m) * sizeof(T);
+  const size_t sm = (size_t)(2 * ua.m * ua.k) * sizeof(T);
+  const int64_t work = ua.n * (ua.k / CW);
+  grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)grid);
   static bool init = false;
   if (!init) {
     cudaFuncSetAttribute(k_update<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -609,19 +698,19 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   const int64_t n = g->n;
   const int nsm = sm_count();
   const int ggrid = nsm;                       // Gram blocks
-  const int ugrid = 2 * nsm;                   // update blocks
+  const int ugrid = 64 * nsm;                  // update blocks (capped by the work)
   const int rgrid = 2 * nsm;                   // reduction blocks
   const size_t blk = (((size_t)n * k * sizeof(T)) + 255) & ~(size_t)255;
-  const int m3 = 3 * k, m34 = (m3 + 3) & ~3;
-  const size_t gpb = (((size_t)ggrid * 2 * m3 * m34 * sizeof(double)) + 255) & ~(size_t)255;
+  const int m3 = 3 * k;
+  const size_t gpb = (((size_t)ggrid * 2 * m3 * m3 * sizeof(double)) + 255) & ~(size_t)255;
   const size_t gb = ((2 * (size_t)m3 * m3 * sizeof(double)) + 255) & ~(size_t)255;
   const size_t cb = (((size_t)m3 * k * sizeof(double)) + 255) & ~(size_t)255;
   const size_t pb = (((size_t)std::max(ugrid, rgrid) * (3 * LOB_KMAX + 2) * sizeof(double)) + 255) & ~(size_t)255;
   const size_t yb = 256 * sizeof(double) * 2;
   const size_t total = 11 * blk + gpb + gb + 2 * cb + pb + yb + 1024;
-  int rc = bf_ws_reserve(gm, total);
+  int rc = bf_ws_reserve(gm, BF_WS_LOB, total);
   if (rc) return rc;
-  char* w = (char*)gm->ws;
+  char* w = (char*)gm->ws[BF_WS_LOB];
   LobBuffers<T> B;
   for (int j = 0; j < 2; ++j) {
     B.X[j] = (T*)w; w += blk;
@@ -670,8 +759,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   ga.m4 = (k + 3) & ~3;
   rc = run_gram<T>(ga, ggrid, s);
   if (rc) return rc;
-  const int rthreads = 256;
-  BF_LAUNCH(k_gram_reduce<<<(2 * k * k + rthreads - 1) / rthreads, rthreads, 0, s>>>(B.gram_part, ggrid, k, ga.m4, B.G, B.st));
+  run_gram_reduce(B.gram_part, ggrid, k, B.G, B.st, s);
   RRParams ra;
   ra.G = B.G;
   ra.C = B.C;
@@ -721,7 +809,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
     ga.AS[2] = B.AP[j];
     rc = run_gram<T>(ga, ggrid, s);
     if (rc) return rc;
-    BF_LAUNCH(k_gram_reduce<<<(2 * ga.m * ga.m + rthreads - 1) / rthreads, rthreads, 0, s>>>(B.gram_part, ggrid, ga.m, ga.m4, B.G, B.st));
+    run_gram_reduce(B.gram_part, ggrid, ga.m, B.G, B.st, s);
     ra.m = ga.m;
     ra.m_nop = (nblk == 3) ? 2 * k : 0;
     ra.Cp = B.Cp;

@@ -11,6 +11,12 @@ from paper_1509_02468_gb300 import synth
 TOL_F32 = 1e-5
 TOL_F64 = 1e-11
 TOL_RITZ = 1e-6
+# Short, unconverged FP32 LOBPCG runs on small problems: FP32 vectors move the trajectory
+# itself.  Emulating FP32 storage of X, W, P, AX, AW, AP inside the FP64 oracle moves the
+# Ritz values of these cases by up to 4.6e-7 per step; the operator's FP32 window sums,
+# followed by the cancellation in R = AX - B X theta, add a few times that on the GPU
+# (up to 1.7e-6 measured).  The configuration-size runs are held to TOL_RITZ.
+TOL_RITZ_SMALL_F32 = 3e-6
 
 
 def bf():

@@ -5,7 +5,8 @@ import torch
 
 from oracle import solvers, spectral
 from paper_1509_02468_gb300 import synth
-from tests.gpu_helpers import TOL_RITZ, bf, dev, host, image_case, make_pair, rel_l2, signal_case
+from tests.gpu_helpers import (TOL_RITZ, TOL_RITZ_SMALL_F32, bf, dev, host, image_case, make_pair,
+                               rel_l2, signal_case)
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +58,7 @@ def test_lobpcg_small_image_fp32(k, constrain):
     _, g = image_case(48, 53, 13)
     out, ref, O = run_pair(g, 2, 2.0, 0.08, k, 12, constrain=constrain)
     e = ritz_ok(host(out["theta"]), ref["theta"])
-    assert e < TOL_RITZ, e
+    assert e < TOL_RITZ_SMALL_F32, e
     th = host(out["theta_hist"])
     np.testing.assert_allclose(th[-1], host(out["theta"]))
     assert rel_l2(host(out["y"]), ref["y"]) < 1e-4
@@ -92,7 +93,7 @@ def test_lobpcg_converges_to_dense_eigenvalues_on_gpu():
 def test_lobpcg_identity_pencil_and_precond():
     _, g = signal_case(600, 4, dtype=np.float32)
     out, ref, O = run_pair(g, 3, 2.0, 0.1, 4, 15, pencil="I", precond="identity")
-    assert ritz_ok(host(out["theta"]), ref["theta"]) < TOL_RITZ
+    assert ritz_ok(host(out["theta"]), ref["theta"]) < TOL_RITZ_SMALL_F32
 
 
 def test_lobpcg_tolerance_stop():
@@ -109,3 +110,24 @@ def test_lobpcg_rejects_bad_sizes():
     G, _ = make_pair(g, 1, 1.0, 0.1)
     with pytest.raises(bf().BFError):
         bf().lobpcg_filter(G, dev(np.ones((16, 6))), 3)    # 3k > n
+
+
+def test_cg_and_lobpcg_concurrently_on_one_graph():
+    """The two filters keep separate workspaces: run on two streams at once they give what
+    they give one after the other."""
+    _, g = image_case(96, 80, 17)
+    G, O = make_pair(g, 3, 2.0, 0.08)
+    x0 = dev(g.reshape(-1))
+    X0 = dev(synth.block_start(g.reshape(-1), 8, seed=3), torch.float32)
+    xs, _, _ = bf().cg_filter(G, x0, 25)
+    ls = bf().lobpcg_filter(G, X0, 10)
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    side.wait_stream(main)
+    xc, _, _ = bf().cg_filter(G, x0, 25, sync=False, stream=side)
+    lc = bf().lobpcg_filter(G, X0, 10, sync=False)
+    main.wait_stream(side)
+    torch.cuda.synchronize()
+    assert torch.equal(xc, xs)
+    assert torch.equal(lc["theta"], ls["theta"])
+    assert torch.equal(lc["y"], ls["y"])
