@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "bf_internal.cuh"
+#include "bf_window_fast.cuh"
 
 int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
@@ -215,6 +216,154 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_update(const CgArgs<T> a) {
   }
 }
 
+// ---- specialised-window versions of k_cg_init / k_cg_dir (float graphs, common windows)
+template <class SH, class F>
+__device__ __forceinline__ void stage1_fast(const Geom<float>& g, int bx, int by, float* sx,
+                                            float* sg, float* sval, const float* guide,
+                                            bool need_guide, F f) {
+  for (int hp = threadIdx.x; hp < SH::hp; hp += BF_THREADS) {
+    const int hy = hp / SH::hw, hx = hp - hy * SH::hw;
+    const int gy = by - SH::ry + hy, gx = bx - SH::rx + hx;
+    const bool in = (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny);
+    float v = 0.0f, gv = 0.0f;
+    if (in) {
+      const int64_t gp = (int64_t)gy * g.nx + gx;
+      v = f(gp);
+      if (need_guide) gv = guide[gp];
+    }
+    sx[hp] = v;
+    if (need_guide) sg[hp] = gv;
+    sval[hp] = in ? 1.0f : 0.0f;
+  }
+}
+
+template <class SH, bool STORED>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_init_fast(const Geom<float> g, const CgArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  float* sx = reinterpret_cast<float*>(smem);
+  float* sg = sx + SH::hp;
+  float* sval = sg + SH::hp;
+  const int bx = blockIdx.x * SH::tw, by = blockIdx.y * SH::th;
+  const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= g.nx && by - SH::ry >= 0 &&
+                      by + SH::th + SH::ry <= g.ny);
+  stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED, [&](int64_t gp) { return a.x0[gp]; });
+  __syncthreads();
+  const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
+  const int x = bx + lx, y = by + ly;
+  const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
+  float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (x < g.nx && y < g.ny) {
+    const int64_t i = (int64_t)y * g.nx + x;
+    float xi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+    window_fast<SH, 1, STORED>(g, hp0, i, g.nx, sg, sval, mask,
+                               reinterpret_cast<const Vec<float, 1>*>(sx), a.wf, a.wmode, a.n, xi, acc, ws);
+    const float r = -acc[0];
+    const float sv = a.dinv ? r * a.dinv[i] : r;
+    a.x[i] = xi[0];
+    a.r[i] = r;
+    a.s[i] = sv;
+    v[0] = sv * r;
+    v[1] = sv * sv;
+    v[2] = r * r;
+    v[3] = xi[0] * xi[0];
+  }
+  double blk[4], tot[4];
+  block_sum<4, float>(v, red, blk);
+  if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->sr = tot[0];
+    st->ss = tot[1];
+    st->rr = tot[2];
+    const double b2 = (double)a.shift * (double)a.shift * tot[3];
+    st->ref2 = b2 > 0.0 ? b2 : tot[2];
+    st->beta = 0.0;
+    st->alpha = 0.0;
+    st->iter = 0;
+    st->status = (isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2])) ? CG_RUN : CG_NONFINITE;
+  }
+}
+
+template <class SH, bool STORED>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_dir_fast(const Geom<float> g, const CgArgs<float> a) {
+  if (a.st->status != CG_RUN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[1 * (BF_THREADS / 32)];
+  __shared__ int last;
+  float* sx = reinterpret_cast<float*>(smem);
+  float* sg = sx + SH::hp;
+  float* sval = sg + SH::hp;
+  const int bx = blockIdx.x * SH::tw, by = blockIdx.y * SH::th;
+  const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= g.nx && by - SH::ry >= 0 &&
+                      by + SH::th + SH::ry <= g.ny);
+  const float beta = (float)a.st->beta;
+  if (a.first)
+    stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED, [&](int64_t gp) { return a.s[gp]; });
+  else
+    stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED,
+                    [&](int64_t gp) { return fmaf(beta, a.p_old[gp], a.s[gp]); });
+  __syncthreads();
+  const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
+  const int x = bx + lx, y = by + ly;
+  const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
+  float v[1] = {0.0f};
+  if (x < g.nx && y < g.ny) {
+    const int64_t i = (int64_t)y * g.nx + x;
+    float pi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+    window_fast<SH, 1, STORED>(g, hp0, i, g.nx, sg, sval, mask,
+                               reinterpret_cast<const Vec<float, 1>*>(sx), a.wf, a.wmode, a.n, pi, acc, ws);
+    const float q = fmaf(a.shift, pi[0], acc[0]);
+    a.p_new[i] = pi[0];
+    a.q[i] = q;
+    v[0] = pi[0] * q;
+  }
+  double blk[1], tot[1];
+  block_sum<1, float>(v, red, blk);
+  if (grid_sum_last<1>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->pq = tot[0];
+    if (st->sr == 0.0) {
+      st->status = CG_CONV;
+    } else if (!isfinite(tot[0])) {
+      st->status = CG_NONFINITE;
+    } else if (!(tot[0] > 0.0)) {
+      st->status = CG_BREAK;
+    } else {
+      st->alpha = st->sr / tot[0];
+    }
+  }
+}
+
+// Launch the init / direction kernels: specialised window when the graph has one.
+template <class SH, bool STORED>
+static void cg_launch_fast(bool init, dim3 tg, cudaStream_t s, const bf_graph* g, const CgArgs<float>& a) {
+  const size_t sm = 3 * SH::hp * sizeof(float);
+  if (init) BF_LAUNCH(k_cg_init_fast<SH, STORED><<<tg, BF_THREADS, sm, s>>>(g->gf, a));
+  else BF_LAUNCH(k_cg_dir_fast<SH, STORED><<<tg, BF_THREADS, sm, s>>>(g->gf, a));
+}
+
+template <class SH>
+static void cg_launch_fast_w(bool init, dim3 tg, cudaStream_t s, const bf_graph* g, const CgArgs<float>& a) {
+  if (g->p.weight_mode == BF_W_ONTHEFLY) cg_launch_fast<SH, false>(init, tg, s, g, a);
+  else cg_launch_fast<SH, true>(init, tg, s, g, a);
+}
+
+template <typename T>
+static void cg_launch_window(bool init, dim3 tg, size_t sm, cudaStream_t s, const bf_graph* g,
+                             const CgArgs<T>& a) {
+  if (sizeof(T) == 4) {
+    const CgArgs<float>& af = reinterpret_cast<const CgArgs<float>&>(a);
+    switch (fast_shape(g)) {
+      case FAST_R3_2D: cg_launch_fast_w<ShapeR3>(init, tg, s, g, af); return;
+      case FAST_R5_1D: cg_launch_fast_w<ShapeR5>(init, tg, s, g, af); return;
+      case FAST_CROSS1: cg_launch_fast_w<ShapeX1>(init, tg, s, g, af); return;
+    }
+  }
+  if (init) BF_LAUNCH(k_cg_init<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+  else BF_LAUNCH(k_cg_dir<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+}
+
 template <typename T>
 int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_out,
            bf_info* info, cudaStream_t s) {
@@ -257,13 +406,13 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   const bool one_d = (g->ny == 1 && g->ry == 0);
   const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
   const size_t sm = hp * 2 * sizeof(T);
-  BF_LAUNCH(k_cg_init<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+  cg_launch_window<T>(true, tg, sm, s, g, a);
   BF_CUDA(cudaGetLastError());
   for (int it = 0; it < kmax; ++it) {
     a.first = (it == 0);
     a.p_old = pbuf[it & 1];
     a.p_new = pbuf[(it + 1) & 1];
-    BF_LAUNCH(k_cg_dir<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+    cg_launch_window<T>(false, tg, sm, s, g, a);
     BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
   }
   BF_CUDA(cudaGetLastError());

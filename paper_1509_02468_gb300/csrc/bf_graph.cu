@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "bf_internal.cuh"
+#include "bf_window_fast.cuh"
 
 // ================================================================== errors
 static thread_local std::string g_last_error;
@@ -229,6 +230,248 @@ __global__ void __launch_bounds__(BF_THREADS) k_apply(const Geom<T> g, const App
   }
 }
 
+// Laplacian-type operators (L, NSYM, NDIAGL) of float graphs with a specialised window.
+template <class SH, int K, bool STORED>
+__global__ void __launch_bounds__(BF_THREADS) k_apply_fast(const Geom<float> g, const ApplyArgs<float> a) {
+  constexpr int V = VecW<float, K>::value;
+  constexpr int NC = K / V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Vec<float, V>* sx = reinterpret_cast<Vec<float, V>*>(smem);
+  float* sg = reinterpret_cast<float*>(sx + (size_t)NC * SH::hp);
+  float* sval = sg + SH::hp;
+  const int bx = blockIdx.x * SH::tw, by = blockIdx.y * SH::th;
+  const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= g.nx && by - SH::ry >= 0 &&
+                      by + SH::th + SH::ry <= g.ny);
+  stage_fast<SH, K>(g, bx, by, a.X, a.ldx, a.scale, a.guide, !STORED, sx, sg, sval);
+  __syncthreads();
+  const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
+  const int x = bx + lx, y = by + ly;
+  const bool active = x < g.nx && y < g.ny;
+  const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
+  float xi[K], acc[K], yv[K];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const Vec<float, V> v = sx[c * SH::hp + hp0];
+#pragma unroll
+    for (int e = 0; e < V; ++e) xi[c * V + e] = v.v[e];
+  }
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = yv[c] = 0.0f;
+  float wsum = 0.0f;
+  const int64_t i = (int64_t)y * g.nx + x;
+  if (active) {
+    window_fast<SH, K, STORED>(g, hp0, i, g.nx, sg, sval, mask, sx, a.wf, a.wmode, a.n, xi, acc, wsum);
+    const float s_i = a.scale ? a.scale[i] : 1.0f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) yv[c] = a.scale ? s_i * acc[c] : acc[c];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      Vec<float, V> o;
+#pragma unroll
+      for (int e = 0; e < V; ++e) o.v[e] = yv[c * V + e];
+      *reinterpret_cast<Vec<float, V>*>(a.Y + i * a.ldy + c * V) = o;
+    }
+  }
+  if (a.dots) {
+    if (a.scale && active) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) xi[c] = a.X[i * a.ldx + c];
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const float s = warp_sum(active ? xi[c] * yv[c] : 0.0f);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&a.dots[c], (double)s);
+    }
+  }
+}
+
+// Register-blocked operator for the 7 x 7 window (see RBTile): L-type operators, K >= 4.
+template <int K, bool STORED>
+__global__ void __launch_bounds__(BF_THREADS, 2) k_apply_rb(const Geom<float> g, const ApplyArgs<float> a) {
+  typedef RBTile<K> TT;
+  constexpr int CS = TT::cs, NG = TT::ng, NC4 = K / 4, CS4 = CS / 4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* sx = reinterpret_cast<float4*>(smem);                 // [NC4][hp]
+  float* sg = reinterpret_cast<float*>(sx + NC4 * TT::hp);      // [hp]
+  float* sval = sg + TT::hp;                                    // [hp]
+  const int bx = blockIdx.x * TT::tw, by = blockIdx.y * TT::th;
+  const bool mask = !(bx - 3 >= 0 && bx + TT::tw + 3 <= g.nx && by - 3 >= 0 && by + TT::th + 3 <= g.ny);
+  for (int idx = threadIdx.x; idx < TT::hp * NC4; idx += BF_THREADS) {
+    const int hp = idx / NC4, c = idx - hp * NC4;
+    const int hy = hp / TT::hw, hx = hp - hy * TT::hw;
+    const int gy = by - 3 + hy, gx = bx - 3 + hx;
+    const bool in = (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny);
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (in) {
+      const int64_t gp = (int64_t)gy * g.nx + gx;
+      v = *reinterpret_cast<const float4*>(a.X + gp * a.ldx + c * 4);
+      if (a.scale) {
+        const float sc = a.scale[gp];
+        v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+      }
+      if (c == 0 && !STORED) sg[hp] = a.guide[gp];
+    } else if (c == 0 && !STORED) {
+      sg[hp] = 0.0f;
+    }
+    if (c == 0) sval[hp] = in ? 1.0f : 0.0f;
+    sx[c * TT::hp + hp] = v;
+  }
+  __syncthreads();
+  const int lx = threadIdx.x & 31;
+  const int rest = threadIdx.x >> 5;
+  const int grp = rest % NG, strip = rest / NG;
+  const int x = bx + lx;
+  const int row0 = strip * RB_P;                 // first strip row within the tile
+  float xi[RB_P][CS], gi[RB_P];
+  unsigned long long acc2[RB_P][CS / 2], xi2[RB_P][CS / 2];
+  int64_t ip[RB_P];
+  bool act[RB_P];
+#pragma unroll
+  for (int p = 0; p < RB_P; ++p) {
+    const int hp = (row0 + p + 3) * TT::hw + lx + 3;
+#pragma unroll
+    for (int c4 = 0; c4 < CS4; ++c4) {
+      const float4 v = sx[(grp * CS4 + c4) * TT::hp + hp];
+      xi[p][4 * c4] = v.x; xi[p][4 * c4 + 1] = v.y; xi[p][4 * c4 + 2] = v.z; xi[p][4 * c4 + 3] = v.w;
+    }
+    gi[p] = STORED ? 0.0f : sg[hp];
+    const int y = by + row0 + p;
+    act[p] = (x < g.nx && y < g.ny);
+    ip[p] = (int64_t)y * g.nx + x;
+#pragma unroll
+    for (int c = 0; c < CS / 2; ++c) {
+      acc2[p][c] = f2_pack(0.0f, 0.0f);
+      xi2[p][c] = f2_pack(xi[p][2 * c], xi[p][2 * c + 1]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RB_P + 6; ++r) {
+#pragma unroll
+    for (int dx = -3; dx <= 3; ++dx) {
+      const int hp = (row0 + r) * TT::hw + lx + 3 + dx;
+      unsigned long long xj2[CS / 2];
+#pragma unroll
+      for (int c4 = 0; c4 < CS4; ++c4) {
+        const float4 v = sx[(grp * CS4 + c4) * TT::hp + hp];
+        xj2[2 * c4] = f2_pack(v.x, v.y);
+        xj2[2 * c4 + 1] = f2_pack(v.z, v.w);
+      }
+      const float gj = STORED ? 0.0f : sg[hp];
+      const float vj = mask ? sval[hp] : 1.0f;
+#pragma unroll
+      for (int p = 0; p < RB_P; ++p) {
+        const int dy = r - 3 - p;
+        if (dy < -3 || dy > 3 || (dy == 0 && dx == 0)) continue;
+        float w;
+        if (STORED) {
+          const bool ok = act[p] && vj != 0.0f;
+          if (dy > 0 || (dy == 0 && dx > 0)) {
+            const int f = ShapeR3::fwd_index(dy, dx);
+            w = ok ? ld_weight(a.wf, (int64_t)f * a.n + ip[p], a.wmode) : 0.0f;
+          } else {
+            const int f = ShapeR3::fwd_index(-dy, -dx);
+            w = ok ? ld_weight(a.wf, (int64_t)f * a.n + ip[p] + (int64_t)dy * g.nx + dx, a.wmode) : 0.0f;
+          }
+        } else {
+          w = rb_exp(gi[p], gj, g.a_r, g.ls[(dy + 3) * 7 + (dx + 3)]) * vj;
+        }
+        const unsigned long long w2 = f2_pack(w, w);
+#pragma unroll
+        for (int c = 0; c < CS / 2; ++c) acc2[p][c] = f2_diff_fma(w2, xi2[p][c], xj2[c], acc2[p][c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < RB_P; ++p) {
+    if (!act[p]) continue;
+    const float s_i = a.scale ? a.scale[ip[p]] : 1.0f;
+#pragma unroll
+    for (int c4 = 0; c4 < CS4; ++c4) {
+      float4 o;
+      f2_unpack(acc2[p][2 * c4], o.x, o.y);
+      f2_unpack(acc2[p][2 * c4 + 1], o.z, o.w);
+      o.x *= s_i; o.y *= s_i; o.z *= s_i; o.w *= s_i;
+      *reinterpret_cast<float4*>(a.Y + ip[p] * a.ldy + (grp * CS4 + c4) * 4) = o;
+    }
+  }
+}
+
+template <int K, bool STORED>
+static int launch_apply_rb(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  typedef RBTile<K> TT;
+  const size_t sm = (size_t)TT::hp * (K / 4) * sizeof(float4) + 2 * TT::hp * sizeof(float);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(k_apply_rb<K, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    227 * 1024);
+  });
+  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply_rb)");
+  const dim3 grid((unsigned)((g->nx + TT::tw - 1) / TT::tw), (unsigned)((g->ny + TT::th - 1) / TT::th), 1);
+  BF_LAUNCH(k_apply_rb<K, STORED><<<grid, BF_THREADS, sm, s>>>(g->gf, a));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+template <int K>
+static int launch_apply_rb_w(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  if (g->p.weight_mode == BF_W_ONTHEFLY) return launch_apply_rb<K, false>(g, a, s);
+  return launch_apply_rb<K, true>(g, a, s);
+}
+
+template <class SH, int K, bool STORED>
+static int launch_apply_fast(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  constexpr int V = VecW<float, K>::value;
+  const size_t sm = (size_t)SH::hp * (K / V) * sizeof(Vec<float, V>) + 2 * SH::hp * sizeof(float);
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(k_apply_fast<SH, K, STORED>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply_fast)");
+  BF_LAUNCH(k_apply_fast<SH, K, STORED><<<tile_grid(g), BF_THREADS, sm, s>>>(g->gf, a));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+template <class SH, int K>
+static int launch_apply_fast_w(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  if (g->p.weight_mode == BF_W_ONTHEFLY) return launch_apply_fast<SH, K, false>(g, a, s);
+  return launch_apply_fast<SH, K, true>(g, a, s);
+}
+
+// Returns 1 when it launched the specialised kernel for this chunk width.
+template <class SH>
+static int apply_fast_shape(const bf_graph* g, int K, const ApplyArgs<float>& a, cudaStream_t s, int* rc) {
+  switch (K) {
+    case 1: *rc = launch_apply_fast_w<SH, 1>(g, a, s); return 1;
+    case 4: *rc = launch_apply_fast_w<SH, 4>(g, a, s); return 1;
+    case 8: *rc = launch_apply_fast_w<SH, 8>(g, a, s); return 1;
+    case 16: *rc = launch_apply_fast_w<SH, 16>(g, a, s); return 1;
+    case 32: *rc = launch_apply_fast_w<SH, 32>(g, a, s); return 1;
+  }
+  return 0;
+}
+
+static int try_apply_fast(const bf_graph* g, int K, const ApplyArgs<float>& a, cudaStream_t s, int* rc) {
+  if (!(a.op == BF_OP_L || a.op == BF_OP_NSYM || a.op == BF_OP_NDIAGL)) return 0;
+  if (fast_shape(g) == FAST_R3_2D && !a.dots) {
+    switch (K) {
+      case 4: *rc = launch_apply_rb_w<4>(g, a, s); return 1;
+      case 8: *rc = launch_apply_rb_w<8>(g, a, s); return 1;
+      case 16: *rc = launch_apply_rb_w<16>(g, a, s); return 1;
+      case 32: *rc = launch_apply_rb_w<32>(g, a, s); return 1;
+    }
+  }
+  switch (fast_shape(g)) {
+    case FAST_R3_2D: return apply_fast_shape<ShapeR3>(g, K, a, s, rc);
+    case FAST_R5_1D: return apply_fast_shape<ShapeR5>(g, K, a, s, rc);
+    case FAST_CROSS1: return apply_fast_shape<ShapeX1>(g, K, a, s, rc);
+  }
+  return 0;
+}
+
 template <typename T, int K>
 static size_t apply_smem(const bf_graph* g) {
   const bool one_d = (g->ny == 1 && g->ry == 0);
@@ -255,6 +498,10 @@ static int launch_apply(const bf_graph* g, const ApplyArgs<T>& a, cudaStream_t s
 
 template <typename T>
 static int apply_chunk(const bf_graph* g, int K, const ApplyArgs<T>& a, cudaStream_t s) {
+  if (sizeof(T) == 4) {
+    int rc = BF_OK;
+    if (try_apply_fast(g, K, reinterpret_cast<const ApplyArgs<float>&>(a), s, &rc)) return rc;
+  }
   switch (K) {
     case 1: return launch_apply<T, 1>(g, a, s);
     case 2: return launch_apply<T, 2>(g, a, s);
