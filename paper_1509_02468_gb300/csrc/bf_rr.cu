@@ -1,26 +1,26 @@
-// The small Rayleigh-Ritz problem of block LOBPCG (Algorithm 3, Section 6), solved in
-// FP64 by one CTA: the k smallest eigenpairs of the pencil (G_A, G_B) of size m <= 96.
+// The small Rayleigh-Ritz problem of block LOBPCG (Algorithm 3, Section 6): the k smallest
+// eigenpairs of the pencil (G_A, G_B) of size m <= 96, solved by one CTA.
 //
-// On GB300 a dependent FP64 FMA costs about 64 cycles, an FP64 divide about 640 and FP64
-// throughput is about 1.7 FMA/clk per SM, so the solver keeps FP64 work near m^3 and, more
-// importantly, keeps every dependent FP64 chain short:
-//   1. symmetrise, scale to unit diag(G_B), right-looking Cholesky G_B = R R^T (a squared
-//      pivot <= 1e-10 means a dependent trial basis: retry on the leading m_nop block,
-//      i.e. without P, else report a breakdown);
-//   2. standard form M = R^-1 G_A R^-T by two right-looking triangular solves;
-//   3. Householder reduction M = Q T Q^T to a tridiagonal T (reflectors kept in M);
-//   4. shifts near the k smallest eigenvalues of T from Sturm counts evaluated in FP32
-//      at 32 points per warp (multisection), which is all the accuracy inverse iteration
-//      needs: the final eigenvalues come from step 6;
-//   5. one eigenvector per shift by four steps of FP64 inverse iteration on
-//      T - lambda I (one tridiagonal factorisation with row interchanges, reused by
-//      every step), all k in parallel;
-//   6. Cholesky QR (twice) of those k vectors and a k x k Rayleigh-Ritz on T (cyclic
-//      Jacobi; the matrix is diagonal up to rounding except inside clusters): FP64
-//      eigenvalues and vectors;
-//   7. back-transformation by the reflectors, C = R^-T Y and the unit-diagonal scaling
-//      undone; with Cp requested, the coefficients of the next P made B-orthogonal to
-//      the next X (see the driver).
+// On GB300 FP64 runs at about 2 FMA/clk per SM with a 64-cycle dependent latency, while
+// FP32 runs at 128 FMA/clk with a 4-cycle latency.  The solver therefore keeps FP64 for
+// the steps whose accuracy decides the result and does the O(m^3) eigen-decomposition in
+// FP32, then restores FP64 accuracy with one residual correction:
+//   1. symmetrise, scale to unit diag(G_B), right-looking Cholesky G_B = R R^T carrying
+//      the forward solve Y = R^-1 G_A along (a squared pivot <= 1e-10 means a dependent
+//      trial basis: retry on the leading m_nop block, i.e. without P, else breakdown);
+//   2. standard form M = Y R^-T (FP64, lower triangle);
+//   3. FP32 eigenpairs (lambda_i, v_i) of float(M): Householder reduction to tridiagonal
+//      form, every eigenvalue by multisection on Sturm counts, inverse iteration for every
+//      eigenvector, modified Gram-Schmidt inside clusters, back-transformation;
+//   4. X = the k eigenvectors of the smallest lambda, Y = M X in FP64, Rayleigh quotients
+//      theta_j and the FP64 residual r_j = y_j - theta_j x_j;
+//   5. first-order correction x_j += sum_i v_i (v_i^T r_j) / (theta_j - lambda_i) over the
+//      unwanted eigenpairs outside a 64 eps_32 |M| neighbourhood of theta_j (FP32 products
+//      of FP64 data; the error of the corrected vectors is second order in the FP32 one);
+//   6. symmetric orthonormalisation T = (X^T X)^-1/2 = I + D, D = -E/2 + 3E^2/8 for
+//      X^T X = I + E, H = T (X^T M X) T in FP64, cyclic Jacobi on the k x k H in FP64;
+//   7. C = R^-T X T Q with the scaling undone; with Cp requested, the coefficients of the
+//      next P made B-orthogonal to the next X (see the driver).
 // Reciprocals and square roots use an FP32 seed refined by two FP64 Newton steps
 // (rounding-level accuracy), avoiding the long FP64 divide and square-root sequences.
 #include <math.h>
@@ -31,6 +31,7 @@
 #define RR_T 512
 #define RR_LD 97            // padded leading dimension of the m x m work matrices
 #define RR_KLD 33           // padded leading dimension of the m x k work matrices
+#define RR_LDF 97           // leading dimension of the FP32 m x m Jacobi matrices
 #define DEP_TOL 1e-10
 
 namespace {
@@ -55,10 +56,10 @@ __device__ __forceinline__ double frsqrt(double x) {
 }
 
 // Number of eigenvalues of the symmetric tridiagonal T (diagonal d, squared off-diagonal
-// e2) smaller than x, in FP32: sign changes along p_0 = 1, p_1 = d_0 - x,
-// p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}.  A zero p_i is counted as a sign change
-// (as if it were a tiny number of the opposite sign); the pair (p_{i-1}, p_i) is rescaled
-// by a power of two whenever p_i leaves [2^-60, 2^60].
+// e2) smaller than x: sign changes along p_0 = 1, p_1 = d_0 - x,
+// p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}.  A zero p_i counts as a sign change (as
+// if it were a tiny number of the opposite sign); the pair (p_{i-1}, p_i) is rescaled by a
+// power of two whenever p_i leaves [2^-60, 2^60].
 __device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
   float p0 = 1.0f, p1 = d[0] - x;
   if (p1 == 0.0f) p1 = -0x1p-40f;
@@ -79,144 +80,224 @@ __device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
   return cnt;
 }
 
-// Factor T - lambda I by elimination with row interchanges: the working row (entries in
-// columns i, i+1, i+2) is compared with the next original row and the larger entry in
-// column i is the pivot.  Kept per row i: the multiplier f[i], whether the rows were
-// interchanged (sw[i]), the pivot reciprocal ri[i] and the two entries right of the
-// pivot (u1, u2).  Zero pivots are replaced by `tiny`.
-__device__ void tri_factor(const double* d, const double* e, int m, double lambda, double tiny,
-                           double* f, unsigned char* sw, double* ri, double* u1, double* u2) {
-  double r0 = d[0] - lambda, r1 = (m > 1) ? e[0] : 0.0, r2 = 0.0;
+// Inverse iteration on T - lambda I (FP32): elimination with row interchanges (the
+// working row, entries in columns i, i+1, i+2, against the next original row; the larger
+// entry in column i pivots; zero pivots become `tiny`), then `reps` solves from the start
+// vector b, each normalised by its largest entry.
+__device__ void tri_inverse_iteration(const float* d, const float* e, int m, float lambda, float tiny,
+                                      int reps, float* b) {
+  float f[RR_MMAX], ri[RR_MMAX], u1[RR_MMAX], u2[RR_MMAX];
+  unsigned char sw[RR_MMAX];
+  float r0 = d[0] - lambda, r1 = (m > 1) ? e[0] : 0.0f, r2 = 0.0f;
   for (int i = 0; i < m - 1; ++i) {
-    const double n0 = e[i], n1 = d[i + 1] - lambda, n2 = (i + 2 < m) ? e[i + 1] : 0.0;
-    const bool keep = fabs(r0) >= fabs(n0);
-    double p0 = keep ? r0 : n0;
-    const double p1 = keep ? r1 : n1, p2 = keep ? r2 : n2;
-    const double o0 = keep ? n0 : r0, o1 = keep ? n1 : r1, o2 = keep ? n2 : r2;
-    if (p0 == 0.0) p0 = tiny;
-    const double rp = frcp(p0);
-    const double fi = o0 * rp;
+    const float n0 = e[i], n1 = d[i + 1] - lambda, n2 = (i + 2 < m) ? e[i + 1] : 0.0f;
+    const bool keep = fabsf(r0) >= fabsf(n0);
+    float p0 = keep ? r0 : n0;
+    const float p1 = keep ? r1 : n1, p2 = keep ? r2 : n2;
+    const float o0 = keep ? n0 : r0, o1 = keep ? n1 : r1, o2 = keep ? n2 : r2;
+    if (p0 == 0.0f) p0 = tiny;
+    const float rp = __fdividef(1.0f, p0);
+    const float fi = o0 * rp;
     f[i] = fi;
     sw[i] = keep ? 0 : 1;
     ri[i] = rp;
     u1[i] = p1;
     u2[i] = p2;
-    r0 = fma(-fi, p1, o1);
-    r1 = fma(-fi, p2, o2);
-    r2 = 0.0;
+    r0 = fmaf(-fi, p1, o1);
+    r1 = fmaf(-fi, p2, o2);
+    r2 = 0.0f;
   }
-  if (r0 == 0.0) r0 = tiny;
-  ri[m - 1] = frcp(r0);
-  u1[m - 1] = 0.0;
-  u2[m - 1] = 0.0;
+  if (r0 == 0.0f) r0 = tiny;
+  ri[m - 1] = __fdividef(1.0f, r0);
+  u1[m - 1] = 0.0f;
+  u2[m - 1] = 0.0f;
+  for (int rep = 0; rep < reps; ++rep) {
+    float rb = b[0];
+    for (int i = 0; i < m - 1; ++i) {
+      const float nb = b[i + 1];
+      const float pb = sw[i] ? nb : rb, ob = sw[i] ? rb : nb;
+      b[i] = pb;
+      rb = fmaf(-f[i], pb, ob);
+    }
+    b[m - 1] = rb * ri[m - 1];
+    if (m > 1) b[m - 2] = fmaf(-u1[m - 2], b[m - 1], b[m - 2]) * ri[m - 2];
+    for (int i = m - 3; i >= 0; --i) b[i] = fmaf(-u2[i], b[i + 2], fmaf(-u1[i], b[i + 1], b[i])) * ri[i];
+    float nrm = 0.0f;
+    for (int i = 0; i < m; ++i) nrm = fmaxf(nrm, fabsf(b[i]));
+    const float inv = (nrm > 0.0f && isfinite(nrm)) ? __fdividef(1.0f, nrm) : 1.0f;
+    for (int i = 0; i < m; ++i) b[i] *= inv;
+  }
 }
 
-// Solve with the factors of tri_factor, b -> x in place.
-__device__ void tri_solve(int m, const double* f, const unsigned char* sw, const double* ri,
-                          const double* u1, const double* u2, double* b) {
-  double rb = b[0];
-  for (int i = 0; i < m - 1; ++i) {
-    const double nb = b[i + 1];
-    const double pb = sw[i] ? nb : rb, ob = sw[i] ? rb : nb;
-    b[i] = pb;
-    rb = fma(-f[i], pb, ob);
-  }
-  b[m - 1] = rb * ri[m - 1];
-  if (m > 1) b[m - 2] = fma(-u1[m - 2], b[m - 1], b[m - 2]) * ri[m - 2];
-  for (int i = m - 3; i >= 0; --i) b[i] = fma(-u2[i], b[i + 2], fma(-u1[i], b[i + 1], b[i])) * ri[i];
-}
-
+// Round-robin pairing of np (even) indices: in step s (0 <= s < np - 1) pair i (i < np / 2)
+// joins s + i and s - i (mod np - 1), pair 0 joins s with the fixed index np - 1.
 __device__ __forceinline__ void jacobi_pair_k(int step, int i, int np, int& p, int& q) {
   const int n1 = np - 1;
   if (i == 0) {
-    p = step % n1;
+    p = step;
     q = n1;
   } else {
-    p = (step + i) % n1;
-    q = (step - i + n1) % n1;
+    p = step + i;
+    if (p >= n1) p -= n1;
+    q = step - i;
+    if (q < 0) q += n1;
   }
   if (p > q) { const int t = p; p = q; q = t; }
+}
+
+// q / d for q < 2^32 / d by a multiply-high with ceil(2^32 / d)
+struct FastDiv {
+  unsigned d, inv;
+  __device__ explicit FastDiv(unsigned dd) : d(dd), inv(dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u) {}
+  __device__ __forceinline__ unsigned div(unsigned q) const { return d > 1 ? __umulhi(q, inv) : q; }
+};
+
+// lower-stored symmetric matrix
+__device__ __forceinline__ double symv(const double* A, int r, int c) {
+  return (c <= r) ? A[r * RR_LD + c] : A[c * RR_LD + r];
+}
+
+// Lane layout for outputs with at most 32 columns: a warp covers 32 >> sh rows of 1 << sh
+// columns (1 << sh >= ncol), so index arithmetic needs shifts and masks only.
+struct Tiling {
+  int sh, rows, lr, lc;
+  __device__ Tiling(int ncol, int lane) {
+    sh = (ncol <= 1) ? 0 : 32 - __clz(ncol - 1);
+    rows = 32 >> sh;
+    lr = lane >> sh;
+    lc = lane & ((1 << sh) - 1);
+  }
+};
+#define RR_NW (RR_T / 32)
+// for (r, c) in [0, nrow) x [0, ncol) with the tiling t (warp w, RR_NW warps)
+#define FOR_RC(t, nrow, ncol, w)                                            \
+  for (int r0_ = (w) * (t).rows; r0_ < (nrow); r0_ += RR_NW * (t).rows)  \
+    for (int r = r0_ + (t).lr, c = (t).lc; r < (nrow) && c < (ncol); r = (nrow))
+
+// Y = M X (FP64), M lower-stored, X and Y [m][RR_KLD]
+__device__ void mul_mx(const double* MA, const double* X, double* Y, int m, const Tiling& tk, int k,
+                       int wid) {
+  FOR_RC(tk, m, k, wid) {
+    double s0 = 0.0, s1 = 0.0;
+    int cc = 0;
+    for (; cc + 1 <= r; cc += 2) {
+      s0 = fma(MA[r * RR_LD + cc], X[cc * RR_KLD + c], s0);
+      s1 = fma(MA[r * RR_LD + cc + 1], X[(cc + 1) * RR_KLD + c], s1);
+    }
+    for (; cc < m; ++cc) s0 = fma(MA[cc * RR_LD + r], X[cc * RR_KLD + c], s0);
+    Y[r * RR_KLD + c] = s0 + s1;
+  }
 }
 
 __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   if (*a.status != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  double* M = reinterpret_cast<double*>(smem);          // [96][RR_LD]
-  double* R = M + RR_MMAX * RR_LD;                      // [96][RR_LD]
-  double* Z = R + RR_MMAX * RR_LD;                      // [96][RR_KLD] eigenvectors
-  double* H = Z + RR_MMAX * RR_KLD;                     // [32][RR_KLD] k x k problem
-  double* Vk = H + RR_KMAX * RR_KLD;                    // [32][RR_KLD]
-  double* sc = Vk + RR_KMAX * RR_KLD;                   // [96] unit-diagonal scaling
-  double* rdg = sc + RR_MMAX;                           // [96] 1 / diag(R)
-  double* dd = rdg + RR_MMAX;                           // [96] diagonal of T
-  double* ee = dd + RR_MMAX;                            // [96] off-diagonal of T
-  double* e2 = ee + RR_MMAX;                            // [96] squared off-diagonal
-  double* bet = e2 + RR_MMAX;                           // [96] reflector scalars
-  double* pv = bet + RR_MMAX;                           // [96] work vector
-  double* lam = pv + RR_MMAX;                           // [32] shifts
-  double* cs = lam + RR_KMAX;                           // [16]
-  double* sn = cs + RR_KMAX / 2;                        // [16]
-  double* rdk = sn + RR_KMAX / 2;                       // [32] 1 / diag of the k x k factor
-  float* d32 = reinterpret_cast<float*>(rdk + RR_KMAX); // [96]
-  float* e32 = d32 + RR_MMAX;                           // [96]
-  int* perm = reinterpret_cast<int*>(e32 + RR_MMAX);    // [32]
-  __shared__ int fail, dropped, nrot;
-  __shared__ double sh_alpha, sh_beta, sh_v0, sh_K, sh_lo, sh_hi;
+  double* MA = reinterpret_cast<double*>(smem);           // [96][RR_LD]: A, Y, M (lower) + R^T (upper)
+  double* RB = MA + RR_MMAX * RR_LD;                      // [96][RR_LD]: B, R (lower); then FP32 J, V
+  double* XD = RB + RR_MMAX * RR_LD;                      // [96][RR_KLD]: X, X'
+  double* YD = XD + RR_MMAX * RR_KLD;                     // [96][RR_KLD]: M X, M X', Z, C
+  double* sc = YD + RR_MMAX * RR_KLD;                     // [96] unit-diagonal scaling
+  double* rdg = sc + RR_MMAX;                             // [96] 1 / diag(R)
+  double* fv = rdg + RR_MMAX;                             // [96] multipliers of one step
+  double* th = fv + RR_MMAX;                              // [32] Rayleigh quotients
+  double* csd = th + RR_KMAX;                             // [16] k x k rotations
+  double* snd = csd + RR_KMAX / 2;                        // [16]
+  float* lam = reinterpret_cast<float*>(snd + RR_KMAX / 2);  // [96] FP32 eigenvalues of M
+  float* dd32 = lam + RR_MMAX;                            // [96] tridiagonal: diagonal
+  float* ee32 = dd32 + RR_MMAX;                           // [96] off-diagonal
+  float* e2f = ee32 + RR_MMAX;                            // [96] squared off-diagonal
+  float* bet32 = e2f + RR_MMAX;                           // [96] reflector scalars
+  float* pv32 = bet32 + RR_MMAX;                          // [96] work vector
+  int* sel = reinterpret_cast<int*>(pv32 + RR_MMAX);      // [32]
+  int* perm = sel + RR_KMAX;                              // [32]
+  int* rk = perm + RR_KMAX;                               // [96] rank of each FP32 eigenvalue
+  int* pp = rk + RR_MMAX;                                 // [48] pairs of one Jacobi step
+  int* qq = pp + RR_MMAX / 2;                             // [48]
+  // lower triangle of order 96 in row-major order: entry (r, l), l <= r, packed r << 8 | l;
+  // every smaller triangle is a prefix of it
+  unsigned short* tri = reinterpret_cast<unsigned short*>(qq + RR_MMAX / 2);  // [4656]
+  // FP32 views of the RB region once R has been moved out of it (J, V: 37,248 B each):
+  // J holds float(M), then T and the reflectors; V the eigenvectors of M
+  float* J = reinterpret_cast<float*>(RB);                // [96][RR_LDF]
+  float* V = J + RR_MMAX * RR_LDF;                        // [96][RR_LDF]
+  // after the FP32 sweeps: J's region holds R32 and CC, V's region the k x k work
+  float* R32 = J;                                         // [96][RR_KLD] FP32 residual
+  float* CC = J + RR_MMAX * RR_KLD;                       // [96][RR_KLD] correction coefficients
+  double* H = reinterpret_cast<double*>(V);               // [32][RR_KLD]
+  double* Vk = H + RR_KMAX * RR_KLD;                      // [32][RR_KLD]
+  double* Wk = Vk + RR_KMAX * RR_KLD;                     // [32][RR_KLD]
+  // k x k work of step 8 in the J region (R32 and CC are dead by then)
+  double* D64 = reinterpret_cast<double*>(J);             // [32][RR_KLD]
+  double* K64 = D64 + RR_KMAX * RR_KLD;                   // [32][RR_KLD]
+  float* E32 = reinterpret_cast<float*>(K64 + RR_KMAX * RR_KLD);  // [32][RR_KLD]
+  float* D32 = E32 + RR_KMAX * RR_KLD;                    // [32][RR_KLD]
+  __shared__ int fail, dropped;
+  __shared__ float lmax, shK, shlo, shhi;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int k = a.k;
+  const Tiling tk(k, lane);
   int m = a.m;
   if (tid == 0) dropped = 0;
+  for (int r = wid; r < a.m; r += RR_NW)
+    for (int l = lane; l <= r; l += 32) tri[r * (r + 1) / 2 + l] = (unsigned short)((r << 8) | l);
 
-  // ---------------------------------------------------------------- 1. scale, Cholesky
+  // ------------------------------------------ 1-2. scale, Cholesky with the forward solve
   for (int attempt = 0; attempt < 2; ++attempt) {
+    const FastDiv fdv(m);
     __syncthreads();
-    for (int q = tid; q < m * m; q += RR_T) {
-      const int r = q / m, c = q - r * m;
-      M[r * RR_LD + c] = 0.5 * (a.G[r * a.m + c] + a.G[c * a.m + r]);
-      R[r * RR_LD + c] = 0.5 * (a.G[a.m * a.m + r * a.m + c] + a.G[a.m * a.m + c * a.m + r]);
-    }
+    for (int r = wid; r < m; r += RR_NW)
+      for (int c = lane; c < m; c += 32) {
+        MA[r * RR_LD + c] = 0.5 * (a.G[r * a.m + c] + a.G[c * a.m + r]);
+        RB[r * RR_LD + c] = 0.5 * (a.G[a.m * a.m + r * a.m + c] + a.G[a.m * a.m + c * a.m + r]);
+      }
     if (tid == 0) fail = 0;
     __syncthreads();
     for (int r = tid; r < m; r += RR_T) {
-      const double dg = R[r * RR_LD + r];
+      const double dg = RB[r * RR_LD + r];
       if (!(dg > 0.0) || !isfinite(dg)) fail = 1;
       sc[r] = (dg > 0.0) ? frsqrt(dg) : 0.0;
     }
     __syncthreads();
     if (!fail) {
-      for (int q = tid; q < m * m; q += RR_T) {
-        const int r = q / m, c = q - r * m;
-        M[r * RR_LD + c] *= sc[r] * sc[c];
-        R[r * RR_LD + c] *= sc[r] * sc[c];
-      }
+      for (int r = wid; r < m; r += RR_NW)
+        for (int c = lane; c < m; c += 32) {
+          const double s2 = sc[r] * sc[c];
+          MA[r * RR_LD + c] *= s2;
+          RB[r * RR_LD + c] *= s2;
+        }
       __syncthreads();
-      // right-looking Cholesky: lower factor in R
+      // Right-looking Cholesky B = R R^T with unscaled columns c (R(:, j) = c / sqrt(piv)),
+      // carrying the forward solve Y = R^-1 A along: both updates use f_i = c_i / piv.
       for (int j = 0; j < m; ++j) {
-        if (tid == 0) {
-          const double piv = R[j * RR_LD + j];
-          if (!(piv > DEP_TOL)) {
-            fail = 1;
-          } else {
-            const double rj = frsqrt(piv);
-            R[j * RR_LD + j] = piv * rj;
-            rdg[j] = rj;
+        if (wid == 0) {
+          const double piv = RB[j * RR_LD + j];
+          if (piv > DEP_TOL) {
+            const double ip = frcp(piv);
+            for (int i = j + 1 + lane; i < m; i += 32) fv[i] = RB[i * RR_LD + j] * ip;
           }
         }
         __syncthreads();
-        if (fail) break;
-        const double rj = rdg[j];
-        for (int i = j + 1 + tid; i < m; i += RR_T) R[i * RR_LD + j] *= rj;
-        __syncthreads();
-        const int t = m - j - 1;
-        for (int q = tid; q < t * t; q += RR_T) {
-          const int i = j + 1 + q / t, l = j + 1 + q % t;
-          if (l <= i) R[i * RR_LD + l] = fma(-R[i * RR_LD + j], R[l * RR_LD + j], R[i * RR_LD + l]);
+        if (!(RB[j * RR_LD + j] > DEP_TOL)) break;       // same value in every thread
+        const int t = m - j - 1, nb = t * (t + 1) / 2;
+        for (int q = tid; q < nb + t * m; q += RR_T) {
+          if (q < nb) {                                  // trailing B: j < l <= i < m
+            const int e = tri[q], i = j + 1 + (e >> 8), l = j + 1 + (e & 255);
+            RB[i * RR_LD + l] = fma(-fv[i], RB[l * RR_LD + j], RB[i * RR_LD + l]);
+          } else {                                       // rows i > j of Y
+            const int q2 = q - nb, i1 = (int)fdv.div((unsigned)q2), c = q2 - i1 * m, i = j + 1 + i1;
+            MA[i * RR_LD + c] = fma(-fv[i], MA[j * RR_LD + c], MA[i * RR_LD + c]);
+          }
         }
         __syncthreads();
       }
+      for (int j = tid; j < m; j += RR_T) {
+        const double piv = RB[j * RR_LD + j];
+        if (!(piv > DEP_TOL)) fail = 1;
+        rdg[j] = (piv > 0.0) ? frsqrt(piv) : 0.0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (!fail) break;
     if (attempt == 0 && a.m_nop > 0 && a.m_nop < a.m) {
       m = a.m_nop;
@@ -226,295 +307,385 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     if (tid == 0) *a.status = 2;
     return;
   }
+  for (int i = wid; i < m; i += RR_NW)              // R(i, c) = c_i rdg_c, Y(i, :) *= rdg_i
+    for (int c = lane; c < m; c += 32) {
+      if (c < i) RB[i * RR_LD + c] *= rdg[c];
+      MA[i * RR_LD + c] *= rdg[i];
+    }
+  __syncthreads();
 
-  // ---------------------------------------------------------------- 2. M = R^-1 M R^-T
-  for (int i = 0; i < m; ++i) {                 // Y = R^-1 M: rows in order
-    for (int c = tid; c < m; c += RR_T) M[i * RR_LD + c] *= rdg[i];
+  // ------------------------------------------ 3. M = Y R^-T (lower triangle), columns in order
+  for (int i = 0; i < m; ++i) {
+    if (wid == 0)
+      for (int r = i + lane; r < m; r += 32) {
+        const double v = MA[r * RR_LD + i] * rdg[i];  // final M(r, i)
+        MA[r * RR_LD + i] = v;
+        fv[r] = v;
+      }
     __syncthreads();
     const int t = m - i - 1;
-    for (int q = tid; q < t * m; q += RR_T) {
-      const int l = i + 1 + q / m, c = q % m;
-      M[l * RR_LD + c] = fma(-R[l * RR_LD + i], M[i * RR_LD + c], M[l * RR_LD + c]);
+    for (int q = tid; q < t * (t + 1) / 2; q += RR_T) {   // i < l <= r < m
+      const int e = tri[q], r = i + 1 + (e >> 8), l = i + 1 + (e & 255);
+      MA[r * RR_LD + l] = fma(-fv[r], RB[l * RR_LD + i], MA[r * RR_LD + l]);
     }
     __syncthreads();
   }
-  for (int i = 0; i < m; ++i) {                 // M = Y R^-T: columns in order, rows >= col
-    for (int r = i + tid; r < m; r += RR_T) M[r * RR_LD + i] *= rdg[i];
-    __syncthreads();
-    const int t = m - i - 1;
-    for (int q = tid; q < t * t; q += RR_T) {
-      const int l = i + 1 + q / t, r = i + 1 + q % t;
-      if (r >= l) M[r * RR_LD + l] = fma(-M[r * RR_LD + i], R[l * RR_LD + i], M[r * RR_LD + l]);
-    }
-    __syncthreads();
-  }
-  // (the tridiagonal reduction below reads the lower triangle only)
+  for (int r = wid; r < m; r += RR_NW)              // strict upper of MA <- R^T
+    for (int c = r + 1 + lane; c < m; c += 32) MA[r * RR_LD + c] = RB[c * RR_LD + r];
+  __syncthreads();
 
-  // ---------------------------------------------------------------- 3. tridiagonal
+  // ------------------------------------------ 4. FP32 eigen-decomposition of M
+  // 4a. Householder reduction of float(M) (full storage in J) to a tridiagonal T; the
+  //     reflector vectors stay below the subdiagonal of J
+  for (int r = wid; r < m; r += RR_NW)
+    for (int c = lane; c < m; c += 32) J[r * RR_LDF + c] = (float)symv(MA, r, c);
+  __syncthreads();
   for (int j = 0; j + 2 < m; ++j) {
     const int n1 = m - j - 1;
-    double* col = M + (j + 1) * RR_LD + j;       // x_i = col[i * RR_LD]
-    if (tid < 32) {
-      double s = 0.0;
-      for (int i = tid; i < n1; i += 32) s = fma(col[i * RR_LD], col[i * RR_LD], s);
+    float* col = J + (j + 1) * RR_LDF + j;          // x_i = col[i * RR_LDF], i < n1
+    if (wid == 0) {
+      float s = 0.0f;
+      for (int i = lane; i < n1; i += 32) s = fmaf(col[i * RR_LDF], col[i * RR_LDF], s);
       s = warp_sum(s);
-      if (tid == 0) {
-        const double x0 = col[0];
-        const double tail = s - x0 * x0;
-        if (!(tail > 0.0)) {
-          sh_beta = 0.0;
-          sh_alpha = x0;
-          sh_v0 = 0.0;
-        } else {
-          const double nrm = s * frsqrt(s);
-          const double al = (x0 >= 0.0) ? -nrm : nrm;
-          const double v0 = x0 - al;
-          sh_alpha = al;
-          sh_v0 = v0;
-          sh_beta = 2.0 * frcp(fma(v0, v0, tail));
+      if (lane == 0) {
+        const float x0 = col[0];
+        const float tail = s - x0 * x0;
+        float al = x0, be = 0.0f;
+        if (tail > 0.0f) {
+          const float nrm = sqrtf(s);
+          al = (x0 >= 0.0f) ? -nrm : nrm;
+          const float v0 = x0 - al;
+          be = 2.0f / fmaf(v0, v0, tail);
+          col[0] = v0;
         }
+        dd32[j] = J[j * RR_LDF + j];
+        ee32[j] = al;
+        bet32[j] = be;
       }
     }
     __syncthreads();
-    const double beta = sh_beta;
-    if (tid == 0) {
-      dd[j] = M[j * RR_LD + j];
-      ee[j] = sh_alpha;
-      bet[j] = beta;
-      if (beta != 0.0) col[0] = sh_v0;          // reflector vector stored below the diagonal
-    }
-    __syncthreads();
-    if (beta == 0.0) continue;
-    double* A1 = M + (j + 1) * RR_LD + (j + 1);  // trailing n1 x n1 block
-    // p = beta A1 v  (eight threads per row; A1 is kept in its lower triangle)
-    for (int row0 = 0; row0 < n1; row0 += RR_T / 8) {
-      const int row = row0 + (tid >> 3), part = tid & 7;
-      double s = 0.0;
-      if (row < n1)
-        for (int c = part; c < n1; c += 8) {
-          const double av = (c <= row) ? A1[row * RR_LD + c] : A1[c * RR_LD + row];
-          s = fma(av, col[c * RR_LD], s);
-        }
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      if (row < n1 && part == 0) pv[row] = beta * s;
-    }
-    __syncthreads();
-    if (tid < 32) {
-      double s = 0.0;
-      for (int i = tid; i < n1; i += 32) s = fma(col[i * RR_LD], pv[i], s);
+    const float beta = bet32[j];
+    if (beta == 0.0f) continue;
+    float* A1 = J + (j + 1) * RR_LDF + (j + 1);      // trailing n1 x n1 block
+    for (int r = wid; r < n1; r += RR_NW) {           // p = beta A1 v
+      float s = 0.0f;
+      for (int c = lane; c < n1; c += 32) s = fmaf(A1[r * RR_LDF + c], col[c * RR_LDF], s);
       s = warp_sum(s);
-      if (tid == 0) sh_K = 0.5 * beta * s;
+      if (lane == 0) pv32[r] = beta * s;
     }
     __syncthreads();
-    for (int i = tid; i < n1; i += RR_T) pv[i] = fma(-sh_K, col[i * RR_LD], pv[i]);   // w
+    if (wid == 0) {
+      float s = 0.0f;
+      for (int i = lane; i < n1; i += 32) s = fmaf(col[i * RR_LDF], pv32[i], s);
+      s = warp_sum(s);
+      if (lane == 0) shK = 0.5f * beta * s;
+    }
     __syncthreads();
-    for (int q = tid; q < n1 * n1; q += RR_T) {
-      const int r = q / n1, c = q - r * n1;
-      if (c <= r)
-        A1[r * RR_LD + c] = fma(-col[r * RR_LD], pv[c], fma(-pv[r], col[c * RR_LD], A1[r * RR_LD + c]));
+    const float K = shK;
+    for (int r = wid; r < n1; r += RR_NW) {           // A1 -= v w^T + w v^T, w = p - K v
+      const float vr = col[r * RR_LDF], wr = fmaf(-K, vr, pv32[r]);
+      for (int c = lane; c < n1; c += 32) {
+        const float vc = col[c * RR_LDF], wc = fmaf(-K, vc, pv32[c]);
+        A1[r * RR_LDF + c] = fmaf(-vr, wc, fmaf(-wr, vc, A1[r * RR_LDF + c]));
+      }
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (m >= 2) {
-      dd[m - 2] = M[(m - 2) * RR_LD + (m - 2)];
-      ee[m - 2] = M[(m - 1) * RR_LD + (m - 2)];
-      bet[m - 2] = 0.0;
+      dd32[m - 2] = J[(m - 2) * RR_LDF + (m - 2)];
+      ee32[m - 2] = J[(m - 1) * RR_LDF + (m - 2)];
+      bet32[m - 2] = 0.0f;
     }
-    dd[m - 1] = M[(m - 1) * RR_LD + (m - 1)];
-    ee[m - 1] = 0.0;
-    double lo = 1e300, hi = -1e300;               // Gershgorin interval
+    dd32[m - 1] = J[(m - 1) * RR_LDF + (m - 1)];
+    ee32[m - 1] = 0.0f;
+    float lo = 3e38f, hi = -3e38f;                  // Gershgorin interval
     for (int i = 0; i < m; ++i) {
-      const double rad = fabs(ee[i]) + (i > 0 ? fabs(ee[i - 1]) : 0.0);
-      lo = fmin(lo, dd[i] - rad);
-      hi = fmax(hi, dd[i] + rad);
+      const float rad = fabsf(ee32[i]) + (i > 0 ? fabsf(ee32[i - 1]) : 0.0f);
+      lo = fminf(lo, dd32[i] - rad);
+      hi = fmaxf(hi, dd32[i] + rad);
     }
-    sh_lo = lo;
-    sh_hi = hi;
+    shlo = lo;
+    shhi = hi;
   }
   __syncthreads();
-  for (int i = tid; i < m; i += RR_T) {
-    e2[i] = ee[i] * ee[i];
-    d32[i] = (float)dd[i];
-    e32[i] = (float)(ee[i] * ee[i]);
-  }
+  for (int i = tid; i < m; i += RR_T) e2f[i] = ee32[i] * ee32[i];
   __syncthreads();
-  const double tn = fmax(fabs(sh_lo), fabs(sh_hi));
-  const double tiny = 4.0 * 2.2e-16 * tn + 1e-300;
-
-  // ---------------------------------------------------------------- 4. FP32 multisection shifts
-  for (int j = wid; j < k; j += RR_T / 32) {
-    float lo = (float)sh_lo, hi = (float)sh_hi;
+  const float tn = fmaxf(fabsf(shlo), fabsf(shhi));
+  // 4b. every eigenvalue of T by multisection on Sturm counts (32 points per warp and round)
+  for (int j = wid; j < m; j += RR_NW) {
+    float lo = shlo, hi = shhi;
     lo -= 1e-6f * fabsf(lo) + 1e-30f;
     hi += 1e-6f * fabsf(hi) + 1e-30f;
-    const float stop = 4.0f * 6e-8f * (float)tn + 1e-30f;
+    const float stop = 4.0f * 6e-8f * tn + 1e-30f;
     for (int round = 0; round < 10 && hi - lo > stop; ++round) {
       const float w = (hi - lo) * (1.0f / 33.0f);
       const float x = lo + w * (float)(lane + 1);
-      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f(d32, e32, m, x) > j);
-      const int first = above ? __ffs(above) - 1 : 32;     // first point with more than j below
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f(dd32, e2f, m, x) > j);
+      const int first = above ? __ffs(above) - 1 : 32;   // first point with more than j below
       const float nlo = (first == 0) ? lo : lo + w * (float)first;
       const float nhi = (first == 32) ? hi : lo + w * (float)(first + 1);
       lo = nlo;
       hi = nhi;
     }
-    if (lane == 0) lam[j] = 0.5 * ((double)lo + (double)hi);
+    if (lane == 0) lam[j] = 0.5f * (lo + hi);
   }
   __syncthreads();
-
-  // ---------------------------------------------------------------- 5. inverse iteration
-  if (tid < k) {
-    double b[RR_MMAX], f[RR_MMAX], ri[RR_MMAX], u1[RR_MMAX], u2[RR_MMAX];
-    unsigned char sw[RR_MMAX];
-    tri_factor(dd, ee, m, lam[tid], tiny, f, sw, ri, u1, u2);
-    for (int i = 0; i < m; ++i) b[i] = 1.0 + 0.25 * (double)(((i + 1) * (tid + 3) * 7919) % 97) / 97.0;
-    for (int rep = 0; rep < 4; ++rep) {
-      tri_solve(m, f, sw, ri, u1, u2, b);
-      double nrm0 = 0.0, nrm1 = 0.0;
-      for (int i = 0; i + 1 < m; i += 2) {
-        nrm0 = fmax(nrm0, fabs(b[i]));
-        nrm1 = fmax(nrm1, fabs(b[i + 1]));
-      }
-      if (m & 1) nrm0 = fmax(nrm0, fabs(b[m - 1]));
-      const double nrm = fmax(nrm0, nrm1);
-      const double inv = (nrm > 0.0 && isfinite(nrm)) ? frcp(nrm) : 1.0;
-      for (int i = 0; i < m; ++i) b[i] *= inv;
-    }
-    for (int i = 0; i < m; ++i) Z[i * RR_KLD + tid] = b[i];
+  // 4c. an eigenvector of T per eigenvalue by three steps of inverse iteration (start
+  //     vectors differ per index, so a cluster's vectors span the cluster's subspace)
+  const float clus = 1e-3f * tn;                    // eigenvalues closer than this: a cluster
+  if (tid < m) {
+    float b[RR_MMAX];
+    for (int i = 0; i < m; ++i) b[i] = 1.0f + 0.25f * (float)(((i + 1) * (tid + 3) * 7919) % 97) / 97.0f;
+    tri_inverse_iteration(dd32, ee32, m, lam[tid], 4.0f * 6e-8f * tn + 1e-30f, 3, b);
+    for (int i = 0; i < m; ++i) V[i * RR_LDF + tid] = b[i];
   }
   __syncthreads();
-
-  // ---------------------------------------------------------------- 6. Cholesky QR twice, k x k Rayleigh-Ritz
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int q = tid; q < k * k; q += RR_T) {        // G = Z^T Z (lower part used)
-      const int i = q / k, j = q - i * k;
-      if (j <= i) {
-        double s0 = 0.0, s1 = 0.0;
-        int r = 0;
-        for (; r + 1 < m; r += 2) {
-          s0 = fma(Z[r * RR_KLD + i], Z[r * RR_KLD + j], s0);
-          s1 = fma(Z[(r + 1) * RR_KLD + i], Z[(r + 1) * RR_KLD + j], s1);
-        }
-        if (r < m) s0 = fma(Z[r * RR_KLD + i], Z[r * RR_KLD + j], s0);
-        H[i * RR_KLD + j] = s0 + s1;
+  // 4d. orthonormalise within clusters (modified Gram-Schmidt), normalise the rest
+  for (int j = wid; j < m; j += RR_NW) {
+    if (j > 0 && lam[j] - lam[j - 1] < clus) continue;   // not the first of its cluster
+    int e = j + 1;
+    while (e < m && lam[e] - lam[e - 1] < clus) ++e;
+    for (int i = j; i < e; ++i) {
+      for (int l = j; l < i; ++l) {
+        float d = 0.0f;
+        for (int r = lane; r < m; r += 32) d = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d);
+        d = warp_sum(d);
+        for (int r = lane; r < m; r += 32) V[r * RR_LDF + i] = fmaf(-d, V[r * RR_LDF + l], V[r * RR_LDF + i]);
+        __syncwarp();
       }
-    }
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {                   // G = L L^T, right-looking
-      if (tid == 0) {
-        const double piv = H[j * RR_KLD + j];
-        const double rj = (piv > 0.0) ? frsqrt(piv) : 0.0;
-        H[j * RR_KLD + j] = piv * rj;
-        rdk[j] = rj;
-      }
-      __syncthreads();
-      const double rj = rdk[j];
-      for (int i = j + 1 + tid; i < k; i += RR_T) H[i * RR_KLD + j] *= rj;
-      __syncthreads();
-      const int t = k - j - 1;
-      for (int q = tid; q < t * t; q += RR_T) {
-        const int i = j + 1 + q / t, l = j + 1 + q % t;
-        if (l <= i) H[i * RR_KLD + l] = fma(-H[i * RR_KLD + j], H[l * RR_KLD + j], H[i * RR_KLD + l]);
-      }
-      __syncthreads();
-    }
-    for (int j = 0; j < k; ++j) {                   // Z <- Z L^-T, columns in order
-      for (int r = tid; r < m; r += RR_T) Z[r * RR_KLD + j] *= rdk[j];
-      __syncthreads();
-      const int t = k - j - 1;
-      for (int q = tid; q < t * m; q += RR_T) {
-        const int l = j + 1 + q / m, r = q % m;
-        Z[r * RR_KLD + l] = fma(-Z[r * RR_KLD + j], H[l * RR_KLD + j], Z[r * RR_KLD + l]);
-      }
-      __syncthreads();
+      float n2 = 0.0f;
+      for (int r = lane; r < m; r += 32) n2 = fmaf(V[r * RR_LDF + i], V[r * RR_LDF + i], n2);
+      n2 = warp_sum(n2);
+      const float inv = (n2 > 0.0f) ? rsqrtf(n2) : 0.0f;
+      for (int r = lane; r < m; r += 32) V[r * RR_LDF + i] *= inv;
+      __syncwarp();
     }
   }
-  // H = Z^T T Z
-  for (int q = tid; q < k * k; q += RR_T) {
-    const int i = q / k, j = q - i * k;
+  __syncthreads();
+  // 4e. back-transformation by the reflectors, last to first, one warp per vector
+  for (int i = wid; i < m; i += RR_NW) {
+    for (int j = m - 3; j >= 0; --j) {
+      const float beta = bet32[j];
+      if (beta == 0.0f) continue;
+      const int n1 = m - j - 1;
+      const float* col = J + (j + 1) * RR_LDF + j;
+      float s = 0.0f;
+      for (int r = lane; r < n1; r += 32) s = fmaf(col[r * RR_LDF], V[(j + 1 + r) * RR_LDF + i], s);
+      s = beta * warp_sum(s);
+      for (int r = lane; r < n1; r += 32)
+        V[(j + 1 + r) * RR_LDF + i] = fmaf(-col[r * RR_LDF], s, V[(j + 1 + r) * RR_LDF + i]);
+      __syncwarp();
+    }
+  }
+
+  // ------------------------------------------ 5. the k smallest FP32 eigenpairs
+  // (multisection returns the eigenvalues in ascending order)
+  if (tid < m) rk[tid] = tid;
+  if (tid < k) sel[tid] = tid;
+  if (tid == 0) lmax = fmaxf(fabsf(lam[0]), fabsf(lam[m - 1]));
+  __syncthreads();
+
+  // ------------------------------------------ 6. X = V(:, sel) in FP64, Y = M X
+  FOR_RC(tk, m, k, wid) XD[r * RR_KLD + c] = (double)V[r * RR_LDF + sel[c]];
+  __syncthreads();
+  mul_mx(MA, XD, YD, m, tk, k, wid);
+  __syncthreads();
+
+  // ------------------------------------------ 7. one correction of X from the FP64 residual
+  for (int j = wid; j < k; j += RR_NW) {
+    double xy = 0.0, xx = 0.0;
+    for (int r = lane; r < m; r += 32) {
+      xy = fma(XD[r * RR_KLD + j], YD[r * RR_KLD + j], xy);
+      xx = fma(XD[r * RR_KLD + j], XD[r * RR_KLD + j], xx);
+    }
+    xy = warp_sum(xy);
+    xx = warp_sum(xx);
+    if (lane == 0) th[j] = xy * frcp(xx);
+  }
+  __syncthreads();
+  FOR_RC(tk, m, k, wid) R32[r * RR_KLD + c] = (float)fma(-th[c], XD[r * RR_KLD + c], YD[r * RR_KLD + c]);
+  __syncthreads();
+  {
+    const float delta = 64.0f * 6e-8f * lmax;      // unwanted: beyond the FP32 resolution
+    const float delta_w = 1e-3f * lmax;             // wanted pairs: well separated only
+    FOR_RC(tk, m, k, wid) {                         // r: eigenpair i, c: column j
+      float f0 = 0.0f, f1 = 0.0f;
+      int q = 0;
+      for (; q + 1 < m; q += 2) {
+        f0 = fmaf(V[q * RR_LDF + r], R32[q * RR_KLD + c], f0);
+        f1 = fmaf(V[(q + 1) * RR_LDF + r], R32[(q + 1) * RR_KLD + c], f1);
+      }
+      if (q < m) f0 = fmaf(V[q * RR_LDF + r], R32[q * RR_KLD + c], f0);
+      const float gap = (float)th[c] - lam[r];
+      // close wanted directions are mixed by the k x k Rayleigh-Ritz below; correcting
+      // only well-separated ones keeps X'^T X' - I of order eps_32 |M| / delta_w
+      CC[r * RR_KLD + c] = (fabsf(gap) > (rk[r] >= k ? delta : delta_w)) ? (f0 + f1) / gap : 0.0f;
+    }
+  }
+  __syncthreads();
+  FOR_RC(tk, m, k, wid) {                           // X' = X + V CC
+    float d0 = 0.0f, d1 = 0.0f;
+    int i = 0;
+    for (; i + 1 < m; i += 2) {
+      d0 = fmaf(V[r * RR_LDF + i], CC[i * RR_KLD + c], d0);
+      d1 = fmaf(V[r * RR_LDF + i + 1], CC[(i + 1) * RR_KLD + c], d1);
+    }
+    if (i < m) d0 = fmaf(V[r * RR_LDF + i], CC[i * RR_KLD + c], d0);
+    XD[r * RR_KLD + c] += (double)(d0 + d1);
+  }
+  __syncthreads();
+  mul_mx(MA, XD, YD, m, tk, k, wid);                // Y' = M X'
+  __syncthreads();
+
+  // ------------------------------------------ 8. orthonormalise, k x k Rayleigh-Ritz
+  // G = X'^T X' = I + E with |E| <= 1e-4, so T = G^-1/2 = I + D with
+  // D = -E/2 + 3/8 E^2 - 5/16 E^3 to O(|E|^4) (E^2, E^3 in FP32); H = T H' T with
+  // H' = X'^T M X', in FP64.
+  FOR_RC(tk, 2 * k, k, wid) {
+    const int which = (r >= k), i = r - which * k;
+    if (which == 0 && c < i) continue;
+    const double* B2 = which ? YD : XD;
+    double s0 = 0.0, s1 = 0.0;
+    int q = 0;
+    for (; q + 1 < m; q += 2) {
+      s0 = fma(XD[q * RR_KLD + i], B2[q * RR_KLD + c], s0);
+      s1 = fma(XD[(q + 1) * RR_KLD + i], B2[(q + 1) * RR_KLD + c], s1);
+    }
+    if (q < m) s0 = fma(XD[q * RR_KLD + i], B2[q * RR_KLD + c], s0);
+    const double v = s0 + s1;
+    if (which) {
+      H[i * RR_KLD + c] = v;
+    } else {
+      const double e = v - (i == c ? 1.0 : 0.0);
+      D64[i * RR_KLD + c] = e;
+      D64[c * RR_KLD + i] = e;
+      E32[i * RR_KLD + c] = (float)e;
+      E32[c * RR_KLD + i] = (float)e;
+    }
+  }
+  __syncthreads();
+  FOR_RC(tk, k, k, wid) {                           // E^2 (FP32, into D32)
+    float s = 0.0f;
+    for (int l = 0; l < k; ++l) s = fmaf(E32[r * RR_KLD + l], E32[l * RR_KLD + c], s);
+    D32[r * RR_KLD + c] = s;
+  }
+  __syncthreads();
+  FOR_RC(tk, k, k, wid) {                           // D = -E/2 + 3/8 E^2 - 5/16 E^3
+    float e3 = 0.0f;
+    for (int l = 0; l < k; ++l) e3 = fmaf(E32[r * RR_KLD + l], D32[l * RR_KLD + c], e3);
+    K64[r * RR_KLD + c] = fma(-0.5, D64[r * RR_KLD + c], (double)fmaf(-0.3125f, e3, 0.375f * D32[r * RR_KLD + c]));
+  }
+  __syncthreads();
+  FOR_RC(tk, k, k, wid) {
+    const double d = K64[r * RR_KLD + c];
+    D64[r * RR_KLD + c] = d;
+    D32[r * RR_KLD + c] = (float)d;
+  }
+  __syncthreads();
+  FOR_RC(tk, k, k, wid) {                           // K = H' D
     double s = 0.0;
-    for (int r = 0; r < m; ++r) {
-      double tz = dd[r] * Z[r * RR_KLD + j];
-      if (r > 0) tz = fma(ee[r - 1], Z[(r - 1) * RR_KLD + j], tz);
-      if (r + 1 < m) tz = fma(ee[r], Z[(r + 1) * RR_KLD + j], tz);
-      s = fma(Z[r * RR_KLD + i], tz, s);
-    }
-    H[i * RR_KLD + j] = s;
+    for (int l = 0; l < k; ++l) s = fma(H[r * RR_KLD + l], D64[l * RR_KLD + c], s);
+    K64[r * RR_KLD + c] = s;
+  }
+  __syncthreads();
+  FOR_RC(tk, k, k, wid) {                           // H = H' + K + D (H' + K)
+    double s = K64[r * RR_KLD + c];
+    for (int l = 0; l < k; ++l) s = fma(D64[r * RR_KLD + l], H[l * RR_KLD + c] + K64[l * RR_KLD + c], s);
+    Wk[r * RR_KLD + c] = H[r * RR_KLD + c] + s;
   }
   __syncthreads();
   const int kp = k + (k & 1);
-  for (int q = tid; q < kp * kp; q += RR_T) {
-    const int i = q / kp, j = q - i * kp;
-    if (i < k && j < k) {
-      if (i < j) {
-        const double v = 0.5 * (H[i * RR_KLD + j] + H[j * RR_KLD + i]);
-        H[i * RR_KLD + j] = v;
-        H[j * RR_KLD + i] = v;
-      }
-    } else {
-      H[i * RR_KLD + j] = (i == j) ? 1e300 : 0.0;
+  const int kh = kp / 2;
+  for (int i = wid; i < kp; i += RR_NW)
+    for (int j = lane; j < kp; j += 32) {
+      double v;
+      if (i < k && j < k) v = 0.5 * (Wk[i * RR_KLD + j] + Wk[j * RR_KLD + i]);
+      else v = (i == j) ? 1e300 : 0.0;
+      H[i * RR_KLD + j] = v;
+      Vk[i * RR_KLD + j] = (i == j) ? 1.0 : 0.0;
     }
-    Vk[i * RR_KLD + j] = (i == j) ? 1.0 : 0.0;
-  }
   __syncthreads();
+  // Cyclic Jacobi in FP64: the angle is taken in FP32 (it only has to shrink the coupling),
+  // the rotation itself is exactly orthogonal in FP64; couplings below 1e-13 of the
+  // diagonal entries cannot change an eigenvalue beyond rounding and are left alone.
   if (kp > 1) {
+    const FastDiv fkp(kp);
+    const int nblk = kh * (kh + 1) / 2;
     for (int sweep = 0; sweep < 30; ++sweep) {
-      if (tid == 0) nrot = 0;
-      __syncthreads();
+      int nrot = 0;
       for (int step = 0; step < kp - 1; ++step) {
-        for (int i = tid; i < kp / 2; i += RR_T) {
+        int rot = 0;
+        if (tid < kh) {
           int p, q;
-          jacobi_pair_k(step, i, kp, p, q);
+          jacobi_pair_k(step, tid, kp, p, q);
+          pp[tid] = p;
+          qq[tid] = q;
           const double apq = H[p * RR_KLD + q], app = H[p * RR_KLD + p], aqq = H[q * RR_KLD + q];
           double c = 1.0, s = 0.0;
-          // rotate unless the coupling is below 1e-13 of the diagonal entries: the
-          // eigenvalue change it could make is then below rounding
           if (fabs(apq) > 1e-13 * (fabs(app) + fabs(aqq)) + 1e-300) {
-            const double tau = (aqq - app) * frcp(2.0 * apq);
-            double t;
-            if (fabs(tau) > 1e14) {
-              t = 0.5 / tau;
+            rot = 1;
+            const float tau = __fdividef((float)(aqq - app), 2.0f * (float)apq);
+            float t32;
+            if (fabsf(tau) > 1e9f) {
+              t32 = __fdividef(0.5f, tau);
             } else {
-              const double u = fma(tau, tau, 1.0);
-              const double root = u * frsqrt(u);
-              t = (tau >= 0.0) ? frcp(tau + root) : -frcp(root - tau);
+              const float u = fmaf(tau, tau, 1.0f);
+              t32 = copysignf(__fdividef(1.0f, fabsf(tau) + u * rsqrtf(u)), tau);
             }
+            const double t = (double)t32;
             c = frsqrt(fma(t, t, 1.0));
             s = t * c;
-            atomicAdd(&nrot, 1);
           }
-          cs[i] = c;
-          sn[i] = s;
+          csd[tid] = c;
+          snd[tid] = s;
         }
-        __syncthreads();
-        for (int q2 = tid; q2 < (kp / 2) * kp; q2 += RR_T) {
-          const int i = q2 / kp, j = q2 - i * kp;
-          if (sn[i] == 0.0) continue;
-          int p, q;
-          jacobi_pair_k(step, i, kp, p, q);
-          const double x = H[p * RR_KLD + j], y = H[q * RR_KLD + j];
-          H[p * RR_KLD + j] = cs[i] * x - sn[i] * y;
-          H[q * RR_KLD + j] = sn[i] * x + cs[i] * y;
-        }
-        __syncthreads();
-        for (int q2 = tid; q2 < (kp / 2) * kp; q2 += RR_T) {
-          const int i = q2 / kp, r = q2 - i * kp;
-          if (sn[i] == 0.0) continue;
-          int p, q;
-          jacobi_pair_k(step, i, kp, p, q);
-          const double x = H[r * RR_KLD + p], y = H[r * RR_KLD + q];
-          H[r * RR_KLD + p] = cs[i] * x - sn[i] * y;
-          H[r * RR_KLD + q] = sn[i] * x + cs[i] * y;
-          const double vx = Vk[r * RR_KLD + p], vy = Vk[r * RR_KLD + q];
-          Vk[r * RR_KLD + p] = cs[i] * vx - sn[i] * vy;
-          Vk[r * RR_KLD + q] = sn[i] * vx + cs[i] * vy;
+        const int nstep = __syncthreads_count(rot);
+        nrot += nstep;
+        if (nstep == 0) continue;
+        for (int q2 = tid; q2 < nblk + kh * kp; q2 += RR_T) {
+          if (q2 < nblk) {
+            const int e = tri[q2], bb = e >> 8, ba = e & 255;
+            const double sa = snd[ba], sb = snd[bb];
+            if (sa == 0.0 && sb == 0.0) continue;
+            const int pa = pp[ba], qa = qq[ba], pb = pp[bb], qb = qq[bb];
+            const double ca = csd[ba], cb = csd[bb];
+            const double j00 = H[pa * RR_KLD + pb], j01 = H[pa * RR_KLD + qb];
+            const double j10 = H[qa * RR_KLD + pb], j11 = H[qa * RR_KLD + qb];
+            const double t00 = ca * j00 - sa * j10, t01 = ca * j01 - sa * j11;
+            const double t10 = sa * j00 + ca * j10, t11 = sa * j01 + ca * j11;
+            const double n00 = cb * t00 - sb * t01, n01 = sb * t00 + cb * t01;
+            const double n10 = cb * t10 - sb * t11, n11 = sb * t10 + cb * t11;
+            if (bb == ba) {
+              const double off = 0.5 * (n01 + n10);
+              H[pa * RR_KLD + pa] = n00;
+              H[qa * RR_KLD + qa] = n11;
+              H[pa * RR_KLD + qa] = off;
+              H[qa * RR_KLD + pa] = off;
+              continue;
+            }
+            H[pa * RR_KLD + pb] = n00;
+            H[pa * RR_KLD + qb] = n01;
+            H[qa * RR_KLD + pb] = n10;
+            H[qa * RR_KLD + qb] = n11;
+            H[pb * RR_KLD + pa] = n00;
+            H[qb * RR_KLD + pa] = n01;
+            H[pb * RR_KLD + qa] = n10;
+            H[qb * RR_KLD + qa] = n11;
+          } else {
+            const int q3 = q2 - nblk, ba = (int)fkp.div((unsigned)q3), r = q3 - ba * kp;
+            const double sa = snd[ba];
+            if (sa == 0.0) continue;
+            const double ca = csd[ba];
+            const int pa = pp[ba], qa = qq[ba];
+            const double vp = Vk[r * RR_KLD + pa], vq = Vk[r * RR_KLD + qa];
+            Vk[r * RR_KLD + pa] = ca * vp - sa * vq;
+            Vk[r * RR_KLD + qa] = sa * vp + ca * vq;
+          }
         }
         __syncthreads();
       }
       if (nrot == 0) break;
-      __syncthreads();
     }
   }
   for (int i = tid; i < k; i += RR_T) {
@@ -527,103 +698,86 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     perm[rank] = i;
   }
   __syncthreads();
-  // Z <- Z Vk[:, perm], row by row
-  for (int r = tid; r < m; r += RR_T) {
-    double zr[RR_KMAX];
-    for (int i = 0; i < k; ++i) zr[i] = Z[r * RR_KLD + i];
-    for (int j = 0; j < k; ++j) {
-      const int col = perm[j];
-      double s = 0.0;
-      for (int i = 0; i < k; ++i) s = fma(zr[i], Vk[i * RR_KLD + col], s);
-      Z[r * RR_KLD + j] = s;
+  FOR_RC(tk, k, k, wid) {                           // W = T Vk(:, perm) = Vk + D Vk (FP32 part)
+    const int pj = perm[c];
+    float s = 0.0f;
+    for (int l = 0; l < k; ++l) s = fmaf(D32[r * RR_KLD + l], (float)Vk[l * RR_KLD + pj], s);
+    Wk[r * RR_KLD + c] = Vk[r * RR_KLD + pj] + (double)s;
+  }
+  __syncthreads();
+  FOR_RC(tk, m, k, wid) {                           // Z = X' W
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < k; i += 2) {
+      s0 = fma(XD[r * RR_KLD + i], Wk[i * RR_KLD + c], s0);
+      s1 = fma(XD[r * RR_KLD + i + 1], Wk[(i + 1) * RR_KLD + c], s1);
     }
+    if (i < k) s0 = fma(XD[r * RR_KLD + i], Wk[i * RR_KLD + c], s0);
+    YD[r * RR_KLD + c] = s0 + s1;
   }
   __syncthreads();
 
-  // ---------------------------------------------------------------- 7. back-transform, C
-  // each warp applies all reflectors, last to first, to its own columns
-  for (int c = wid; c < k; c += RR_T / 32) {
-    for (int j = m - 3; j >= 0; --j) {
-      const double beta = bet[j];
-      if (beta == 0.0) continue;
-      const int n1 = m - j - 1;
-      const double* col = M + (j + 1) * RR_LD + j;
-      double s = 0.0;
-      for (int i = lane; i < n1; i += 32) s = fma(col[i * RR_LD], Z[(j + 1 + i) * RR_KLD + c], s);
-      s = beta * warp_sum(s);
-      for (int i = lane; i < n1; i += 32)
-        Z[(j + 1 + i) * RR_KLD + c] = fma(-col[i * RR_LD], s, Z[(j + 1 + i) * RR_KLD + c]);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  // C = R^-T Z: rows from the bottom, all columns in parallel
+  // ------------------------------------------ 9. C = R^-T Z (rows from the bottom), unscale
   for (int i = m - 1; i >= 0; --i) {
-    for (int c = tid; c < k; c += RR_T) Z[i * RR_KLD + c] *= rdg[i];
+    if (wid == 0 && lane < k) fv[lane] = YD[i * RR_KLD + lane] * rdg[i];
     __syncthreads();
-    for (int q = tid; q < i * k; q += RR_T) {
-      const int p = q / k, c = q - p * k;
-      Z[p * RR_KLD + c] = fma(-R[i * RR_LD + p], Z[i * RR_KLD + c], Z[p * RR_KLD + c]);
-    }
+    FOR_RC(tk, i, k, wid) YD[r * RR_KLD + c] = fma(-MA[r * RR_LD + i], fv[c], YD[r * RR_KLD + c]);
     __syncthreads();
   }
-  for (int q = tid; q < a.m * k; q += RR_T) {
-    const int r = q / k, c = q - r * k;
-    a.C[q] = (r < m) ? Z[r * RR_KLD + c] * sc[r] : 0.0;
-  }
+  FOR_RC(tk, a.m, k, wid) a.C[r * k + c] = (r < m) ? YD[r * RR_KLD + c] * (rdg[r] * sc[r]) : 0.0;
   if (tid < k) {
-    const double th = H[perm[tid] * RR_KLD + perm[tid]];
-    a.theta[tid] = th;
-    if (a.theta_hist) a.theta_hist[tid] = th;
-    if (!isfinite(th)) *a.status = 3;
+    const double thv = H[perm[tid] * RR_KLD + perm[tid]];
+    a.theta[tid] = thv;
+    if (a.theta_hist) a.theta_hist[tid] = thv;
+    if (!isfinite(thv)) *a.status = 3;
   }
   if (tid == 0 && dropped && a.restarts) *a.restarts += 1;
   if (!a.Cp) return;
-  // Coefficients of the next P, B-orthogonal to the next X:  Cw = C with the X rows
-  // zeroed,  Z2 = C^T G_B Cw  (k x k),  Cp = Cw - C Z2.
+  // ------------------------------------------ 10. coefficients of the next P, B-orthogonal
+  // to the next X:  Cw = C with the X rows zeroed,  Z2 = C^T G_B Cw,  Cp = Cw - C Z2.
   __syncthreads();
   const int mm = a.m;
-  double* Cs = M;                    // [mm][k]
-  double* T1 = M + mm * k;           // [mm][k]
+  double* Cs = MA;                   // [mm][k]
+  double* T1 = MA + mm * k;          // [mm][k]
   double* Z2 = T1 + mm * k;          // [k][k]
-  for (int q = tid; q < mm * k; q += RR_T) Cs[q] = a.C[q];
+  FOR_RC(tk, mm, k, wid) Cs[r * k + c] = a.C[r * k + c];
   __syncthreads();
   const double* GBg = a.G + (size_t)mm * mm;
-  for (int q = tid; q < mm * k; q += RR_T) {
-    const int r = q / k, j = q - r * k;
+  FOR_RC(tk, mm, k, wid) {
     double acc0 = 0.0, acc1 = 0.0;
     int b = k;
     for (; b + 1 < mm; b += 2) {
-      acc0 = fma(GBg[r * mm + b], Cs[b * k + j], acc0);
-      acc1 = fma(GBg[r * mm + b + 1], Cs[(b + 1) * k + j], acc1);
+      acc0 = fma(GBg[r * mm + b], Cs[b * k + c], acc0);
+      acc1 = fma(GBg[r * mm + b + 1], Cs[(b + 1) * k + c], acc1);
     }
-    if (b < mm) acc0 = fma(GBg[r * mm + b], Cs[b * k + j], acc0);
-    T1[q] = acc0 + acc1;
+    if (b < mm) acc0 = fma(GBg[r * mm + b], Cs[b * k + c], acc0);
+    T1[r * k + c] = acc0 + acc1;
   }
   __syncthreads();
-  for (int q = tid; q < k * k; q += RR_T) {
-    const int i = q / k, j = q - i * k;
+  FOR_RC(tk, k, k, wid) {
     double acc0 = 0.0, acc1 = 0.0;
-    int r = 0;
-    for (; r + 1 < mm; r += 2) {
-      acc0 = fma(Cs[r * k + i], T1[r * k + j], acc0);
-      acc1 = fma(Cs[(r + 1) * k + i], T1[(r + 1) * k + j], acc1);
+    int q = 0;
+    for (; q + 1 < mm; q += 2) {
+      acc0 = fma(Cs[q * k + r], T1[q * k + c], acc0);
+      acc1 = fma(Cs[(q + 1) * k + r], T1[(q + 1) * k + c], acc1);
     }
-    if (r < mm) acc0 = fma(Cs[r * k + i], T1[r * k + j], acc0);
-    Z2[q] = acc0 + acc1;
+    if (q < mm) acc0 = fma(Cs[q * k + r], T1[q * k + c], acc0);
+    Z2[r * k + c] = acc0 + acc1;
   }
   __syncthreads();
-  for (int q = tid; q < mm * k; q += RR_T) {
-    const int r = q / k, j = q - r * k;
-    double acc = (r >= k) ? Cs[q] : 0.0;
-    for (int i = 0; i < k; ++i) acc = fma(-Cs[r * k + i], Z2[i * k + j], acc);
-    a.Cp[q] = acc;
+  FOR_RC(tk, mm, k, wid) {
+    double acc = (r >= k) ? Cs[r * k + c] : 0.0;
+    for (int i = 0; i < k; ++i) acc = fma(-Cs[r * k + i], Z2[i * k + c], acc);
+    a.Cp[r * k + c] = acc;
   }
 }
 
 size_t rr_smem_bytes() {
-  return (size_t)(2 * RR_MMAX * RR_LD + RR_MMAX * RR_KLD + 2 * RR_KMAX * RR_KLD + 7 * RR_MMAX +
-                  3 * RR_KMAX) * sizeof(double) + 2 * RR_MMAX * sizeof(float) + RR_KMAX * sizeof(int);
+  return (size_t)(2 * RR_MMAX * RR_LD + 2 * RR_MMAX * RR_KLD + 3 * RR_MMAX + RR_KMAX + RR_KMAX) *
+             sizeof(double) +
+         (size_t)(6 * RR_MMAX) * sizeof(float) +
+         (2 * RR_KMAX + RR_MMAX + RR_MMAX) * sizeof(int) +
+         (size_t)(RR_MMAX * (RR_MMAX + 1) / 2) * sizeof(unsigned short);
 }
 
 }  // namespace
