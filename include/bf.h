@@ -62,6 +62,7 @@ extern "C" {
 
 #define BF_PRECOND_JACOBI   0 /* T = D^-1 (Algorithm 2's preconditioner)                  */
 #define BF_PRECOND_IDENTITY 1 /* T = I                                                    */
+#define BF_PRECOND_NET      2 /* T = the learned conv net of a bf_net (FP32 graphs)        */
 
 #define BF_BETA_FLEXIBLE  0   /* beta = s^T (r - r_old) / (s_old^T r_old)                 */
 #define BF_BETA_PRINTED   1   /* beta = s^T (r - r_old) / (s_old^T s_old), as printed     */
@@ -86,6 +87,7 @@ typedef struct bf_params {
 } bf_params;
 
 typedef struct bf_graph bf_graph;   /* opaque */
+typedef struct bf_net bf_net;       /* opaque: the learned preconditioner (see below) */
 
 typedef struct bf_info {
   int32_t iters;         /* iterations completed                                            */
@@ -102,6 +104,7 @@ typedef struct bf_cg_opts {
   double  shift;         /* sigma >= 0: solve (L + sigma I) x = sigma x0; 0 = L x = 0       */
   double  tol;           /* > 0: stop once ||r|| <= tol * ||b|| (||r_0|| if b = 0)          */
   double* hist;          /* optional device array [2 * kmax]: alpha_j, beta_j per iteration */
+  const bf_net* net;     /* BF_PRECOND_NET: the preconditioner (else ignored)               */
 } bf_cg_opts;
 
 typedef struct bf_lobpcg_opts {
@@ -111,6 +114,7 @@ typedef struct bf_lobpcg_opts {
   int32_t reserved;
   double  tol;           /* > 0: stop once max_j ||L x_j - theta_j B x_j|| / ||B x_j|| <= tol */
   double* theta_hist;    /* optional device array [(kmax + 1) * k]: Ritz values per step    */
+  const bf_net* net;     /* BF_PRECOND_NET: the preconditioner (else ignored)               */
 } bf_lobpcg_opts;
 
 /* ---- graph ------------------------------------------------------------------------ */
@@ -193,6 +197,40 @@ int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, int k, int km
  * threads) race and must be serialised by the caller. */
 int cg_filter_noalloc(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
                       void* x_out, bf_info* info, void* stream);
+
+/* ---- the learned preconditioner ----------------------------------------------------
+ * The preconditioner T of Algorithms 2 and 3 is left open by the paper (Section 5: the
+ * flexible beta admits a variable, nonlinear T).  A bf_net is a three-layer 3 x 3 conv
+ * net on the image-shaped residual r of a graph's grid (no bias, zero outside the image):
+ *   C = [ (D^-1 r) / rho, g, 1/d ] with rho = rms(D^-1 r),
+ *   A1 = conv(C, W1) (16 channels), A2 = conv(relu(A1), W2) (16), O = conv(relu(A2), W3),
+ *   T(r) = rho O.
+ * Weights w[bf_net_nweights()] = W1 [16][3][3][3], W2 [16][16][3][3], W3 [1][16][3][3]
+ * (output channel, input channel, tap row, tap column), kept in FP32 and applied rounded
+ * to BF16 with FP32 accumulation.  Training pairs (r, z) solve (L + sigma I) z = r; the
+ * loss of a pair is ||T(r) - z||^2 / ||z||^2.  A bf_net owns its weights, Adam state and
+ * workspace; calls that use one net must be ordered on one stream.  FP32 graphs only. */
+int bf_net_nweights(void);
+/* New net from host weights (copied); *out must be freed with bf_net_free. */
+int bf_net_create(const float* w_host, bf_net** out);
+int bf_net_free(bf_net* net);
+/* Copy the FP32 master weights (rounded = 0) or the BF16-rounded ones (1) to the host. */
+int bf_net_weights(const bf_net* net, float* w_host, int rounded);
+/* Z[:, j] = T(R[:, j]) for k image-shaped columns on g's grid (pixel-major blocks). */
+int bf_net_apply(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k,
+                 float* Z, int64_t ldz, void* stream);
+/* Reset the accumulated gradient and loss. */
+int bf_net_zero_grad(bf_net* net, void* stream);
+/* Add the gradient and the loss of the pair (r, z) (n floats each, on g's grid). */
+int bf_net_accumulate(bf_net* net, const bf_graph* g, const float* r, const float* z,
+                      void* stream);
+/* Read the accumulated gradient [bf_net_nweights()] and loss to the host (either may be
+ * NULL); synchronises the stream. */
+int bf_net_grad(const bf_net* net, float* grad_host, double* loss_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on scale times
+ * the accumulated gradient (scale = 1 / pairs for the mean); then resets the
+ * accumulators. */
+int bf_net_adam(bf_net* net, float lr, float scale, void* stream);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char* bf_last_error(void);

@@ -20,7 +20,7 @@ F32, F64 = 0, 1
 WINDOWS = {"square": 0, "cross": 1}
 WEIGHT_MODES = {"onthefly": 0, "stored_f32": 1, "stored_bf16": 2}
 OPS = {"W": 0, "L": 1, "DINV_W": 2, "D": 3, "NSYM": 4, "NDIAGL": 5}
-PRECONDS = {"jacobi": 0, "identity": 1}
+PRECONDS = {"jacobi": 0, "identity": 1, "net": 2}
 BETAS = {"flexible": 0, "printed": 1}
 PENCILS = {"D": 0, "I": 1}
 STATUS = {0: "ran", 1: "converged", 2: "breakdown"}
@@ -49,13 +49,14 @@ class bf_info(ctypes.Structure):
 class bf_cg_opts(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("shift", ctypes.c_double), ("tol", ctypes.c_double),
-                ("hist", ctypes.c_void_p)]
+                ("hist", ctypes.c_void_p), ("net", ctypes.c_void_p)]
 
 
 class bf_lobpcg_opts(ctypes.Structure):
     _fields_ = [("pencil", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("constrain_e", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("tol", ctypes.c_double), ("theta_hist", ctypes.c_void_p)]
+                ("tol", ctypes.c_double), ("theta_hist", ctypes.c_void_p),
+                ("net", ctypes.c_void_p)]
 
 
 def _load():
@@ -78,6 +79,15 @@ def _load():
                           ctypes.POINTER(bf_info), vp],
         "bf_rayleigh_ritz": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
         "cg_filter_noalloc": [vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, ctypes.POINTER(bf_info), vp],
+        "bf_net_nweights": [],
+        "bf_net_create": [vp, ctypes.POINTER(vp)],
+        "bf_net_free": [vp],
+        "bf_net_weights": [vp, vp, i32],
+        "bf_net_apply": [vp, vp, vp, i64, i32, vp, i64, vp],
+        "bf_net_zero_grad": [vp, vp],
+        "bf_net_accumulate": [vp, vp, vp, vp, vp],
+        "bf_net_grad": [vp, vp, vp, vp],
+        "bf_net_adam": [vp, ctypes.c_float, ctypes.c_float, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -221,12 +231,14 @@ def bf_simple_filter(g: Graph, x0: torch.Tensor, iters: int, out=None, stream=No
 
 def cg_filter(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jacobi",
               beta: str = "flexible", shift: float = 0.0, tol: float = 0.0,
-              hist: bool = False, out=None, sync: bool = True, stream=None):
-    """Algorithm 2.  Returns (x, info, hist) -- info None unless sync, hist None unless asked."""
+              hist: bool = False, out=None, sync: bool = True, stream=None, net: "Net | None" = None):
+    """Algorithm 2.  Returns (x, info, hist) -- info None unless sync, hist None unless asked.
+    precond="net" uses the learned preconditioner `net`."""
     out = torch.empty_like(x0) if out is None else out
     h = torch.full((2 * max(kmax, 1),), float("nan"), dtype=torch.float64, device=x0.device) if hist else None
     o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS[beta], shift=shift, tol=tol,
-                   hist=h.data_ptr() if h is not None else None)
+                   hist=h.data_ptr() if h is not None else None,
+                   net=net.handle if net is not None else None)
     info = bf_info() if sync else None
     _check(_lib.cg_filter(g.handle, _ptr(x0), kmax, ctypes.byref(o), _ptr(out),
                           ctypes.byref(info) if info is not None else None, _stream(stream)))
@@ -250,7 +262,7 @@ def cg_filter_noalloc(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jac
 def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
                   precond: str = "jacobi", constrain: bool = False, tol: float = 0.0,
                   want_X: bool = True, want_y: bool = True, theta_hist: bool = False,
-                  sync: bool = True, stream=None):
+                  sync: bool = True, stream=None, net: "Net | None" = None):
     """Algorithm 3 on a block X0 of shape (n, k).  Returns a dict with X, theta, resid, y,
     theta_hist and info (entries None when not requested)."""
     Xb, k = _as_block(X0)
@@ -262,7 +274,8 @@ def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
     th = torch.full(((kmax + 1) * k,), float("nan"), dtype=torch.float64, device=dev) if theta_hist else None
     o = bf_lobpcg_opts(pencil=PENCILS[pencil], precond=PRECONDS[precond],
                        constrain_e=int(constrain), reserved=0, tol=tol,
-                       theta_hist=th.data_ptr() if th is not None else None)
+                       theta_hist=th.data_ptr() if th is not None else None,
+                       net=net.handle if net is not None else None)
     info = bf_info() if sync else None
     _check(_lib.lobpcg_filter(g.handle, _ptr(Xb), Xb.stride(0), k, kmax, ctypes.byref(o),
                               _ptr(X), _ptr(theta), _ptr(resid), _ptr(y),
@@ -287,3 +300,68 @@ def rayleigh_ritz(GA: torch.Tensor, GB: torch.Tensor, k: int, m_nop: int = 0,
                                  _ptr(flags), _stream(stream)))
     f = flags.cpu().tolist()
     return C, theta, Cp, f[0], f[1]
+
+
+class Net:
+    """The learned preconditioner (bf_net): a 3-layer 3 x 3 conv net, weights in FP32 and
+    applied rounded to BF16.  `weights` is a flat float32 array of nweights() values or the
+    list [W1 (16,3,3,3), W2 (16,16,3,3), W3 (1,16,3,3)]."""
+
+    def __init__(self, weights):
+        import numpy as np
+        if isinstance(weights, (list, tuple)):
+            weights = np.concatenate([np.asarray(w, np.float32).ravel() for w in weights])
+        w = np.ascontiguousarray(np.asarray(weights, np.float32).ravel())
+        if w.size != nweights():
+            raise ValueError(f"expected {nweights()} weights, got {w.size}")
+        h = ctypes.c_void_p()
+        _check(_lib.bf_net_create(w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self.handle = h.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _lib.bf_net_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def weights(self, rounded: bool = False):
+        """Flat float32 numpy copy of the master (or BF16-rounded) weights."""
+        import numpy as np
+        w = np.empty(nweights(), np.float32)
+        _check(_lib.bf_net_weights(self.handle, w.ctypes.data_as(ctypes.c_void_p), int(rounded)))
+        return w
+
+    def apply(self, g: Graph, R: torch.Tensor, out=None, stream=None):
+        """Z = T(R) column by column; R is (n,) or (n, k)."""
+        Rb, k = _as_block(R)
+        Z = torch.empty_like(Rb) if out is None else out
+        _check(_lib.bf_net_apply(self.handle, g.handle, _ptr(Rb), Rb.stride(0), k, _ptr(Z),
+                                 Z.stride(0), _stream(stream)))
+        return Z.view_as(R) if R.dim() == 1 else Z
+
+    def zero_grad(self, stream=None):
+        _check(_lib.bf_net_zero_grad(self.handle, _stream(stream)))
+
+    def accumulate(self, g: Graph, r: torch.Tensor, z: torch.Tensor, stream=None):
+        _check(_lib.bf_net_accumulate(self.handle, g.handle, _ptr(r), _ptr(z), _stream(stream)))
+
+    def grad(self, stream=None):
+        """(flat float32 gradient, loss) accumulated since the last reset."""
+        import numpy as np
+        gr = np.empty(nweights(), np.float32)
+        loss = ctypes.c_double()
+        _check(_lib.bf_net_grad(self.handle, gr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss),
+                                _stream(stream)))
+        return gr, loss.value
+
+    def adam(self, lr: float, scale: float = 1.0, stream=None):
+        _check(_lib.bf_net_adam(self.handle, ctypes.c_float(lr), ctypes.c_float(scale), _stream(stream)))
+
+
+def nweights() -> int:
+    return int(_lib.bf_net_nweights())

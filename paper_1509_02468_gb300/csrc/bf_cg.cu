@@ -23,10 +23,20 @@ int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, 
                  int64_t ldy, double* dots, cudaStream_t s);
 int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
+int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
+                     int64_t ldz, cudaStream_t s);
 
 namespace {
 
 enum { CG_RUN = 0, CG_CONV = 1, CG_BREAK = 2, CG_NONFINITE = 3 };
+
+// s = T r with the learned preconditioner (FP32 graphs; cg_filter checks the dtype)
+inline int net_precond(const bf_net* net, const bf_graph* g, const float* r, float* s, cudaStream_t st) {
+  return bf_net_apply_f32(net, g, r, 1, 1, s, 1, st);
+}
+inline int net_precond(const bf_net*, const bf_graph*, const double*, double*, cudaStream_t) {
+  return bf_fail(BF_EINVAL, "cg_filter: the net preconditioner needs an FP32 graph");
+}
 
 struct CgState {
   double sr;        // s^T r of the current residual
@@ -172,6 +182,29 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_dir(const Geom<T> g, const Cg
   }
 }
 
+// Last block of an update: record alpha/beta, beta for the next direction from
+// s^T (r - r_old) = -alpha s^T q, new sums, convergence and finiteness tests.
+template <typename T>
+__device__ void cg_step_tail(const CgArgs<T>& a, const double* tot) {
+  CgState* st = a.st;
+  const int it = st->iter;
+  if (a.hist) {
+    a.hist[2 * it] = st->alpha;
+    a.hist[2 * it + 1] = a.first ? 0.0 : st->beta;
+  }
+  st->iter = it + 1;
+  const double den = (st->beta_mode == BF_BETA_PRINTED) ? st->ss : st->sr;
+  const double beta_next = -st->alpha * tot[1] / den;
+  st->sr = tot[0];
+  st->ss = tot[2];
+  st->rr = tot[3];
+  st->beta = beta_next;
+  if (!(isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2]) && isfinite(tot[3])))
+    st->status = CG_NONFINITE;
+  else if (st->tol2 > 0.0 && tot[3] <= st->tol2 * st->ref2)
+    st->status = CG_CONV;
+}
+
 // x += alpha p, r -= alpha q, s = T r; s^T r, s^T q, s^T s, r^T r; beta for the next step.
 template <typename T>
 __global__ void __launch_bounds__(BF_THREADS) k_cg_update(const CgArgs<T> a) {
@@ -195,24 +228,48 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_update(const CgArgs<T> a) {
   }
   double blk[4], tot[4];
   block_sum<4, T>(v, red, blk);
+  if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) cg_step_tail(a, tot);
+}
+
+// x += alpha p, r -= alpha q only: with the net preconditioner s = T r is computed next
+// by its own kernels, then k_cg_sdots takes the sums.
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_xr(const CgArgs<T> a) {
+  if (a.st->status != CG_RUN) return;
+  const T alpha = (T)a.st->alpha;
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * BF_THREADS) {
+    a.x[i] = fma(alpha, a.p_new[i], a.x[i]);
+    a.r[i] = fma(-alpha, a.q[i], a.r[i]);
+  }
+}
+
+// The sums of k_cg_update for a given s (the net's output); init: after k_cg_init only
+// s^T r and s^T s are refreshed.
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_sdots(const CgArgs<T> a, int init) {
+  if (a.st->status != CG_RUN) return;
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * BF_THREADS) {
+    const T r = a.r[i], s = a.s[i], q = init ? T(0) : a.q[i];
+    v[0] += s * r;
+    v[1] += s * q;
+    v[2] += s * s;
+    v[3] += r * r;
+  }
+  double blk[4], tot[4];
+  block_sum<4, T>(v, red, blk);
   if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) {
-    CgState* st = a.st;
-    const int it = st->iter;
-    if (a.hist) {
-      a.hist[2 * it] = st->alpha;
-      a.hist[2 * it + 1] = a.first ? 0.0 : st->beta;
+    if (init) {
+      a.st->sr = tot[0];
+      a.st->ss = tot[2];
+      if (!(isfinite(tot[0]) && isfinite(tot[2]))) a.st->status = CG_NONFINITE;
+    } else {
+      cg_step_tail(a, tot);
     }
-    st->iter = it + 1;
-    const double den = (st->beta_mode == BF_BETA_PRINTED) ? st->ss : st->sr;
-    const double beta_next = -st->alpha * tot[1] / den;
-    st->sr = tot[0];
-    st->ss = tot[2];
-    st->rr = tot[3];
-    st->beta = beta_next;
-    if (!(isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2]) && isfinite(tot[3])))
-      st->status = CG_NONFINITE;
-    else if (st->tol2 > 0.0 && tot[3] <= st->tol2 * st->ref2)
-      st->status = CG_CONV;
   }
 }
 
@@ -406,14 +463,25 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   const bool one_d = (g->ny == 1 && g->ry == 0);
   const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
   const size_t sm = hp * 2 * sizeof(T);
+  const bool net = (o.precond == BF_PRECOND_NET);
   cg_launch_window<T>(true, tg, sm, s, g, a);
   BF_CUDA(cudaGetLastError());
+  if (net) {
+    if ((rc = net_precond(o.net, g, a.r, a.s, s))) return rc;
+    BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 1));
+  }
   for (int it = 0; it < kmax; ++it) {
     a.first = (it == 0);
     a.p_old = pbuf[it & 1];
     a.p_new = pbuf[(it + 1) & 1];
     cg_launch_window<T>(false, tg, sm, s, g, a);
-    BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+    if (net) {
+      BF_LAUNCH(k_cg_xr<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+      if ((rc = net_precond(o.net, g, a.r, a.s, s))) return rc;
+      BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 0));
+    } else {
+      BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+    }
   }
   BF_CUDA(cudaGetLastError());
   if (info) {
@@ -441,8 +509,10 @@ extern "C" int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_c
   bf_cg_opts o;
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY)
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET)
     return bf_fail(BF_EINVAL, "cg_filter: bad precond");
+  if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4))
+    return bf_fail(BF_EINVAL, "cg_filter: BF_PRECOND_NET needs a net and an FP32 graph");
   if (o.beta != BF_BETA_FLEXIBLE && o.beta != BF_BETA_PRINTED)
     return bf_fail(BF_EINVAL, "cg_filter: bad beta");
   if (!(o.shift >= 0.0) || !(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "cg_filter: shift and tol must be >= 0");

@@ -41,6 +41,13 @@ MUTATIONS = [
     # Section 4 simple iteration, Section 5 polynomial recurrence
     ("oracle/solvers.py", "x = G.DINV_W @ x", "x = G.W @ x"),
     ("oracle/spectral.py", "chi = chi + a * pi", "chi = chi + a * sig"),
+    # the conv-net preconditioner: input scaling, adjoint shift, ReLU mask of the wrong layer
+    ("oracle/convnet.py", "c0 = np.asarray(r, np.float64) / np.asarray(d, np.float64)",
+     "c0 = np.asarray(r, np.float64)"),
+    ("oracle/convnet.py", "shifted = gp[:, 1 - a:1 - a + H, 1 - b:1 - b + W]",
+     "shifted = gp[:, 1 + a:1 + a + H, 1 + b:1 + b + W]"),
+    ("oracle/convnet.py", 'G1 = conv_t(G2, W2) * (c["A1"] > 0)', 'G1 = conv_t(G2, W2) * (c["A2"] > 0)'),
+    ("oracle/convnet.py", "vv = b2 * vv + (1 - b2) * g * g", "vv = b2 * vv + (1 - b2) * g"),
 ]
 
 
@@ -56,6 +63,7 @@ def test_pins_catch_planted_mistake(tmp_path, path, old, new):
     assert old in src, f"mutation anchor not found in {path}: {old!r}"
     target.write_text(src.replace(old, new, 1))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_graph.py", "tests/test_oracle_solvers.py"],
+                        "tests/test_oracle_graph.py", "tests/test_oracle_solvers.py",
+                        "tests/test_oracle_convnet.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake not caught: {path}: {new!r}\n{r.stdout[-2000:]}"
