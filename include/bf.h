@@ -164,7 +164,10 @@ int bf_simple_filter(const bf_graph* g, const void* x0, int iters, void* x_out,
  * (breakdown: x keeps its last value) or, with tol > 0, once ||r|| <= tol * ||b||.
  * x0 and x_out hold n elements (may be the same array).  opts may be NULL (Jacobi,
  * flexible beta, shift 0, tol 0).  If info is not NULL the stream is synchronised and
- * info filled; a breakdown then returns BF_EBREAKDOWN. */
+ * info filled; a breakdown then returns BF_EBREAKDOWN.  With tol > 0 the call also reads
+ * the solver status every 64 iterations (a stream synchronisation) and stops enqueueing
+ * once the run has stopped; with tol = 0 it never reads back before the end (so it can be
+ * captured in a CUDA graph).  BF_PRECOND_NET takes T from opts->net. */
 int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
               void* x_out, bf_info* info, void* stream);
 

@@ -24,17 +24,19 @@ int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, 
 int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
 int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
-                     int64_t ldz, cudaStream_t s);
+                     int64_t ldz, cudaStream_t s, const int* stop);
 
 namespace {
 
 enum { CG_RUN = 0, CG_CONV = 1, CG_BREAK = 2, CG_NONFINITE = 3 };
+#define CG_POLL 64
 
 // s = T r with the learned preconditioner (FP32 graphs; cg_filter checks the dtype)
-inline int net_precond(const bf_net* net, const bf_graph* g, const float* r, float* s, cudaStream_t st) {
-  return bf_net_apply_f32(net, g, r, 1, 1, s, 1, st);
+inline int net_precond(const bf_net* net, const bf_graph* g, const float* r, float* s, cudaStream_t st,
+                       const int* stop) {
+  return bf_net_apply_f32(net, g, r, 1, 1, s, 1, st, stop);
 }
-inline int net_precond(const bf_net*, const bf_graph*, const double*, double*, cudaStream_t) {
+inline int net_precond(const bf_net*, const bf_graph*, const double*, double*, cudaStream_t, const int*) {
   return bf_fail(BF_EINVAL, "cg_filter: the net preconditioner needs an FP32 graph");
 }
 
@@ -467,7 +469,7 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   cg_launch_window<T>(true, tg, sm, s, g, a);
   BF_CUDA(cudaGetLastError());
   if (net) {
-    if ((rc = net_precond(o.net, g, a.r, a.s, s))) return rc;
+    if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
     BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 1));
   }
   for (int it = 0; it < kmax; ++it) {
@@ -477,10 +479,18 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
     cg_launch_window<T>(false, tg, sm, s, g, a);
     if (net) {
       BF_LAUNCH(k_cg_xr<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
-      if ((rc = net_precond(o.net, g, a.r, a.s, s))) return rc;
+      if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
       BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 0));
     } else {
       BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+    }
+    // with a tolerance, look at the status every CG_POLL iterations so that a converged
+    // run stops enqueueing (a fixed-count run never reads back and can be captured)
+    if (o.tol > 0.0 && (it + 1) % CG_POLL == 0 && it + 1 < kmax) {
+      int stv = 0;
+      BF_CUDA(cudaMemcpyAsync(&stv, &a.st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      BF_CUDA(cudaStreamSynchronize(s));
+      if (stv != CG_RUN) break;
     }
   }
   BF_CUDA(cudaGetLastError());

@@ -20,6 +20,8 @@
 
 int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
+int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
+                     int64_t ldz, cudaStream_t s, const int* stop);
 int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
 
@@ -678,15 +680,30 @@ static int run_update(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
   return BF_OK;
 }
 
-// A X = L X, then the residual kernel: W = T (A X - B X theta) and its norms.
+inline int net_T(const bf_net* net, const bf_graph* g, float* W, int k, cudaStream_t s, const int* stop) {
+  return bf_net_apply_f32(net, g, W, k, k, W, k, s, stop);
+}
+inline int net_T(const bf_net*, const bf_graph*, double*, int, cudaStream_t, const int*) {
+  return bf_fail(BF_EINVAL, "lobpcg_filter: the net preconditioner needs an FP32 graph");
+}
+
+// A X = L X, then the residual kernel: W = T (A X - B X theta) and its norms.  With the
+// learned preconditioner the kernel writes R = A X - B X theta, the net maps it to
+// W = T(R) in place and the constraint coefficients e^T B W / e^T B e are recomputed.
 template <typename T>
 static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T* bdiag,
                      const T* tinv, int constrain, double* part, LobState* st, int rgrid,
-                     cudaStream_t s) {
+                     cudaStream_t s, const bf_net* net = nullptr) {
   int rc = apply_T<T>(g, BF_OP_L, X, k, k, AX, k, s);
   if (rc) return rc;
-  BF_LAUNCH(k_resid<T><<<rgrid, 256, 0, s>>>(X, AX, k, g->n, bdiag, tinv, Wn, constrain, part, st));
+  BF_LAUNCH(k_resid<T><<<rgrid, 256, 0, s>>>(X, AX, k, g->n, bdiag, net ? nullptr : tinv, Wn, constrain,
+                                             part, st));
   BF_CUDA(cudaGetLastError());
+  if (net) {
+    if ((rc = net_T(net, g, Wn, k, s, &st->status))) return rc;
+    if (constrain) BF_LAUNCH(k_bsums<T><<<rgrid, 256, 0, s>>>(Wn, k, g->n, bdiag, part, st));
+    BF_CUDA(cudaGetLastError());
+  }
   return BF_OK;
 }
 
@@ -787,7 +804,8 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   ua.Pn = nullptr;
   rc = run_update<T>(ua, ugrid, s);
   if (rc) return rc;
-  rc = run_resid<T>(g, B.X[0], B.AX[0], k, B.W[0], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s);
+  const bf_net* net = (o.precond == BF_PRECOND_NET) ? o.net : nullptr;
+  rc = run_resid<T>(g, B.X[0], B.AX[0], k, B.W[0], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s, net);
   if (rc) return rc;
   // the start step counted as one residual evaluation: iterations count from 0 after it
   BF_LAUNCH(k_state_iter0<<<1, 32, 0, s>>>(B.st));
@@ -826,7 +844,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
     if (rc) return rc;
     rc = apply_T<T>(g, BF_OP_L, B.P[nj], k, k, B.AP[nj], k, s);
     if (rc) return rc;
-    rc = run_resid<T>(g, B.X[nj], B.AX[nj], k, B.W[nj], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s);
+    rc = run_resid<T>(g, B.X[nj], B.AX[nj], k, B.W[nj], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s, net);
     if (rc) return rc;
   }
   // ---- outputs
@@ -868,8 +886,10 @@ extern "C" int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, in
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   if (o.pencil != BF_PENCIL_D && o.pencil != BF_PENCIL_I) return bf_fail(BF_EINVAL, "lobpcg_filter: bad pencil");
-  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY)
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET)
     return bf_fail(BF_EINVAL, "lobpcg_filter: bad precond");
+  if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4))
+    return bf_fail(BF_EINVAL, "lobpcg_filter: BF_PRECOND_NET needs a net and an FP32 graph");
   if (!(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "lobpcg_filter: tol must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   if (g->esize == 4)

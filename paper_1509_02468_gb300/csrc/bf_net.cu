@@ -68,6 +68,7 @@ struct NetArgs {
   int64_t ldz;
   const float* w;        // layer weights as stored: [cout_l][cin_l][9]
   int transpose;         // use the adjoint (flipped, transposed) weights
+  const int* stop;       // optional solver status: nonzero = stopped, skip the work
 };
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -126,6 +127,7 @@ __device__ __forceinline__ void net_stage(const NetArgs& a, int col, int bx, int
 template <int CIN, int COUT, int IN, int OUT>
 __global__ void __launch_bounds__(NET_TW * NET_TH) k_net_conv(const NetArgs a) {
   constexpr int COUTP = (COUT + 3) & ~3;
+  if (a.stop && *a.stop != 0) return;
   __shared__ __align__(16) float sx[CIN * NET_HP];
   __shared__ __align__(16) float sw[CIN * 9 * COUTP];       // [c][tap][o]
   const int col = blockIdx.z;
@@ -166,14 +168,30 @@ __global__ void __launch_bounds__(NET_TW * NET_TH) k_net_conv(const NetArgs a) {
   } else {
     float* dst = a.out + ((int64_t)col * a.n + i) * COUT;
     const float* mk = (OUT == OUT_MASKED) ? a.mask + ((int64_t)col * a.n + i) * COUT : nullptr;
+    if (COUT % 4 == 0) {
 #pragma unroll
-    for (int o = 0; o < COUT; ++o) dst[o] = (OUT == OUT_MASKED) ? (mk[o] > 0.0f ? acc[o] : 0.0f) : acc[o];
+      for (int o4 = 0; o4 < COUT / 4; ++o4) {
+        float4 v = make_float4(acc[4 * o4], acc[4 * o4 + 1], acc[4 * o4 + 2], acc[4 * o4 + 3]);
+        if (OUT == OUT_MASKED) {
+          const float4 m = reinterpret_cast<const float4*>(mk)[o4];
+          v.x = m.x > 0.0f ? v.x : 0.0f;
+          v.y = m.y > 0.0f ? v.y : 0.0f;
+          v.z = m.z > 0.0f ? v.z : 0.0f;
+          v.w = m.w > 0.0f ? v.w : 0.0f;
+        }
+        reinterpret_cast<float4*>(dst)[o4] = v;
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < COUT; ++o) dst[o] = (OUT == OUT_MASKED) ? (mk[o] > 0.0f ? acc[o] : 0.0f) : acc[o];
+    }
   }
 }
 
 // Per-block sums for rho (sum (r/d)^2) and, with z, sum z^2; blockIdx.y is the column.
 __global__ void __launch_bounds__(256) k_net_sums(const float* r, int64_t ldr, const float* d, const float* z,
-                                                  int64_t n, double* partials) {
+                                                  int64_t n, double* partials, const int* stop) {
+  if (stop && *stop != 0) return;
   __shared__ double red[2 * 8];
   const int col = blockIdx.y;
   double s0 = 0.0, s1 = 0.0;
@@ -201,7 +219,9 @@ __global__ void __launch_bounds__(256) k_net_sums(const float* r, int64_t ldr, c
 }
 
 // rho[col] = sqrt(mean), zz = sum z^2 (column 0), summed over blocks in order.
-__global__ void k_net_rho(const double* partials, int nblocks, int64_t n, float* rho, double* zz) {
+__global__ void k_net_rho(const double* partials, int nblocks, int64_t n, float* rho, double* zz,
+                          const int* stop) {
+  if (stop && *stop != 0) return;
   const int col = blockIdx.x;
   double a0 = 0.0, a1 = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += 32) {
@@ -386,11 +406,11 @@ int launch_conv(const NetArgs& a, int cols, cudaStream_t s) {
 
 // rho of `cols` columns of r (and zz of z when given)
 int net_sums(const bf_graph* g, const float* r, int64_t ldr, const float* z, int cols, const Bufs& b,
-             cudaStream_t s) {
+             cudaStream_t s, const int* stop = nullptr) {
   const int64_t n = g->n;
   const int nb = (int)std::min<int64_t>((n + 255) / 256, 1024);
-  BF_LAUNCH((k_net_sums<<<dim3(nb, cols), 256, 0, s>>>(r, ldr, (const float*)g->d, z, n, b.dpart)));
-  BF_LAUNCH((k_net_rho<<<cols, 32, 0, s>>>(b.dpart, nb, n, b.rho, z ? b.zz : nullptr)));
+  BF_LAUNCH((k_net_sums<<<dim3(nb, cols), 256, 0, s>>>(r, ldr, (const float*)g->d, z, n, b.dpart, stop)));
+  BF_LAUNCH((k_net_rho<<<cols, 32, 0, s>>>(b.dpart, nb, n, b.rho, z ? b.zz : nullptr, stop)));
   BF_CUDA(cudaGetLastError());
   return BF_OK;
 }
@@ -406,7 +426,7 @@ int check_pair(const bf_net* net, const bf_graph* g) {
 
 // ------------------------------------------------------------------ exported
 int bf_net_apply_f32(const bf_net* net_c, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
-                     int64_t ldz, cudaStream_t s) {
+                     int64_t ldz, cudaStream_t s, const int* stop) {
   bf_net* net = const_cast<bf_net*>(net_c);
   int rc = check_pair(net, g);
   if (rc) return rc;
@@ -415,9 +435,10 @@ int bf_net_apply_f32(const bf_net* net_c, const bf_graph* g, const float* R, int
     Bufs b;
     rc = net_ws(net, g, cols, false, &b);
     if (rc) return rc;
-    rc = net_sums(g, R + c0, ldr, nullptr, cols, b, s);
+    rc = net_sums(g, R + c0, ldr, nullptr, cols, b, s, stop);
     if (rc) return rc;
     NetArgs a = net_args(net, g);
+    a.stop = stop;
     a.r = R + c0;
     a.ldr = ldr;
     a.rho = b.rho;
@@ -482,7 +503,7 @@ extern "C" int bf_net_apply(const bf_net* net, const bf_graph* g, const float* R
                             int64_t ldz, void* stream) {
   if (!R || !Z) return bf_fail(BF_EINVAL, "bf_net_apply: NULL argument");
   if (k < 1 || ldr < k || ldz < k) return bf_fail(BF_EINVAL, "bf_net_apply: need 1 <= k <= ld");
-  return bf_net_apply_f32(net, g, R, ldr, k, Z, ldz, (cudaStream_t)stream);
+  return bf_net_apply_f32(net, g, R, ldr, k, Z, ldz, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" int bf_net_zero_grad(bf_net* net, void* stream) {
