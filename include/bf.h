@@ -235,6 +235,31 @@ int bf_net_grad(const bf_net* net, float* grad_host, double* loss_host, void* st
  * accumulators. */
 int bf_net_adam(bf_net* net, float lr, float scale, void* stream);
 
+/* ---- batched CG -----------------------------------------------------------------------
+ * Algorithm 2 on many instances (images and signals of uneven sizes) at once: every launch
+ * covers the tiles of all instances (one work list per window shape), so small instances
+ * still fill the GPU; per-instance FP64 scalars as in cg_filter.  The whole run of kmax
+ * iterations is captured once as a CUDA graph and replayed by later calls with the same
+ * kmax and options.  Graphs must be FP32 with on-the-fly weights and a 7 x 7 (images),
+ * 11-tap (signals) or 5-point cross window; instances with the same window shape must
+ * share sigma_s and sigma_r.  The batch keeps pointers to the graphs (which must outlive
+ * it) and owns the per-instance vectors (5 n-vectors each). */
+typedef struct bf_batch bf_batch;
+int bf_batch_create(const bf_graph* const* graphs, int count, bf_batch** out);
+int bf_batch_free(bf_batch* b);
+/* x0[i], x_out[i]: HOST array of device pointers, n_i floats each (x_out[i] may equal
+ * x0[i]).  opts as for cg_filter (Jacobi or identity; hist and net unused).  infos: NULL
+ * or a host array of count bf_info, filled after synchronising the stream. */
+int bf_batch_cg(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
+                const bf_cg_opts* opts, bf_info* infos, void* stream);
+/* Autotuner: time `iters` iterations with each candidate tile shape of the image class
+ * (32 x 8, 64 x 4, 16 x 16 pixels) on these vectors and keep the fastest; ms_out (host,
+ * 3 floats) receives the timings.  Synchronises the stream. */
+int bf_batch_tune(bf_batch* b, const float* const* x0, float* const* x_out, int iters,
+                  float* ms_out, void* stream);
+/* Total tiles of the work lists and the image-class tile shape in use (0, 1, 2 as above). */
+int bf_batch_tiles(const bf_batch* b, int64_t* tiles_out, int* variant_out);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char* bf_last_error(void);
 

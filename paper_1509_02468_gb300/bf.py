@@ -88,6 +88,11 @@ def _load():
         "bf_net_accumulate": [vp, vp, vp, vp, vp],
         "bf_net_grad": [vp, vp, vp, vp],
         "bf_net_adam": [vp, ctypes.c_float, ctypes.c_float, vp],
+        "bf_batch_create": [vp, i32, ctypes.POINTER(vp)],
+        "bf_batch_free": [vp],
+        "bf_batch_cg": [vp, vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, vp],
+        "bf_batch_tune": [vp, vp, vp, i32, vp, vp],
+        "bf_batch_tiles": [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -365,3 +370,52 @@ class Net:
 
 def nweights() -> int:
     return int(_lib.bf_net_nweights())
+
+
+class Batch:
+    """Batched CG over many graphs (bf_batch): one work list per window shape, one CUDA
+    graph per (kmax, options)."""
+
+    def __init__(self, graphs):
+        self.graphs = list(graphs)              # the batch keeps pointers to them
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle for g in self.graphs])
+        h = ctypes.c_void_p()
+        _check(_lib.bf_batch_create(arr, len(self.graphs), ctypes.byref(h)))
+        self.handle = h.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _lib.bf_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ptrs(ts):
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def cg(self, x0s, kmax: int, precond: str = "jacobi", beta: str = "flexible", shift: float = 0.0,
+           tol: float = 0.0, outs=None, sync: bool = True, stream=None):
+        """Returns (outs, infos) -- infos None unless sync."""
+        outs = [torch.empty_like(x) for x in x0s] if outs is None else outs
+        o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS[beta], shift=shift, tol=tol, hist=None, net=None)
+        infos = (bf_info * len(x0s))() if sync else None
+        _check(_lib.bf_batch_cg(self.handle, self._ptrs(x0s), self._ptrs(outs), kmax, ctypes.byref(o),
+                                infos, _stream(stream)))
+        return outs, ([_info(i) for i in infos] if infos is not None else None)
+
+    def tune(self, x0s, iters: int = 5, outs=None, stream=None):
+        """Autotune the image tile shape; returns the timings (ms) of the three candidates."""
+        outs = [torch.empty_like(x) for x in x0s] if outs is None else outs
+        ms = (ctypes.c_float * 3)()
+        _check(_lib.bf_batch_tune(self.handle, self._ptrs(x0s), self._ptrs(outs), iters, ms, _stream(stream)))
+        return list(ms)
+
+    def tiles(self):
+        t, v = ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.bf_batch_tiles(self.handle, ctypes.byref(t), ctypes.byref(v)))
+        return t.value, v.value

@@ -1,0 +1,579 @@
+// Batched CG filters (Algorithm 2, Section 5) over many instances of uneven size -- images
+// and signals -- in one launch sequence, captured once as a CUDA graph and replayed.
+//
+// All instances' tiles form one work list per window shape (7 x 7 images, 11-tap signals,
+// 5-point lattices); one block handles one tile, so a launch covers the whole batch and
+// the GPU stays full however small the single instances are.  The tiles of an instance
+// are consecutive in its list; the last block of an instance to finish (per-instance
+// arrival counter) sums that instance's block partials in a fixed order and updates its
+// FP64 scalars (alpha, beta, the stopping tests), exactly as the single-instance kernels
+// do for the whole grid.  Per iteration: one direction kernel (p, q = (L + sigma I) p,
+// p^T q, alpha) per shape class and one update kernel (x, r, s = T r, the sums, beta) per
+// class.  Instances that have stopped return at once.
+//
+// The autotuner (bf_batch_tune) times the candidate tile shapes of the image class on the
+// batch itself and keeps the fastest for later runs.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bf_internal.cuh"
+#include "bf_window_fast.cuh"
+
+namespace {
+
+enum { B_RUN = 0, B_CONV = 1, B_BREAK = 2, B_NONFINITE = 3 };
+
+struct BState {
+  double sr, ss, rr, pq, alpha, beta, ref2;
+  int status, iter;
+};
+
+struct BInst {
+  int nx, ny;
+  int64_t n;
+  const float* guide;
+  const float* dinv;      // NULL: identity preconditioner
+  const float* x0;
+  float* x;
+  float* r;
+  float* s;
+  float* q;
+  float* p[2];
+  int job0, njobs;        // range in the class work list (per tile shape)
+  unsigned counter;
+  BState st;
+};
+
+struct BJob {
+  int inst;
+  int bx, by;
+};
+
+struct BArgs {
+  BInst* inst;
+  const BJob* jobs;
+  double* partials;       // [jobs][4] of this class
+  float shift;
+  double tol2;
+  int beta_mode;
+};
+
+// Last block of an instance: sums the instance's partials (job0 .. job0 + njobs) in order.
+template <int NV>
+__device__ __forceinline__ bool inst_sum_last(const double (&blk)[NV], const BArgs& a, BInst& in, int job,
+                                              double (&tot)[NV], int* is_last) {
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) a.partials[(size_t)job * 4 + j] = blk[j];
+    __threadfence();
+    const unsigned prev = atomicAdd(&in.counter, 1u);
+    *is_last = (prev == (unsigned)in.njobs - 1);
+  }
+  __syncthreads();
+  if (!*is_last) return false;
+  __threadfence();
+  double v[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+  for (int q = threadIdx.x; q < in.njobs; q += BF_THREADS) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] += ((volatile double*)a.partials)[(size_t)(in.job0 + q) * 4 + j];
+  }
+  __shared__ double red2[NV * (BF_THREADS / 32)];
+  block_sum<NV, double>(v, red2, tot);
+  if (threadIdx.x == 0) in.counter = 0u;
+  return threadIdx.x == 0;
+}
+
+template <class SH, class F>
+__device__ __forceinline__ void bstage(const BInst& in, int bx, int by, float* sx, float* sg, float* sval, F f) {
+  for (int hp = threadIdx.x; hp < SH::hp; hp += BF_THREADS) {
+    const int hy = hp / SH::hw, hx = hp - hy * SH::hw;
+    const int gy = by - SH::ry + hy, gx = bx - SH::rx + hx;
+    const bool inside = gx >= 0 && gx < in.nx && gy >= 0 && gy < in.ny;
+    float v = 0.0f, gv = 0.0f;
+    if (inside) {
+      const int64_t gp = (int64_t)gy * in.nx + gx;
+      v = f(gp);
+      gv = in.guide[gp];
+    }
+    sx[hp] = v;
+    sg[hp] = gv;
+    sval[hp] = inside ? 1.0f : 0.0f;
+  }
+}
+
+// r = -L x0, x = x0, s = T r; sums s^T r, s^T s, r^T r, x0^T x0; state of the instance.
+template <class SH>
+__global__ void __launch_bounds__(BF_THREADS) k_bcg_init(const Geom<float> g, const BArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  float* sx = reinterpret_cast<float*>(smem);
+  float* sg = sx + SH::hp;
+  float* sval = sg + SH::hp;
+  const int job = blockIdx.x;
+  const BJob jb = a.jobs[job];
+  BInst& in = a.inst[jb.inst];
+  const bool mask = !(jb.bx - SH::rx >= 0 && jb.bx + SH::tw + SH::rx <= in.nx && jb.by - SH::ry >= 0 &&
+                      jb.by + SH::th + SH::ry <= in.ny);
+  bstage<SH>(in, jb.bx, jb.by, sx, sg, sval, [&](int64_t gp) { return in.x0[gp]; });
+  __syncthreads();
+  const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
+  const int x = jb.bx + lx, y = jb.by + ly;
+  const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
+  float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (x < in.nx && y < in.ny) {
+    const int64_t i = (int64_t)y * in.nx + x;
+    float xi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+    window_fast<SH, 1, false>(g, hp0, i, in.nx, sg, sval, mask, reinterpret_cast<const Vec<float, 1>*>(sx),
+                              nullptr, BF_W_ONTHEFLY, in.n, xi, acc, ws);
+    const float r = -acc[0];
+    const float sv = in.dinv ? r * in.dinv[i] : r;
+    in.x[i] = xi[0];
+    in.r[i] = r;
+    in.s[i] = sv;
+    v[0] = sv * r;
+    v[1] = sv * sv;
+    v[2] = r * r;
+    v[3] = xi[0] * xi[0];
+  }
+  double blk[4], tot[4];
+  block_sum<4, float>(v, red, blk);
+  if (inst_sum_last<4>(blk, a, in, job, tot, &last)) {
+    BState& st = in.st;
+    st.sr = tot[0];
+    st.ss = tot[1];
+    st.rr = tot[2];
+    const double b2 = (double)a.shift * (double)a.shift * tot[3];
+    st.ref2 = b2 > 0.0 ? b2 : tot[2];
+    st.beta = 0.0;
+    st.alpha = 0.0;
+    st.iter = 0;
+    st.status = (isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2])) ? B_RUN : B_NONFINITE;
+  }
+}
+
+// p = s + beta p_old on tile + halo (first iteration: p = s), q = (L + shift I) p, p^T q, alpha.
+template <class SH>
+__global__ void __launch_bounds__(BF_THREADS) k_bcg_dir(const Geom<float> g, const BArgs a) {
+  const int job = blockIdx.x;
+  const BJob jb = a.jobs[job];
+  BInst& in = a.inst[jb.inst];
+  if (in.st.status != B_RUN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[BF_THREADS / 32];
+  __shared__ int last;
+  float* sx = reinterpret_cast<float*>(smem);
+  float* sg = sx + SH::hp;
+  float* sval = sg + SH::hp;
+  const int it = in.st.iter;
+  const float* p_old = in.p[it & 1];
+  float* p_new = in.p[(it + 1) & 1];
+  const bool mask = !(jb.bx - SH::rx >= 0 && jb.bx + SH::tw + SH::rx <= in.nx && jb.by - SH::ry >= 0 &&
+                      jb.by + SH::th + SH::ry <= in.ny);
+  const float beta = (float)in.st.beta;
+  if (it == 0)
+    bstage<SH>(in, jb.bx, jb.by, sx, sg, sval, [&](int64_t gp) { return in.s[gp]; });
+  else
+    bstage<SH>(in, jb.bx, jb.by, sx, sg, sval, [&](int64_t gp) { return fmaf(beta, p_old[gp], in.s[gp]); });
+  __syncthreads();
+  const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
+  const int x = jb.bx + lx, y = jb.by + ly;
+  const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
+  float v[1] = {0.0f};
+  if (x < in.nx && y < in.ny) {
+    const int64_t i = (int64_t)y * in.nx + x;
+    float pi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+    window_fast<SH, 1, false>(g, hp0, i, in.nx, sg, sval, mask, reinterpret_cast<const Vec<float, 1>*>(sx),
+                              nullptr, BF_W_ONTHEFLY, in.n, pi, acc, ws);
+    const float q = fmaf(a.shift, pi[0], acc[0]);
+    p_new[i] = pi[0];
+    in.q[i] = q;
+    v[0] = pi[0] * q;
+  }
+  double blk[1], tot[1];
+  block_sum<1, float>(v, red, blk);
+  if (inst_sum_last<1>(blk, a, in, job, tot, &last)) {
+    BState& st = in.st;
+    st.pq = tot[0];
+    if (st.sr == 0.0) st.status = B_CONV;
+    else if (!isfinite(tot[0])) st.status = B_NONFINITE;
+    else if (!(tot[0] > 0.0)) st.status = B_BREAK;
+    else st.alpha = st.sr / tot[0];
+  }
+}
+
+// x += alpha p, r -= alpha q, s = T r on the tile; sums; beta and the stopping tests.
+template <class SH>
+__global__ void __launch_bounds__(BF_THREADS) k_bcg_update(const BArgs a) {
+  const int job = blockIdx.x;
+  const BJob jb = a.jobs[job];
+  BInst& in = a.inst[jb.inst];
+  if (in.st.status != B_RUN) return;
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  const float alpha = (float)in.st.alpha;
+  const float* p = in.p[(in.st.iter + 1) & 1];
+  const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
+  const int x = jb.bx + lx, y = jb.by + ly;
+  float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (x < in.nx && y < in.ny) {
+    const int64_t i = (int64_t)y * in.nx + x;
+    const float pi = p[i], q = in.q[i];
+    in.x[i] = fmaf(alpha, pi, in.x[i]);
+    const float r = fmaf(-alpha, q, in.r[i]);
+    const float sv = in.dinv ? r * in.dinv[i] : r;
+    in.r[i] = r;
+    in.s[i] = sv;
+    v[0] = sv * r;
+    v[1] = sv * q;
+    v[2] = sv * sv;
+    v[3] = r * r;
+  }
+  double blk[4], tot[4];
+  block_sum<4, float>(v, red, blk);
+  if (inst_sum_last<4>(blk, a, in, job, tot, &last)) {
+    BState& st = in.st;
+    st.iter += 1;
+    const double den = (a.beta_mode == BF_BETA_PRINTED) ? st.ss : st.sr;
+    st.beta = -st.alpha * tot[1] / den;
+    st.sr = tot[0];
+    st.ss = tot[2];
+    st.rr = tot[3];
+    if (!(isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2]) && isfinite(tot[3]))) st.status = B_NONFINITE;
+    else if (a.tol2 > 0.0 && tot[3] <= a.tol2 * st.ref2) st.status = B_CONV;
+  }
+}
+
+// candidate tile shapes of the image class (the autotuner's choices)
+typedef WinShapeT<3, 3, false, 32, 8> R3_32x8;
+typedef WinShapeT<3, 3, false, 64, 4> R3_64x4;
+typedef WinShapeT<3, 3, false, 16, 16> R3_16x16;
+enum { CLS_R3 = 0, CLS_R5 = 1, CLS_X1 = 2, NCLS = 3 };
+const int R3_TW[3] = {32, 64, 16}, R3_TH[3] = {8, 4, 16};
+
+}  // namespace
+
+struct bf_batch {
+  int count;
+  int device;
+  std::vector<const bf_graph*> graphs;
+  std::vector<int> cls;              // class of each instance
+  Geom<float> geom[NCLS];
+  bool has[NCLS];
+  int r3_variant;                    // tile shape of the image class (autotuned)
+  int njobs[NCLS];
+  BInst* d_inst;                     // [count]
+  BJob* d_jobs[NCLS];
+  double* d_part[NCLS];
+  void* d_vec;                       // r, s, q, p0, p1 of every instance
+  std::vector<BInst> h_inst;
+  // captured run
+  cudaGraphExec_t exec;
+  uint64_t graph_kernels;            // kernels in the captured graph
+  int exec_kmax;
+  bf_cg_opts exec_opts;
+  int exec_variant;
+};
+
+namespace {
+
+template <class SH>
+size_t bsmem() { return 3 * SH::hp * sizeof(float); }
+
+int build_jobs(bf_batch* b) {
+  std::vector<BJob> jobs[NCLS];
+  for (int c = 0; c < NCLS; ++c) jobs[c].clear();
+  for (int i = 0; i < b->count; ++i) {
+    const int c = b->cls[i];
+    const int tw = (c == CLS_R3) ? R3_TW[b->r3_variant] : (c == CLS_R5 ? ShapeR5::tw : ShapeX1::tw);
+    const int th = (c == CLS_R3) ? R3_TH[b->r3_variant] : (c == CLS_R5 ? ShapeR5::th : ShapeX1::th);
+    BInst& in = b->h_inst[i];
+    in.job0 = (int)jobs[c].size();
+    for (int by = 0; by < in.ny; by += th)
+      for (int bx = 0; bx < in.nx; bx += tw) jobs[c].push_back(BJob{i, bx, by});
+    in.njobs = (int)jobs[c].size() - in.job0;
+  }
+  for (int c = 0; c < NCLS; ++c) {
+    if (b->d_jobs[c]) cudaFree(b->d_jobs[c]);
+    if (b->d_part[c]) cudaFree(b->d_part[c]);
+    b->d_jobs[c] = nullptr;
+    b->d_part[c] = nullptr;
+    b->njobs[c] = (int)jobs[c].size();
+    if (jobs[c].empty()) continue;
+    BF_CUDA(cudaMalloc(&b->d_jobs[c], jobs[c].size() * sizeof(BJob)));
+    BF_CUDA(cudaMalloc(&b->d_part[c], jobs[c].size() * 4 * sizeof(double)));
+    BF_CUDA(cudaMemcpy(b->d_jobs[c], jobs[c].data(), jobs[c].size() * sizeof(BJob), cudaMemcpyHostToDevice));
+  }
+  return BF_OK;
+}
+
+BArgs make_args(const bf_batch* b, int c, const bf_cg_opts& o) {
+  BArgs a;
+  a.inst = b->d_inst;
+  a.jobs = b->d_jobs[c];
+  a.partials = b->d_part[c];
+  a.shift = (float)o.shift;
+  a.tol2 = o.tol > 0 ? o.tol * o.tol : 0.0;
+  a.beta_mode = o.beta;
+  return a;
+}
+
+template <class SH>
+void launch_phase(int phase, const bf_batch* b, int c, const BArgs& a, cudaStream_t s) {
+  const unsigned nj = (unsigned)b->njobs[c];
+  if (!nj) return;
+  if (phase == 0) BF_LAUNCH(k_bcg_init<SH><<<nj, BF_THREADS, bsmem<SH>(), s>>>(b->geom[c], a));
+  else if (phase == 1) BF_LAUNCH(k_bcg_dir<SH><<<nj, BF_THREADS, bsmem<SH>(), s>>>(b->geom[c], a));
+  else BF_LAUNCH(k_bcg_update<SH><<<nj, BF_THREADS, 0, s>>>(a));
+}
+
+void launch_all(int phase, const bf_batch* b, const bf_cg_opts& o, int r3v, cudaStream_t s) {
+  for (int c = 0; c < NCLS; ++c) {
+    if (!b->has[c]) continue;
+    const BArgs a = make_args(b, c, o);
+    if (c == CLS_R3) {
+      if (r3v == 0) launch_phase<R3_32x8>(phase, b, c, a, s);
+      else if (r3v == 1) launch_phase<R3_64x4>(phase, b, c, a, s);
+      else launch_phase<R3_16x16>(phase, b, c, a, s);
+    } else if (c == CLS_R5) {
+      launch_phase<ShapeR5>(phase, b, c, a, s);
+    } else {
+      launch_phase<ShapeX1>(phase, b, c, a, s);
+    }
+  }
+}
+
+int enqueue_run(const bf_batch* b, int kmax, const bf_cg_opts& o, cudaStream_t s) {
+  launch_all(0, b, o, b->r3_variant, s);
+  for (int it = 0; it < kmax; ++it) {
+    launch_all(1, b, o, b->r3_variant, s);
+    launch_all(2, b, o, b->r3_variant, s);
+  }
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+bool same_opts(const bf_cg_opts& a, const bf_cg_opts& b) {
+  return a.precond == b.precond && a.beta == b.beta && a.shift == b.shift && a.tol == b.tol;
+}
+
+}  // namespace
+
+extern "C" int bf_batch_create(const bf_graph* const* graphs, int count, bf_batch** out) {
+  if (!graphs || !out || count < 1) return bf_fail(BF_EINVAL, "bf_batch_create: need graphs and count >= 1");
+  *out = nullptr;
+  bf_batch* b = new bf_batch();
+  b->count = count;
+  b->graphs.assign(graphs, graphs + count);
+  b->cls.resize(count);
+  b->h_inst.resize(count);
+  b->r3_variant = 0;
+  b->d_inst = nullptr;
+  b->d_vec = nullptr;
+  b->exec = nullptr;
+  b->graph_kernels = 0;
+  b->exec_kmax = -1;
+  b->exec_variant = -1;
+  for (int c = 0; c < NCLS; ++c) {
+    b->has[c] = false;
+    b->d_jobs[c] = nullptr;
+    b->d_part[c] = nullptr;
+    b->njobs[c] = 0;
+  }
+  cudaGetDevice(&b->device);
+  size_t vtot = 0;
+  for (int i = 0; i < count; ++i) {
+    const bf_graph* g = graphs[i];
+    if (!g || g->esize != 4 || g->p.weight_mode != BF_W_ONTHEFLY) {
+      delete b;
+      return bf_fail(BF_EINVAL, "bf_batch_create: every graph must be FP32 with on-the-fly weights");
+    }
+    const int fs = fast_shape(g);
+    const int c = fs == FAST_R3_2D ? CLS_R3 : fs == FAST_R5_1D ? CLS_R5 : fs == FAST_CROSS1 ? CLS_X1 : -1;
+    if (c < 0) {
+      delete b;
+      return bf_fail(BF_EINVAL, "bf_batch_create: window must be 7x7 (images), 11 taps (signals) or the 5-point cross");
+    }
+    if (!b->has[c]) {
+      b->has[c] = true;
+      b->geom[c] = g->gf;
+    } else {
+      const Geom<float>& r = b->geom[c];
+      bool same = r.a_r == g->gf.a_r;
+      for (int t = 0; t < BF_MAX_BOX && same; ++t) same = (r.ls[t] == g->gf.ls[t]);
+      if (!same) {
+        delete b;
+        return bf_fail(BF_EINVAL, "bf_batch_create: instances of one window shape must share sigma_s and sigma_r");
+      }
+    }
+    b->cls[i] = c;
+    BInst& in = b->h_inst[i];
+    memset(&in, 0, sizeof(in));
+    in.nx = g->nx;
+    in.ny = g->ny;
+    in.n = g->n;
+    in.guide = (const float*)g->guide;
+    vtot += ((size_t)g->n * sizeof(float) + 255) & ~(size_t)255;
+  }
+  cudaError_t e = cudaMalloc(&b->d_vec, 5 * vtot);
+  if (e != cudaSuccess) {
+    delete b;
+    return bf_cuda_fail(e, "cudaMalloc(batch vectors)");
+  }
+  char* p = (char*)b->d_vec;
+  for (int i = 0; i < count; ++i) {
+    const size_t vb = ((size_t)b->h_inst[i].n * sizeof(float) + 255) & ~(size_t)255;
+    BInst& in = b->h_inst[i];
+    in.r = (float*)p; p += vb;
+    in.s = (float*)p; p += vb;
+    in.q = (float*)p; p += vb;
+    in.p[0] = (float*)p; p += vb;
+    in.p[1] = (float*)p; p += vb;
+  }
+  e = cudaMalloc(&b->d_inst, count * sizeof(BInst));
+  if (e != cudaSuccess) {
+    cudaFree(b->d_vec);
+    delete b;
+    return bf_cuda_fail(e, "cudaMalloc(batch instances)");
+  }
+  int rc = build_jobs(b);
+  if (rc) return rc;
+  *out = b;
+  return BF_OK;
+}
+
+extern "C" int bf_batch_free(bf_batch* b) {
+  if (!b) return BF_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (int c = 0; c < NCLS; ++c) {
+    if (b->d_jobs[c]) cudaFree(b->d_jobs[c]);
+    if (b->d_part[c]) cudaFree(b->d_part[c]);
+  }
+  if (b->d_inst) cudaFree(b->d_inst);
+  if (b->d_vec) cudaFree(b->d_vec);
+  delete b;
+  return BF_OK;
+}
+
+extern "C" int bf_batch_tiles(const bf_batch* b, int64_t* tiles_out, int* variant_out) {
+  if (!b) return bf_fail(BF_EINVAL, "bf_batch_tiles: NULL batch");
+  if (tiles_out) *tiles_out = (int64_t)b->njobs[0] + b->njobs[1] + b->njobs[2];
+  if (variant_out) *variant_out = b->r3_variant;
+  return BF_OK;
+}
+
+static int batch_upload(bf_batch* b, const float* const* x0, float* const* x_out, const bf_cg_opts& o,
+                        cudaStream_t s) {
+  for (int i = 0; i < b->count; ++i) {
+    BInst& in = b->h_inst[i];
+    const bf_graph* g = b->graphs[i];
+    in.x0 = x0[i];
+    in.x = x_out[i];
+    in.dinv = o.precond == BF_PRECOND_JACOBI ? (const float*)g->dinv : nullptr;
+    in.counter = 0;
+    memset(&in.st, 0, sizeof(in.st));
+  }
+  BF_CUDA(cudaMemcpyAsync(b->d_inst, b->h_inst.data(), b->count * sizeof(BInst), cudaMemcpyHostToDevice, s));
+  return BF_OK;
+}
+
+extern "C" int bf_batch_cg(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
+                           const bf_cg_opts* opts, bf_info* infos, void* stream) {
+  if (!b || !x0 || !x_out) return bf_fail(BF_EINVAL, "bf_batch_cg: NULL argument");
+  if (kmax < 0) return bf_fail(BF_EINVAL, "bf_batch_cg: kmax < 0");
+  bf_cg_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY)
+    return bf_fail(BF_EINVAL, "bf_batch_cg: precond must be Jacobi or identity");
+  if (o.beta != BF_BETA_FLEXIBLE && o.beta != BF_BETA_PRINTED) return bf_fail(BF_EINVAL, "bf_batch_cg: bad beta");
+  if (!(o.shift >= 0.0) || !(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "bf_batch_cg: shift and tol must be >= 0");
+  for (int i = 0; i < b->count; ++i)
+    if (!x0[i] || !x_out[i]) return bf_fail(BF_EINVAL, "bf_batch_cg: NULL instance vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = batch_upload(b, x0, x_out, o, s);
+  if (rc) return rc;
+  // the whole run is one CUDA graph, captured once per (kmax, options, tile shape)
+  if (!b->exec || b->exec_kmax != kmax || !same_opts(b->exec_opts, o) || b->exec_variant != b->r3_variant) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    cudaStream_t cs;
+    BF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    BF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const uint64_t c0 = bf_launch_count();
+    rc = enqueue_run(b, kmax, o, cs);
+    b->graph_kernels = bf_launch_count() - c0;   // captured, not run: counted per replay
+    bf_count_launches(-(int)b->graph_kernels);
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    if (e != cudaSuccess) return bf_cuda_fail(e, "cudaStreamEndCapture(batch)");
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bf_cuda_fail(e, "cudaGraphInstantiate(batch)");
+    b->exec_kmax = kmax;
+    b->exec_opts = o;
+    b->exec_variant = b->r3_variant;
+  }
+  BF_CUDA(cudaGraphLaunch(b->exec, s));
+  bf_count_launches((int)b->graph_kernels);
+  if (infos) {
+    std::vector<BInst> h(b->count);
+    BF_CUDA(cudaMemcpyAsync(h.data(), b->d_inst, b->count * sizeof(BInst), cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < b->count; ++i) {
+      const BState& st = h[i].st;
+      infos[i].iters = st.iter;
+      infos[i].status = st.status == B_CONV ? BF_CG_CONVERGED : (st.status == B_BREAK ? BF_CG_BREAKDOWN : 0);
+      infos[i].restarts = 0;
+      infos[i].reserved = st.status == B_NONFINITE ? 1 : 0;
+      infos[i].rnorm = sqrt(st.rr);
+      infos[i].ref = sqrt(st.ref2);
+    }
+  }
+  return BF_OK;
+}
+
+// Autotune the image class's tile shape: time `iters` CG iterations of the batch with each
+// candidate (32 x 8, 64 x 4, 16 x 16) on the given vectors and keep the fastest.
+extern "C" int bf_batch_tune(bf_batch* b, const float* const* x0, float* const* x_out, int iters,
+                             float* ms_out, void* stream) {
+  if (!b || !x0 || !x_out) return bf_fail(BF_EINVAL, "bf_batch_tune: NULL argument");
+  if (!b->has[CLS_R3]) return BF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bf_cg_opts o;
+  memset(&o, 0, sizeof(o));
+  cudaEvent_t e0, e1;
+  BF_CUDA(cudaEventCreate(&e0));
+  BF_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestv = 0;
+  for (int v = 0; v < 3; ++v) {
+    b->r3_variant = v;
+    int rc = build_jobs(b);
+    if (rc) return rc;
+    for (int rep = 0; rep < 2; ++rep) {          // first repetition warms up
+      if ((rc = batch_upload(b, x0, x_out, o, s))) return rc;
+      BF_CUDA(cudaEventRecord(e0, s));
+      if ((rc = enqueue_run(b, iters, o, s))) return rc;
+      BF_CUDA(cudaEventRecord(e1, s));
+    }
+    BF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    BF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms_out) ms_out[v] = ms;
+    if (ms < best) {
+      best = ms;
+      bestv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->r3_variant = bestv;
+  return build_jobs(b);
+}

@@ -11,13 +11,14 @@
 
 #include "bf_internal.cuh"
 
-template <int RX, int RY, bool CROSS>
-struct WinShape {
+// Window of radii RX, RY (CROSS: the 5-point-like cross) on tiles of TW x TH pixels.
+template <int RX, int RY, bool CROSS, int TW = (RY == 0 ? BF_TW1 : BF_TW2), int TH = (RY == 0 ? 1 : BF_TH2)>
+struct WinShapeT {
   static constexpr int rx = RX, ry = RY;
   static constexpr bool cross = CROSS;
   static constexpr bool one_d = (RY == 0);
-  static constexpr int tw = one_d ? BF_TW1 : BF_TW2;
-  static constexpr int th = one_d ? 1 : BF_TH2;
+  static constexpr int tw = TW;
+  static constexpr int th = TH;
   static constexpr int hw = tw + 2 * RX;
   static constexpr int hh = th + 2 * RY;
   static constexpr int hp = hw * hh;
@@ -120,6 +121,9 @@ __device__ __forceinline__ void window_fast(const Geom<float>& g, int hp0, int64
     for (int c = 0; c < K / 2; ++c) f2_unpack(a2[c], acc[2 * c], acc[2 * c + 1]);
   }
 }
+
+template <int RX, int RY, bool CROSS>
+using WinShape = WinShapeT<RX, RY, CROSS>;
 
 // Which specialised shape (if any) a graph's window has.
 enum { FAST_NONE = 0, FAST_R3_2D = 1, FAST_R5_1D = 2, FAST_CROSS1 = 3 };

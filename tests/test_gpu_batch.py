@@ -1,0 +1,87 @@
+"""Batched CG (bf_batch: one work list over many uneven instances, one CUDA graph) against
+the FP64 oracle per instance and against the single-instance GPU path."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import solvers
+from tests.gpu_helpers import TOL_F32, bf, dev, host, image_case, make_pair, rel_l2, signal_case
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed(seed=0):
+    """Images of ragged sizes (7x7 window), signals (11 taps) and one 5-point-lattice image."""
+    cases = []
+    for (ny, nx) in [(40, 37), (64, 64), (17, 100), (9, 9)]:
+        _, noisy = image_case(ny, nx, seed + ny)
+        G, O = make_pair(noisy, 3, 2.0, 0.08)
+        cases.append((G, O, noisy.ravel()))
+    for n in (500, 1234):
+        _, noisy = signal_case(n, seed + n, dtype=np.float32)
+        G, O = make_pair(noisy, 5, 3.0, 0.1)
+        cases.append((G, O, noisy.ravel()))
+    _, noisy = image_case(30, 33, seed + 7)
+    G, O = make_pair(noisy, 1, 2.0, 0.1, window="cross")
+    cases.append((G, O, noisy.ravel()))
+    return cases
+
+
+@pytest.mark.parametrize("shift", [0.0, 1e-2])
+def test_batched_cg_matches_oracle_and_single_path(shift):
+    cases = mixed()
+    B = bf().Batch([c[0] for c in cases])
+    x0s = [dev(c[2]) for c in cases]
+    outs, infos = B.cg(x0s, 12, shift=shift)
+    for (G, O, x0), x, info in zip(cases, outs, infos):
+        ref = solvers.cg(O, x0.astype(np.float64), 12, shift=shift)
+        assert info.iters == ref["iters"]
+        assert rel_l2(host(x), ref["x"]) <= TOL_F32
+        single, sinfo, _ = bf().cg_filter(G, dev(x0), 12, shift=shift)
+        assert rel_l2(host(x), host(single)) <= 1e-6
+        assert sinfo.iters == info.iters
+
+
+def test_batched_cg_with_tolerance_stops_each_instance():
+    cases = mixed(seed=3)
+    B = bf().Batch([c[0] for c in cases])
+    x0s = [dev(c[2]) for c in cases]
+    outs, infos = B.cg(x0s, 200, shift=1e-1, tol=1e-4)
+    for (G, O, x0), x, info in zip(cases, outs, infos):
+        single, sinfo, _ = bf().cg_filter(G, dev(x0), 200, shift=1e-1, tol=1e-4)
+        assert info.status == sinfo.status == "converged"
+        assert info.iters == sinfo.iters
+        assert rel_l2(host(x), host(single)) <= 1e-6
+
+
+def test_graph_replay_and_autotune_keep_results():
+    cases = mixed(seed=5)
+    B = bf().Batch([c[0] for c in cases])
+    x0s = [dev(c[2]) for c in cases]
+    first, _ = B.cg(x0s, 8)
+    x0b = [x * 0.5 + 0.25 for x in x0s]
+    second, _ = B.cg(x0b, 8)                 # replay of the captured graph, new inputs
+    for (G, O, x0), x in zip(cases, second):
+        ref = solvers.cg(O, 0.5 * x0.astype(np.float64) + 0.25, 8)
+        assert rel_l2(host(x), ref["x"]) <= TOL_F32
+    ms = B.tune(x0s, iters=3)
+    assert len(ms) == 3 and all(m > 0 for m in ms)
+    tiles, variant = B.tiles()
+    assert variant == int(np.argmin(ms)) and tiles > 0
+    tuned, _ = B.cg(x0s, 8)
+    for a, b in zip(first, tuned):
+        assert rel_l2(host(b), host(a)) <= 1e-6
+
+
+def test_batch_rejects_unsupported_graphs():
+    _, noisy = image_case(16, 16, 1)
+    G64 = bf().bf_weights(dev(noisy, torch.float64), 3, 2.0, 0.08)
+    with pytest.raises(bf().BFError):
+        bf().Batch([G64])
+    Ga = bf().bf_weights(dev(noisy), 3, 2.0, 0.08)
+    Gb = bf().bf_weights(dev(noisy), 3, 2.5, 0.08)
+    with pytest.raises(bf().BFError):
+        bf().Batch([Ga, Gb])
+    Gs = bf().bf_weights(dev(noisy), 3, 2.0, 0.08, weight_mode="stored_f32")
+    with pytest.raises(bf().BFError):
+        bf().Batch([Gs])
