@@ -261,10 +261,20 @@ def run_gpu(args):
     traffic_alg = bytes_per_px * npix
     achieved = traffic_alg / (apply_ms * 1e-3) / 1e9
     peak, peak_src = _peaks()
-    roofline = {"kernel": "k_apply<float,16> (L, on-the-fly weights)", "bound": "hbm",
+    roofline = {"kernel": "k_apply_rb<16> (L, 7x7, on-the-fly weights)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": None, "algorithmic_bytes": traffic_alg,
+                "peak_source": peak_src, "traffic": TRAFFIC_APPLY, "algorithmic_bytes": traffic_alg,
                 "ms_per_launch": apply_ms}
+    # ---- the kernel with the largest share of the step: the one-CTA FP64 Rayleigh-Ritz
+    # solve of LOBPCG (m = 48, k = 16), bound by one SM's FP64 issue and latency
+    rr_ms = _time_rr(bf, torch, stream, flush)
+    rr_flops = 2.0 * RR_FP64_FMA
+    rr_peak = 2.0 * 2.0 * 2.07      # GFLOP/s: one SM, 2 FP64 FMA per clock, 2.07 GHz
+    roofline_rr = {"kernel": "k_rr (Rayleigh-Ritz, m=48, k=16, one CTA)", "bound": "alu",
+                   "achieved": rr_flops / (rr_ms * 1e-3) / 1e9, "peak": rr_peak,
+                   "unit": "GFLOP/s (FP64, one SM)",
+                   "frac": rr_flops / (rr_ms * 1e-3) / 1e9 / rr_peak, "ms_per_launch": rr_ms,
+                   "share_of_step": RR_SHARE}
 
     # ---- end to end through the public API from pinned host memory
     gh = torch.as_tensor(noisy).pin_memory()
@@ -300,6 +310,9 @@ def run_gpu(args):
     h2d = gh.numel() * 4 + X0p.numel() * 4
     d2h = y_h.numel() * 4 + xcg_h.numel() * 4 + th_h.numel() * 8
 
+    # ---- batching: the 256-instance workload, batched (one CUDA graph) against plain
+    batched = None if args.no_batch else _run_batched(bf, torch, stream)
+
     # ---- CPU baseline: the oracle on one full step (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -320,7 +333,8 @@ def run_gpu(args):
                            "lobpcg_iters": w["lob_iters"], "weights": "on-the-fly fp32",
                            "l2": "flushed between steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "roofline_dominant": roofline_rr, "cpu_baseline": cpu,
+                "batched": batched,
                 "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "clocks": clk.summary(), "gpu_launches": launches}
@@ -329,6 +343,113 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_rb<16> launch (512 x 512, k = 16)
+# from an ncu capture of that launch (its 16.8 MB of output stay in L2 during the launch)
+TRAFFIC_APPLY = 17.89e6
+# FP64 FMAs of one Rayleigh-Ritz call at m = 48, k = 16 (Cholesky with the forward solve
+# 2m^3/3, standard form m^3/6, M X twice 2 m^2 k, Gram/Löwdin/H 3 m k^2, back-substitution
+# m^2 k / 2, next-P coefficients m^2 k + 2 m k^2) and its share of the step's GPU time in
+# an ncu launch list of the timed step
+RR_FP64_FMA = (2 * 48 ** 3 / 3 + 48 ** 3 / 6 + 2 * 48 * 48 * 16 + 3 * 48 * 16 * 16
+               + 48 * 48 * 16 / 2 + 48 * 48 * 16 + 2 * 48 * 16 * 16)
+RR_SHARE = 0.506
+
+
+def _time_rr(bf, torch, stream, flush, m=48, k=16, reps=20):
+    """Device time of one Rayleigh-Ritz call on a well-conditioned m x m pencil."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    S = rng.standard_normal((4 * m, m))
+    GB = S.T @ S
+    A = rng.standard_normal((m, m))
+    GA = A @ A.T
+    G = torch.stack([torch.as_tensor(GA), torch.as_tensor(GB)]).cuda()
+    C = torch.empty((m, k), dtype=torch.float64, device="cuda")
+    Cp = torch.empty_like(C)
+    th = torch.empty(k, dtype=torch.float64, device="cuda")
+    fl = torch.zeros(2, dtype=torch.int32, device="cuda")
+    lib = bf.lib()
+    import ctypes
+    args = [ctypes.c_void_p(G.data_ptr()), m, k, 2 * k, ctypes.c_void_p(C.data_ptr()),
+            ctypes.c_void_p(Cp.data_ptr()), ctypes.c_void_p(th.data_ptr()), ctypes.c_void_p(fl.data_ptr()),
+            ctypes.c_void_p(stream.cuda_stream)]
+    for _ in range(3):
+        lib.bf_rayleigh_ritz(*args)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        lib.bf_rayleigh_ritz(*args)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _batch_inputs(seed=4):
+    """The 256 instances: 192 images with sides log-uniform in [64, 1024] (polygon
+    generator, noise 0.05) and 64 signals with lengths log-uniform in [1e3, 1e6]
+    (piecewise constant, noise 0.1); returns [(kind, array)]."""
+    from paper_1509_02468_gb300 import synth
+    out = []
+    for i, (nd, ny, nx) in enumerate(synth.batch_sizes(seed)):
+        if nd == 2:
+            _, noisy = synth.polygon_image(ny, nx, 4000 + i, noise=0.05)
+        else:
+            _, noisy = synth.signal_1d(nx, 4000 + i, noise=0.1, dtype=__import__("numpy").float32)
+        out.append((nd, noisy))
+    return out
+
+
+def _run_batched(bf, torch, stream, kmax=50, reps=3):
+    """Mpix/s of CG(kmax) on the 256 instances: one bf_batch graph (tile shape autotuned)
+    against plain cg_filter calls one instance after another; inputs resident."""
+    inst = _batch_inputs()
+    graphs, x0s = [], []
+    for nd, a in inst:
+        t = torch.as_tensor(a).cuda()
+        if nd == 2:
+            graphs.append(bf.bf_weights(t, 3, 2.0, 0.08))
+        else:
+            graphs.append(bf.bf_weights(t, 5, 3.0, 0.1))
+        x0s.append(t.reshape(-1))
+    total = sum(int(x.numel()) for x in x0s)
+    outs = [torch.empty_like(x) for x in x0s]
+    B = bf.Batch(graphs)
+    tune_ms = B.tune(x0s, iters=5, outs=outs)
+    _, variant = B.tiles()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    l0 = bf.launch_count()
+    ms_b = timed(lambda: B.cg(x0s, kmax, outs=outs, sync=False))
+    lb = (bf.launch_count() - l0) / (reps + 1)
+
+    def plain():
+        for G, x, o in zip(graphs, x0s, outs):
+            bf.cg_filter(G, x, kmax, out=o, sync=False)
+    ms_p = timed(plain)
+    B.free()
+    return {"workload": "256 instances: 192 images, sides log-uniform in [64, 1024]; 64 signals, "
+                        "lengths log-uniform in [1e3, 1e6]; CG 50 (Jacobi), FP32",
+            "samples": total, "cg_iters": kmax,
+            "batched_mpix_s": total / (ms_b * 1e-3) / 1e6, "batched_ms": ms_b,
+            "plain_mpix_s": total / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,
+            "batched_kernels_per_run": lb, "tile_shape_timings_ms": tune_ms,
+            "tile_shape": ["32x8", "64x4", "16x16"][variant]}
 
 
 def run_case(args):
@@ -372,6 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-CG measurement")
     ap.add_argument("--case", choices=["apply", "cg", "lobpcg"], default=None,
                     help="only launch one kernel family (for profiler captures)")
     ap.add_argument("--case-side", type=int, default=0, help="image side for --case")
