@@ -70,6 +70,10 @@ extern "C" {
 #define BF_PENCIL_D       0   /* LOBPCG for L x = lambda D x (Algorithm 3)                */
 #define BF_PENCIL_I       1   /* LOBPCG for L x = lambda x                                */
 
+#define BF_GRAM_FP32      0   /* FP32 products in runs of 16 pixels, folded into FP64     */
+#define BF_GRAM_BF16      1   /* tensor cores (tcgen05): BF16 operands, FP32 accumulation */
+#define BF_GRAM_BF16X3    2   /* tensor cores: x = hi + lo in BF16, hi*hi + hi*lo + lo*hi */
+
 #define BF_CG_CONVERGED   1   /* bf_info.status: stopped by s^T r = 0 or by tol           */
 #define BF_CG_BREAKDOWN   2   /* bf_info.status: stopped by p^T q <= 0                    */
 
@@ -111,7 +115,7 @@ typedef struct bf_lobpcg_opts {
   int32_t pencil;        /* BF_PENCIL_*                                                     */
   int32_t precond;       /* BF_PRECOND_*                                                    */
   int32_t constrain_e;   /* 1: keep X B-orthogonal to the constant vector e (Section 6)     */
-  int32_t reserved;
+  int32_t gram;          /* BF_GRAM_*: precision of the Gram products S^T [A S, B S]        */
   double  tol;           /* > 0: stop once max_j ||L x_j - theta_j B x_j|| / ||B x_j|| <= tol */
   double* theta_hist;    /* optional device array [(kmax + 1) * k]: Ritz values per step    */
   const bf_net* net;     /* BF_PRECOND_NET: the preconditioner (else ignored)               */

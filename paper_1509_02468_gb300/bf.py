@@ -23,6 +23,7 @@ OPS = {"W": 0, "L": 1, "DINV_W": 2, "D": 3, "NSYM": 4, "NDIAGL": 5}
 PRECONDS = {"jacobi": 0, "identity": 1, "net": 2}
 BETAS = {"flexible": 0, "printed": 1}
 PENCILS = {"D": 0, "I": 1}
+GRAMS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 STATUS = {0: "ran", 1: "converged", 2: "breakdown"}
 
 
@@ -54,7 +55,7 @@ class bf_cg_opts(ctypes.Structure):
 
 class bf_lobpcg_opts(ctypes.Structure):
     _fields_ = [("pencil", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("constrain_e", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("constrain_e", ctypes.c_int32), ("gram", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("theta_hist", ctypes.c_void_p),
                 ("net", ctypes.c_void_p)]
 
@@ -88,6 +89,7 @@ def _load():
         "bf_net_accumulate": [vp, vp, vp, vp, vp],
         "bf_net_grad": [vp, vp, vp, vp],
         "bf_net_adam": [vp, ctypes.c_float, ctypes.c_float, vp],
+        "bf_gram_tc_test": [vp, vp, vp, vp, vp, vp, vp, i32, i32, i64, i32, vp, vp],
         "bf_batch_create": [vp, i32, ctypes.POINTER(vp)],
         "bf_batch_free": [vp],
         "bf_batch_cg": [vp, vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, vp],
@@ -267,8 +269,8 @@ def cg_filter_noalloc(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jac
 def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
                   precond: str = "jacobi", constrain: bool = False, tol: float = 0.0,
                   want_X: bool = True, want_y: bool = True, theta_hist: bool = False,
-                  sync: bool = True, stream=None, net: "Net | None" = None):
-    """Algorithm 3 on a block X0 of shape (n, k).  Returns a dict with X, theta, resid, y,
+                  sync: bool = True, stream=None, net: "Net | None" = None, gram: str = "fp32"):
+    """Algorithm 3 on a block X0 of shape (n, k).  gram: "fp32" | "bf16" | "bf16x3" (tensor cores).  Returns a dict with X, theta, resid, y,
     theta_hist and info (entries None when not requested)."""
     Xb, k = _as_block(X0)
     dev = X0.device
@@ -278,7 +280,7 @@ def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
     resid = torch.empty(k, dtype=torch.float64, device=dev)
     th = torch.full(((kmax + 1) * k,), float("nan"), dtype=torch.float64, device=dev) if theta_hist else None
     o = bf_lobpcg_opts(pencil=PENCILS[pencil], precond=PRECONDS[precond],
-                       constrain_e=int(constrain), reserved=0, tol=tol,
+                       constrain_e=int(constrain), gram=GRAMS[gram], tol=tol,
                        theta_hist=th.data_ptr() if th is not None else None,
                        net=net.handle if net is not None else None)
     info = bf_info() if sync else None
@@ -419,3 +421,16 @@ class Batch:
         t, v = ctypes.c_int64(), ctypes.c_int32()
         _check(_lib.bf_batch_tiles(self.handle, ctypes.byref(t), ctypes.byref(v)))
         return t.value, v.value
+
+
+def gram_tc(S_blocks, AS_blocks, b=None, split: bool = False, stream=None):
+    """Tensor-core Gram (include/bf_testing.h): returns (S^T AS, S^T B S) as float64 tensors
+    for lists of 1..3 pixel-major float32 blocks of shape (n, k)."""
+    nblk = len(S_blocks)
+    n, k = S_blocks[0].shape
+    m = nblk * k
+    G = torch.empty((2, m, m), dtype=torch.float64, device=S_blocks[0].device)
+    Sp = [_ptr(x) for x in S_blocks] + [None] * (3 - nblk)
+    Ap = [_ptr(x) for x in AS_blocks] + [None] * (3 - nblk)
+    _check(_lib.bf_gram_tc_test(*Sp, *Ap, _ptr(b), nblk, k, n, int(split), _ptr(G), _stream(stream)))
+    return G[0], G[1]

@@ -1,0 +1,349 @@
+// Gram products of the Rayleigh-Ritz step of block LOBPCG (Algorithm 3, Section 6) on the
+// fifth-generation tensor cores: [G_A | G_B] = S^T [A S | B S] for the trial basis
+// S = [X W P] (n x m, m = 2k or 3k <= 96), as one BF16 GEMM with FP32 accumulation
+// (M = 128 rows of S^T, N = 2m rounded up to 16, K = the pixels), split over the CTAs by
+// chunks of 64 pixels.
+//
+// Per chunk the CTA converts S, A S and B S = diag(b) S from FP32 (pixel-major blocks) to
+// BF16 and writes them transposed into shared memory in the K-major, unswizzled canonical
+// layout (8-row x 16-byte core matrices, 128 B apart along K, 1024 B apart along rows);
+// one thread issues the tcgen05.mma instructions, whose accumulator stays in tensor
+// memory for the whole split-K range; tcgen05.commit arrives on an mbarrier per buffer,
+// so staging of the next chunk overlaps the MMAs of the current one.  With `split` each
+// operand is x = hi + lo (both BF16) and the products hi*hi + hi*lo + lo*hi are
+// accumulated (about 16 significant bits).  At the end the accumulator is read with
+// tcgen05.ld and the FP32 partials of all CTAs are summed in FP64.
+//
+// Every mbarrier wait is bounded: on a timeout the kernel records an error, waits once
+// more (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "bf_internal.cuh"
+
+#define TC_THREADS 256
+#define TC_KT 64                   // pixels per chunk (K per stage)
+#define TC_M 128                   // MMA rows (rows of S^T, m padded)
+#define TC_TMEM_COLS 256           // tensor-memory columns allocated (>= N)
+#define TC_WAIT_ITERS (1 << 22)    // bound on mbarrier polls
+
+namespace {
+
+struct TcArgs {
+  const float* S[3];
+  const float* AS[3];
+  const float* b;                  // B diagonal (NULL: I)
+  int nblk, k, m, N;
+  int64_t n;
+  float* partials;                 // [gridDim.x][m][2m]
+  const int* status;               // LOBPCG status: nonzero = stopped
+  int* err;                        // set to 4 on a wait timeout
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < TC_WAIT_ITERS; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride (row-group) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N, int M) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 8 consecutive accumulator columns of this thread's lane (32x32b shape).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of (row, pixel) in a K-major unswizzled operand tile of TC_KT pixels.
+__device__ __forceinline__ uint32_t tc_off(int row, int pix) {
+  return (uint32_t)((row >> 3) * 1024 + (pix >> 3) * 128 + (row & 7) * 16 + (pix & 7) * 2);
+}
+
+template <bool SPLIT>
+__device__ __forceinline__ void put_pair(unsigned char* hi, unsigned char* lo, int row, int pix, float x0, float x1) {
+  const uint32_t off = tc_off(row, pix);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+  if (SPLIT) {
+    const float2 hf = __bfloat1622float2(h);
+    *reinterpret_cast<__nv_bfloat162*>(lo + off) = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  }
+}
+
+// Stage chunk c (pixels c * TC_KT ...) into the operand tiles: A rows = columns of S,
+// B rows = columns of A S, then of B S.
+template <bool SPLIT>
+__device__ void tc_stage(const TcArgs& a, int64_t c, unsigned char* Ahi, unsigned char* Alo, unsigned char* Bhi,
+                         unsigned char* Blo) {
+  const int kq = a.k >> 2;
+  const int per = a.nblk * (TC_KT / 2) * kq;
+  const int64_t p0 = c * TC_KT;
+  for (int t = threadIdx.x; t < 2 * per; t += TC_THREADS) {
+    const bool is_as = t >= per;
+    const int tt = is_as ? t - per : t;
+    const int cq = tt % kq, rest = tt / kq;
+    const int pp = rest % (TC_KT / 2), bk = rest / (TC_KT / 2);
+    const int64_t p = p0 + 2 * pp;
+    const float* src = is_as ? a.AS[bk] : a.S[bk];
+    float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), v1 = v0;
+    if (p < a.n) v0 = *reinterpret_cast<const float4*>(src + p * a.k + 4 * cq);
+    if (p + 1 < a.n) v1 = *reinterpret_cast<const float4*>(src + (p + 1) * a.k + 4 * cq);
+    const int col = bk * a.k + 4 * cq;
+    const float x0[4] = {v0.x, v0.y, v0.z, v0.w}, x1[4] = {v1.x, v1.y, v1.z, v1.w};
+    if (!is_as) {
+      const float b0 = (a.b && p < a.n) ? a.b[p] : 1.0f;
+      const float b1 = (a.b && p + 1 < a.n) ? a.b[p + 1] : 1.0f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        put_pair<SPLIT>(Ahi, Alo, col + i, 2 * pp, x0[i], x1[i]);
+        put_pair<SPLIT>(Bhi, Blo, a.m + col + i, 2 * pp, b0 * x0[i], b1 * x1[i]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) put_pair<SPLIT>(Bhi, Blo, col + i, 2 * pp, x0[i], x1[i]);
+    }
+  }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const TcArgs a) {
+  if (a.status && *a.status != 0) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_sh;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const uint32_t a_bytes = TC_M * TC_KT * 2;                 // 16 KB
+  const uint32_t b_bytes = (uint32_t)a.N * TC_KT * 2;
+  const uint32_t half = a_bytes + b_bytes;                   // hi (or lo) part of one buffer
+  const uint32_t buf_bytes = (SPLIT ? 2 : 1) * half;
+  unsigned char* bufp[2] = {smem, smem + buf_bytes};
+  for (uint32_t i = tid; i < 2 * buf_bytes / 16; i += TC_THREADS)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);   // padding rows stay zero
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  const int64_t nch = (a.n + TC_KT - 1) / TC_KT;
+  const int my = (int)((nch - blockIdx.x + gridDim.x - 1) / gridDim.x);   // chunks blockIdx.x + j * grid
+  const uint32_t idesc = idesc_bf16(a.N, TC_M);
+  bool ok = true;
+  uint32_t phase[2] = {0u, 0u};
+  if (my > 0) {
+    unsigned char* b0 = bufp[0];
+    tc_stage<SPLIT>(a, blockIdx.x, b0, b0 + half, b0 + a_bytes, b0 + half + a_bytes);
+    proxy_fence();
+  }
+  __syncthreads();
+  for (int j = 0; j < my; ++j) {
+    const int cb = j & 1;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t base = smem_u32(bufp[cb]);
+      const uint32_t Ah = base, Bh = base + a_bytes, Al = base + half, Bl = base + half + a_bytes;
+#pragma unroll
+      for (int s = 0; s < TC_KT / 16; ++s) {
+        const uint32_t ko = s * 256;
+        umma_bf16(tmem, smem_desc(Ah + ko, 128, 1024), smem_desc(Bh + ko, 128, 1024), idesc, (j > 0 || s > 0));
+        if (SPLIT) {
+          umma_bf16(tmem, smem_desc(Ah + ko, 128, 1024), smem_desc(Bl + ko, 128, 1024), idesc, 1u);
+          umma_bf16(tmem, smem_desc(Al + ko, 128, 1024), smem_desc(Bh + ko, 128, 1024), idesc, 1u);
+        }
+      }
+      umma_commit(&bars[cb]);
+    }
+    if (j + 1 < my) {
+      const int nb = (j + 1) & 1;
+      if (j >= 1) {                       // buffer nb was read by the MMAs of chunk j - 1
+        ok = mbar_wait(&bars[nb], phase[nb]) && ok;
+        phase[nb] ^= 1u;
+      }
+      unsigned char* bn = bufp[nb];
+      tc_stage<SPLIT>(a, blockIdx.x + (int64_t)(j + 1) * gridDim.x, bn, bn + half, bn + a_bytes,
+                      bn + half + a_bytes);
+      proxy_fence();
+    }
+    __syncthreads();
+  }
+  if (my > 0) {                           // the last commit covers every MMA issued before it
+    const int lb = (my - 1) & 1;
+    if (!mbar_wait(&bars[lb], phase[lb])) {
+      ok = false;
+      mbar_wait(&bars[lb], phase[lb]);
+    }
+  }
+  tc_fence_after();
+  // accumulator rows = columns of S (lanes), columns = columns of [A S | B S]
+  const int q = wid & 3, hcol = wid >> 2;
+  const int row = 32 * q + lane;
+  const int m2 = 2 * a.m;
+  float* out = a.partials + (size_t)blockIdx.x * a.m * m2;
+  for (int c0 = hcol * (a.N / 2); c0 < (hcol + 1) * (a.N / 2); c0 += 8) {
+    float v[8];
+    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+    if (row < a.m) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (c0 + i < m2) out[(size_t)row * m2 + c0 + i] = (my > 0) ? v[i] : 0.0f;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+  if (!ok && tid == 0 && a.err) atomicExch(a.err, 4);
+}
+
+// G[0] = S^T A S, G[1] = S^T B S (FP64, [2][m][m]) from the CTAs' FP32 partials.
+__global__ void k_gram_tc_reduce(const float* partials, int nblocks, int m, double* G, const int* status) {
+  if (status && *status != 0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m2 = 2 * m;
+  if (e >= m * m2) return;
+  double s = 0.0;
+  for (int bl = 0; bl < nblocks; ++bl) s += (double)partials[(size_t)bl * m * m2 + e];
+  const int i = e / m2, j = e - i * m2;
+  if (j < m) G[(size_t)i * m + j] = s;
+  else G[(size_t)m * m + (size_t)i * m + (j - m)] = s;
+}
+
+}  // namespace
+
+// Launch the tensor-core Gram: returns BF_EINVAL for shapes it does not cover (k not a
+// multiple of 4, m > 96), so the caller can use the FP32 kernel instead.
+int bf_gram_tc(const float* const* S, const float* const* AS, const float* b, int nblk, int k, int64_t n,
+               bool split, float* partials, int grid, double* G, const int* status, int* err, cudaStream_t s) {
+  const int m = nblk * k;
+  if (k % 4 != 0 || m > 96 || n < 1) return BF_EINVAL;
+  TcArgs a;
+  for (int i = 0; i < 3; ++i) {
+    a.S[i] = i < nblk ? S[i] : nullptr;
+    a.AS[i] = i < nblk ? AS[i] : nullptr;
+  }
+  a.b = b;
+  a.nblk = nblk;
+  a.k = k;
+  a.m = m;
+  a.N = (2 * m + 15) & ~15;
+  a.n = n;
+  a.partials = partials;
+  a.status = status;
+  a.err = err;
+  const size_t half = (size_t)TC_M * TC_KT * 2 + (size_t)a.N * TC_KT * 2;
+  const size_t sm = 2 * (split ? 2 : 1) * half;
+  const int64_t nch = (n + TC_KT - 1) / TC_KT;
+  grid = (int)std::min<int64_t>(grid, nch);
+  static bool init[2] = {false, false};
+  if (!init[split]) {
+    cudaError_t e = split ? cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
+                          : cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return bf_cuda_fail(e, "cudaFuncSetAttribute(k_gram_tc)");
+    init[split] = true;
+  }
+  if (split) BF_LAUNCH((k_gram_tc<true><<<grid, TC_THREADS, sm, s>>>(a)));
+  else BF_LAUNCH((k_gram_tc<false><<<grid, TC_THREADS, sm, s>>>(a)));
+  const int ne = m * 2 * m;
+  BF_LAUNCH((k_gram_tc_reduce<<<(ne + 255) / 256, 256, 0, s>>>(partials, grid, m, G, status)));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+// Test entry point (include/bf_testing.h): the tensor-core Gram of given blocks.
+extern "C" int bf_gram_tc_test(const float* S0, const float* S1, const float* S2, const float* AS0, const float* AS1,
+                               const float* AS2, const float* b, int nblk, int k, int64_t n, int split, double* G,
+                               void* stream) {
+  if (nblk < 1 || nblk > 3 || !S0 || !AS0 || !G) return bf_fail(BF_EINVAL, "bf_gram_tc_test: bad arguments");
+  if (k % 4 != 0 || nblk * k > 96) return bf_fail(BF_EINVAL, "bf_gram_tc_test: need k % 4 == 0 and nblk * k <= 96");
+  const float* S[3] = {S0, S1, S2};
+  const float* AS[3] = {AS0, AS1, AS2};
+  int dev = 0, nsm = 0;
+  BF_CUDA(cudaGetDevice(&dev));
+  BF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int m = nblk * k;
+  float* part = nullptr;
+  int* flag = nullptr;
+  BF_CUDA(cudaMalloc(&part, (size_t)nsm * m * 2 * m * sizeof(float)));
+  BF_CUDA(cudaMalloc(&flag, sizeof(int)));
+  cudaStream_t s = (cudaStream_t)stream;
+  BF_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  int rc = bf_gram_tc(S, AS, b, nblk, k, n, split != 0, part, nsm, G, flag, flag, s);
+  int h = 0;
+  if (rc == BF_OK) {
+    BF_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+  }
+  cudaFree(part);
+  cudaFree(flag);
+  if (rc) return rc;
+  if (h) return bf_fail(BF_ETIMEOUT, "bf_gram_tc_test: a bounded wait gave up");
+  return BF_OK;
+}

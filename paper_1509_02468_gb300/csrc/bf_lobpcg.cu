@@ -22,6 +22,8 @@ int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, 
                  int64_t ldy, double* dots, cudaStream_t s);
 int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
                      int64_t ldz, cudaStream_t s, const int* stop);
+int bf_gram_tc(const float* const* S, const float* const* AS, const float* b, int nblk, int k, int64_t n,
+               bool split, float* partials, int grid, double* G, const int* status, int* err, cudaStream_t s);
 int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
 
@@ -29,7 +31,7 @@ int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k,
 
 namespace {
 
-enum { LOB_RUN = 0, LOB_CONV = 1, LOB_BREAK = 2, LOB_NONFINITE = 3 };
+enum { LOB_RUN = 0, LOB_CONV = 1, LOB_BREAK = 2, LOB_NONFINITE = 3, LOB_TIMEOUT = 4 };
 
 struct LobState {
   double theta[LOB_KMAX];
@@ -707,6 +709,23 @@ static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T
   return BF_OK;
 }
 
+// The Gram products: FP32 kernel, or (FP32 graphs, k % 4 == 0) the tensor-core kernel in
+// BF16 or split-BF16.
+template <typename T>
+static int gram_step(const GramArgs<T>& ga, int gram_mode, int ggrid, double* part, double* G, LobState* st,
+                     cudaStream_t s) {
+  if (sizeof(T) == 4 && gram_mode != BF_GRAM_FP32) {
+    const int rc = bf_gram_tc(reinterpret_cast<const float* const*>(ga.S), reinterpret_cast<const float* const*>(ga.AS),
+                              reinterpret_cast<const float*>(ga.b), ga.nblk, ga.k, ga.n, gram_mode == BF_GRAM_BF16X3,
+                              reinterpret_cast<float*>(part), ggrid, G, &st->status, &st->status, s);
+    if (rc != BF_EINVAL) return rc;
+  }
+  const int rc = run_gram<T>(ga, ggrid, s);
+  if (rc) return rc;
+  run_gram_reduce(part, ggrid, ga.m, G, st, s);
+  return BF_OK;
+}
+
 template <typename T>
 int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
             const bf_lobpcg_opts& o, T* X_out, double* theta_out, double* resid_out, T* y_out,
@@ -774,9 +793,8 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   ga.AS[0] = B.AX[1];
   ga.m = k;
   ga.m4 = (k + 3) & ~3;
-  rc = run_gram<T>(ga, ggrid, s);
+  rc = gram_step<T>(ga, o.gram, ggrid, B.gram_part, B.G, B.st, s);
   if (rc) return rc;
-  run_gram_reduce(B.gram_part, ggrid, k, B.G, B.st, s);
   RRParams ra;
   ra.G = B.G;
   ra.C = B.C;
@@ -825,9 +843,8 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
     ga.AS[1] = B.AW;
     ga.S[2] = B.P[j];
     ga.AS[2] = B.AP[j];
-    rc = run_gram<T>(ga, ggrid, s);
+    rc = gram_step<T>(ga, o.gram, ggrid, B.gram_part, B.G, B.st, s);
     if (rc) return rc;
-    run_gram_reduce(B.gram_part, ggrid, ga.m, B.G, B.st, s);
     ra.m = ga.m;
     ra.m_nop = (nblk == 3) ? 2 * k : 0;
     ra.Cp = B.Cp;
@@ -869,6 +886,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
     info->ref = 0.0;
     if (h.status == LOB_BREAK) return bf_fail(BF_EBREAKDOWN, "lobpcg_filter: dependent trial basis");
     if (h.status == LOB_NONFINITE) return bf_fail(BF_ENONFINITE, "lobpcg_filter: non-finite value");
+    if (h.status == LOB_TIMEOUT) return bf_fail(BF_ETIMEOUT, "lobpcg_filter: a bounded wait of the Gram kernel gave up");
   }
   return BF_OK;
 }
@@ -891,6 +909,8 @@ extern "C" int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, in
   if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4))
     return bf_fail(BF_EINVAL, "lobpcg_filter: BF_PRECOND_NET needs a net and an FP32 graph");
   if (!(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "lobpcg_filter: tol must be >= 0");
+  if (o.gram != BF_GRAM_FP32 && o.gram != BF_GRAM_BF16 && o.gram != BF_GRAM_BF16X3)
+    return bf_fail(BF_EINVAL, "lobpcg_filter: bad gram mode");
   cudaStream_t s = (cudaStream_t)stream;
   if (g->esize == 4)
     return lob_run<float>(g, (const float*)X0, ldx0, k, kmax, o, (float*)X_out, theta_out, resid_out,

@@ -1,0 +1,54 @@
+"""Gram products on the tensor cores (tcgen05, BF16 and split-BF16 operands, FP32
+accumulation) against FP64 products of the same FP32 blocks, with error bounds from the
+operand rounding; and LOBPCG with each Gram precision mode."""
+import numpy as np
+import pytest
+import torch
+
+from tests.gpu_helpers import TOL_RITZ, bf, dev, host, image_case, make_pair
+
+pytestmark = pytest.mark.gpu
+
+
+def blocks(n, k, nblk, seed):
+    rng = np.random.default_rng(seed)
+    S = [rng.standard_normal((n, k)).astype(np.float32) * (1.0 + 9.0 * rng.random(k)).astype(np.float32)
+         for _ in range(nblk)]
+    AS = [rng.standard_normal((n, k)).astype(np.float32) for _ in range(nblk)]
+    b = rng.uniform(1.0, 20.0, n).astype(np.float32)
+    return S, AS, b
+
+
+@pytest.mark.parametrize("n,k,nblk", [(5000, 16, 3), (4097, 8, 2), (300, 32, 3), (64, 4, 1), (131, 12, 3)])
+@pytest.mark.parametrize("split", [False, True])
+def test_tensor_core_gram_within_rounding_bounds(n, k, nblk, split):
+    S, AS, b = blocks(n, k, nblk, seed=n + k)
+    GA, GB = bf().gram_tc([dev(x) for x in S], [dev(x) for x in AS], dev(b), split=split)
+    S64 = np.hstack(S).astype(np.float64)
+    AS64 = np.hstack(AS).astype(np.float64)
+    BS64 = b.astype(np.float64)[:, None] * S64
+    refA, refB = S64.T @ AS64, S64.T @ BS64
+    # per-entry scale: |s_i| . |t_j| (Cauchy-Schwarz bound of the product sums' size)
+    sA = np.linalg.norm(S64, axis=0)[:, None] * np.linalg.norm(AS64, axis=0)[None, :]
+    sB = np.linalg.norm(S64, axis=0)[:, None] * np.linalg.norm(BS64, axis=0)[None, :]
+    # BF16 rounding of both factors: |rel| <= 2^-8 each; split: the dropped lo*lo term and
+    # the rounding of lo give ~2^-16, FP32 accumulation adds up to ~2^-24 sqrt(n) per entry
+    eps = (2.0 ** -16 + 2.0 ** -24 * np.sqrt(n)) if split else 2.0 ** -7
+    assert np.max(np.abs(host(GA) - refA) / sA) <= 4 * eps
+    assert np.max(np.abs(host(GB) - refB) / sB) <= 4 * eps
+
+
+@pytest.mark.parametrize("gram", ["bf16x3", "bf16"])
+def test_lobpcg_with_tensor_core_gram(gram):
+    from paper_1509_02468_gb300 import synth
+    _, noisy = image_case(96, 112, 21)
+    G, O = make_pair(noisy, 3, 2.0, 0.08)
+    X0 = dev(synth.block_start(noisy.ravel(), 16, 21))
+    ref = bf().lobpcg_filter(G, X0, 12)
+    out = bf().lobpcg_filter(G, X0, 12, gram=gram)
+    th_ref, th = host(ref["theta"]), host(out["theta"])
+    err = np.max(np.abs(th - th_ref) / np.maximum(np.abs(th_ref), 1e-3 * np.abs(th_ref).max()))
+    # split-BF16 reproduces the FP32 Gram's run to the FP32 tolerance; plain BF16 converges
+    # to a nearby trajectory (its Gram carries ~4e-3 relative errors)
+    assert err <= (10 * TOL_RITZ if gram == "bf16x3" else 0.2), err
+    assert out["info"].status in ("ran", "converged")
