@@ -128,25 +128,43 @@ __device__ __forceinline__ void put_pair(unsigned char* hi, unsigned char* lo, i
 }
 
 // Stage chunk c (pixels c * TC_KT ...) into the operand tiles: A rows = columns of S,
-// B rows = columns of A S, then of B S.
+// B rows = columns of A S, then of B S.  A thread owns tasks tid, tid + TC_THREADS, ...
+// (a pixel pair and four columns of one block); all its global loads are issued before
+// any conversion so that they are in flight together.
+#define TC_MAXT 6                  // tasks per thread: 2 * (m / 4) * 32 / 256 <= 6 for m <= 96
 template <bool SPLIT>
 __device__ void tc_stage(const TcArgs& a, int64_t c, unsigned char* Ahi, unsigned char* Alo, unsigned char* Bhi,
                          unsigned char* Blo) {
   const int kq = a.k >> 2;
   const int per = a.nblk * (TC_KT / 2) * kq;
   const int64_t p0 = c * TC_KT;
-  for (int t = threadIdx.x; t < 2 * per; t += TC_THREADS) {
+  float4 v0[TC_MAXT], v1[TC_MAXT];
+#pragma unroll
+  for (int u = 0; u < TC_MAXT; ++u) {
+    const int t = threadIdx.x + u * TC_THREADS;
+    v0[u] = v1[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (t < 2 * per) {
+      const bool is_as = t >= per;
+      const int tt = is_as ? t - per : t;
+      const int cq = tt % kq, rest = tt / kq;
+      const int pp = rest % (TC_KT / 2), bk = rest / (TC_KT / 2);
+      const int64_t p = p0 + 2 * pp;
+      const float* src = is_as ? a.AS[bk] : a.S[bk];
+      if (p < a.n) v0[u] = __ldg(reinterpret_cast<const float4*>(src + p * a.k + 4 * cq));
+      if (p + 1 < a.n) v1[u] = __ldg(reinterpret_cast<const float4*>(src + (p + 1) * a.k + 4 * cq));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < TC_MAXT; ++u) {
+    const int t = threadIdx.x + u * TC_THREADS;
+    if (t >= 2 * per) break;
     const bool is_as = t >= per;
     const int tt = is_as ? t - per : t;
     const int cq = tt % kq, rest = tt / kq;
     const int pp = rest % (TC_KT / 2), bk = rest / (TC_KT / 2);
     const int64_t p = p0 + 2 * pp;
-    const float* src = is_as ? a.AS[bk] : a.S[bk];
-    float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), v1 = v0;
-    if (p < a.n) v0 = *reinterpret_cast<const float4*>(src + p * a.k + 4 * cq);
-    if (p + 1 < a.n) v1 = *reinterpret_cast<const float4*>(src + (p + 1) * a.k + 4 * cq);
     const int col = bk * a.k + 4 * cq;
-    const float x0[4] = {v0.x, v0.y, v0.z, v0.w}, x1[4] = {v1.x, v1.y, v1.z, v1.w};
+    const float x0[4] = {v0[u].x, v0[u].y, v0[u].z, v0[u].w}, x1[4] = {v1[u].x, v1[u].y, v1[u].z, v1[u].w};
     if (!is_as) {
       const float b0 = (a.b && p < a.n) ? a.b[p] : 1.0f;
       const float b1 = (a.b && p + 1 < a.n) ? a.b[p + 1] : 1.0f;

@@ -186,6 +186,7 @@ __global__ void k_project(T* V, int k, int64_t n, const LobState* st) {
 // TwoSums, and the block partial hi + lo is written in FP64.
 #define GRAM_T 512
 #define GRAM_PXC 64
+#define GRAM_BUF (GRAM_PXC * 96)  // one buffered chunk: GRAM_PXC pixels x m4 <= 96 columns
 
 template <typename T>
 struct GramArgs {
@@ -225,9 +226,9 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
     ta = row;
     tb = row + t;
   }
-  T* sS = reinterpret_cast<T*>(smem);                 // [GRAM_PXC][m4]
-  T* sA = sS + GRAM_PXC * m4;                         // [GRAM_PXC][m4]
-  T* sb = sA + GRAM_PXC * m4;                         // [GRAM_PXC]
+  T* sS = reinterpret_cast<T*>(smem);                 // [2][GRAM_BUF]: chunk of S, [GRAM_PXC][m4]
+  T* sA = sS + 2 * GRAM_BUF;                          // [2][GRAM_BUF]: chunk of A S
+  T* sb = sA + 2 * GRAM_BUF;                          // [2][GRAM_PXC]
   T cA[16], cB[16], hA[16], lA[16], hB[16], lB[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) cA[e] = cB[e] = hA[e] = lA[e] = hB[e] = lB[e] = T(0);
@@ -235,13 +236,58 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
   const int fold_every = 16;      // FP32 runs of 16 products (64 cost ~5e-7 in Ritz values on small images)
   const int64_t nchunks = (a.n + GRAM_PXC - 1) / GRAM_PXC;
   const bool vec = (k % 4 == 0);
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+  // FP32 blocks with k % 4 == 0: the next chunk is copied into the second shared-memory
+  // buffer by cp.async while the current one is processed (zero-filled past n and m).
+  const bool pipe = vec && sizeof(T) == 4;
+  const int q4 = m4 / 4;
+  auto issue = [&](int64_t ch, int buf) {
     const int64_t i0 = ch * GRAM_PXC;
-    __syncthreads();
-    if (vec) {
-      const int q4 = m4 / 4;
-      for (int q = threadIdx.x; q < GRAM_PXC * q4; q += GRAM_T) {
-        const int p = q / q4, c4 = q - p * q4;
+    T* dS = sS + (size_t)buf * GRAM_BUF;
+    T* dA = sA + (size_t)buf * GRAM_BUF;
+    T* db = sb + (size_t)buf * GRAM_PXC;
+    for (int q = threadIdx.x; q < GRAM_PXC * q4; q += GRAM_T) {
+      const int p = q / q4, c4 = q - p * q4;
+      const int64_t i = i0 + p;
+      const int col = c4 * 4, blk = col / k, c = col - blk * k;
+      const bool ok = i < a.n && col < m;
+      const T* gs = ok ? a.S[blk] + i * k + c : a.S[0];
+      const T* ga = ok ? a.AS[blk] + i * k + c : a.AS[0];
+      const unsigned nb = ok ? 16u : 0u;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dS + p * m4 + col)),
+                   "l"(gs), "r"(nb) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dA + p * m4 + col)),
+                   "l"(ga), "r"(nb) : "memory");
+    }
+    if (threadIdx.x < GRAM_PXC) {
+      const int64_t i = i0 + threadIdx.x;
+      if (a.b) {
+        const bool ok = i < a.n;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(db + threadIdx.x)),
+                     "l"(ok ? a.b + i : a.b), "r"(ok ? 4u : 0u) : "memory");
+      } else {
+        db[threadIdx.x] = (i < a.n) ? T(1) : T(0);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (pipe && blockIdx.x < nchunks) issue(blockIdx.x, 0);
+  int it_local = 0;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it_local) {
+    const int64_t i0 = ch * GRAM_PXC;
+    const int cur = pipe ? (it_local & 1) : 0;
+    __syncthreads();                       // the previous chunk's readers are done
+    if (pipe) {
+      if (ch + gridDim.x < nchunks) {
+        issue(ch + gridDim.x, cur ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      __syncthreads();
+    } else if (vec) {
+      const int q4v = m4 / 4;
+      for (int q = threadIdx.x; q < GRAM_PXC * q4v; q += GRAM_T) {
+        const int p = q / q4v, c4 = q - p * q4v;
         const int64_t i = i0 + p;
         const int col = c4 * 4, blk = col / k, c = col - blk * k;
         Vec<T, 4> vs, va;
@@ -255,6 +301,11 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
         *reinterpret_cast<Vec<T, 4>*>(sS + p * m4 + col) = vs;
         *reinterpret_cast<Vec<T, 4>*>(sA + p * m4 + col) = va;
       }
+      for (int p = threadIdx.x; p < GRAM_PXC; p += GRAM_T) {
+        const int64_t i = i0 + p;
+        sb[p] = (i < a.n) ? (a.b ? a.b[i] : T(1)) : T(0);
+      }
+      __syncthreads();
     } else {
       for (int q = threadIdx.x; q < GRAM_PXC * m4; q += GRAM_T) {
         const int p = q / m4, col = q - p * m4;
@@ -268,18 +319,21 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
         sS[q] = vs;
         sA[q] = va;
       }
+      for (int p = threadIdx.x; p < GRAM_PXC; p += GRAM_T) {
+        const int64_t i = i0 + p;
+        sb[p] = (i < a.n) ? (a.b ? a.b[i] : T(1)) : T(0);
+      }
+      __syncthreads();
     }
-    for (int p = threadIdx.x; p < GRAM_PXC; p += GRAM_T) {
-      const int64_t i = i0 + p;
-      sb[p] = (i < a.n) ? (a.b ? a.b[i] : T(1)) : T(0);
-    }
-    __syncthreads();
+    const T* cS = sS + (size_t)cur * GRAM_BUF;
+    const T* cA_ = sA + (size_t)cur * GRAM_BUF;
+    const T* cb = sb + (size_t)cur * GRAM_PXC;
     if (act) {
       for (int p = grp; p < GRAM_PXC; p += ng) {
-        const Vec<T, 4> xa = *reinterpret_cast<const Vec<T, 4>*>(sS + p * m4 + ta * 4);
-        const Vec<T, 4> xb = *reinterpret_cast<const Vec<T, 4>*>(sS + p * m4 + tb * 4);
-        const Vec<T, 4> yb = *reinterpret_cast<const Vec<T, 4>*>(sA + p * m4 + tb * 4);
-        const T bp = sb[p];
+        const Vec<T, 4> xa = *reinterpret_cast<const Vec<T, 4>*>(cS + p * m4 + ta * 4);
+        const Vec<T, 4> xb = *reinterpret_cast<const Vec<T, 4>*>(cS + p * m4 + tb * 4);
+        const Vec<T, 4> yb = *reinterpret_cast<const Vec<T, 4>*>(cA_ + p * m4 + tb * 4);
+        const T bp = cb[p];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const T bx = bp * xa.v[i];
@@ -643,7 +697,7 @@ static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
   const int nt = ta_n * (ta_n + 1) / 2;
   if (nt > GRAM_T) return bf_fail(BF_EINVAL, "lobpcg_filter: block too wide");
   const int ng = GRAM_T / nt;
-  size_t sm = (size_t)(2 * GRAM_PXC * ga.m4 + GRAM_PXC) * sizeof(T);
+  size_t sm = (size_t)(4 * GRAM_BUF + 2 * GRAM_PXC) * sizeof(T);
   sm = std::max(sm, (size_t)(ng / 2 + 1) * nt * 64 * sizeof(T));
   static bool init = false;
   if (!init) {
