@@ -516,19 +516,16 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
 }
 
 // ------------------------------------------------------------------ residual
-// R = AX - b X theta, W = t R (t = 1/d or 1), per-column sums of R^2, (b X)^2 and b W
-// (thread t of a block owns column t % k of pixel lane t / k).  The last block writes the
-// relative residual norms and the constraint coefficients e^T B W / e^T B e, counts the
-// step and applies the tolerance test.
+// R = AX - b X theta, W = t R (t = 1/d or 1), per-column block sums of R^2, (b X)^2 and
+// b W (thread t of a block owns column t % k of pixel lane t / k); k_resid_cols and
+// k_resid_tail turn them into the residual norms.
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T* __restrict__ AX,
-                                               int k, int64_t n, const T* b, const T* tinv,
-                                               T* Wn, int constrain, double* partials,
-                                               LobState* st) {
+                                               int k, int64_t n, const T* __restrict__ b,
+                                               const T* __restrict__ tinv, T* __restrict__ Wn,
+                                               double* __restrict__ partials, const LobState* st) {
   if (st->status != LOB_RUN) return;
   __shared__ double sums[3 * LOB_KMAX];
-  __shared__ double outs[3 * LOB_KMAX];
-  __shared__ int last;
   for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) sums[q] = 0.0;
   __syncthreads();
   const int lanes = blockDim.x / k;
@@ -536,6 +533,7 @@ __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T*
   T r2 = T(0), bx2 = T(0), bw = T(0);
   if (pl < lanes) {
     const T th = (T)st->theta[c];
+#pragma unroll 4
     for (int64_t i = (int64_t)blockIdx.x * lanes + pl; i < n; i += (int64_t)gridDim.x * lanes) {
       const T bi = b ? b[i] : T(1);
       const T ti = tinv ? tinv[i] : T(1);
@@ -567,24 +565,48 @@ __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T*
     atomicAdd(&sums[k + c], (double)bx2);
     atomicAdd(&sums[2 * k + c], (double)bw);
   }
-  if (grid_colsum_last(sums, 3 * k, partials, &st->counter, outs, &last)) {
-    if (threadIdx.x < k) {
-      const int q = threadIdx.x;
-      st->resid[q] = sqrt(outs[q]) / sqrt(outs[k + q]);
-      st->cw[q] = constrain ? outs[2 * k + q] / st->ebe : 0.0;
+  // block partials only, summed by the next kernels (a kernel boundary instead of a fence,
+  // an arrival counter and a last block, which cost more than the pass itself)
+  __syncthreads();
+  for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) partials[(size_t)blockIdx.x * 3 * k + q] = sums[q];
+}
+
+// Column sums of k_resid's block partials: block j sums value j over all blocks (each
+// thread a strided share, then a fixed-order block reduction) into cols[j].
+__global__ void __launch_bounds__(256) k_resid_cols(const double* __restrict__ partials, int nb, int nv,
+                                                    double* __restrict__ cols, const LobState* st) {
+  if (st->status != LOB_RUN) return;
+  __shared__ double red[256 / 32];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) acc += partials[(size_t)b * nv + j];
+  double v[1] = {acc}, tot[1];
+  block_sum<1, double>(v, red, tot);
+  if (threadIdx.x == 0) cols[j] = tot[0];
+}
+
+// The relative residual norms, the constraint coefficients e^T B W / e^T B e, the step
+// count and the tolerance test from the column sums of R^2, (b X)^2 and b W.
+__global__ void k_resid_tail(const double* __restrict__ cols, int k, int constrain, LobState* st) {
+  if (st->status != LOB_RUN) return;
+  const int t = threadIdx.x;
+  double r = 0.0;
+  if (t < k) {
+    r = sqrt(cols[t]) / sqrt(cols[k + t]);
+    st->resid[t] = r;
+    st->cw[t] = constrain ? cols[2 * k + t] / st->ebe : 0.0;
+  }
+  __syncwarp();
+  if (t == 0) {
+    st->iter += 1;
+    double mx = 0.0;
+    bool fin = true;
+    for (int q = 0; q < k; ++q) {
+      mx = fmax(mx, st->resid[q]);
+      fin = fin && isfinite(st->resid[q]);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      st->iter += 1;
-      double mx = 0.0;
-      bool fin = true;
-      for (int q = 0; q < k; ++q) {
-        mx = fmax(mx, st->resid[q]);
-        fin = fin && isfinite(st->resid[q]);
-      }
-      if (!fin) st->status = LOB_NONFINITE;
-      else if (st->tol > 0.0 && mx <= st->tol) st->status = LOB_CONV;
-    }
+    if (!fin) st->status = LOB_NONFINITE;
+    else if (st->tol > 0.0 && mx <= st->tol) st->status = LOB_CONV;
   }
 }
 
@@ -752,8 +774,11 @@ static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T
                      cudaStream_t s, const bf_net* net = nullptr) {
   int rc = apply_T<T>(g, BF_OP_L, X, k, k, AX, k, s);
   if (rc) return rc;
-  BF_LAUNCH(k_resid<T><<<rgrid, 256, 0, s>>>(X, AX, k, g->n, bdiag, net ? nullptr : tinv, Wn, constrain,
-                                             part, st));
+  const int resgrid = 4 * rgrid;                // many blocks: enough loads in flight
+  BF_LAUNCH(k_resid<T><<<resgrid, 256, 0, s>>>(X, AX, k, g->n, bdiag, net ? nullptr : tinv, Wn, part, st));
+  double* cols = part + (size_t)resgrid * 3 * k;
+  BF_LAUNCH(k_resid_cols<<<3 * k, 256, 0, s>>>(part, resgrid, 3 * k, cols, st));
+  BF_LAUNCH(k_resid_tail<<<1, 32, 0, s>>>(cols, k, constrain, st));
   BF_CUDA(cudaGetLastError());
   if (net) {
     if ((rc = net_T(net, g, Wn, k, s, &st->status))) return rc;
@@ -797,7 +822,8 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   const size_t cb = (((size_t)m3 * k * sizeof(double)) + 255) & ~(size_t)255;
   const size_t pb = (((size_t)std::max(ugrid, rgrid) * (3 * LOB_KMAX + 2) * sizeof(double)) + 255) & ~(size_t)255;
   const size_t yb = 256 * sizeof(double) * 2;
-  const size_t total = 11 * blk + gpb + gb + 2 * cb + pb + yb + 1024;
+  const size_t rrb = (sizeof(RRScratch) + 255) & ~(size_t)255;
+  const size_t total = 11 * blk + gpb + gb + 2 * cb + pb + yb + rrb + 1024;
   int rc = bf_ws_reserve(gm, BF_WS_LOB, total);
   if (rc) return rc;
   char* w = (char*)gm->ws[BF_WS_LOB];
@@ -816,6 +842,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   B.Cp = (double*)w; w += cb;
   B.part = (double*)w; w += pb;
   B.ysums = (double*)w; w += yb;
+  RRScratch* rr_scr = (RRScratch*)w; w += rrb;
   B.st = (LobState*)w; w += 1024;
 
   const T* bdiag = (o.pencil == BF_PENCIL_D) ? (const T*)g->d : nullptr;
@@ -860,6 +887,7 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   ra.m = k;
   ra.m_nop = 0;
   ra.theta_hist = o.theta_hist;
+  ra.scr = rr_scr;
   rc = bf_rr_launch(ra, s);
   if (rc) return rc;
   UpdArgs<T> ua;

@@ -10,8 +10,9 @@
 //      trial basis: retry on the leading m_nop block, i.e. without P, else breakdown);
 //   2. standard form M = Y R^-T (FP64, lower triangle);
 //   3. FP32 eigenpairs (lambda_i, v_i) of float(M): Householder reduction to tridiagonal
-//      form, every eigenvalue by multisection on Sturm counts, inverse iteration for every
-//      eigenvector, modified Gram-Schmidt inside clusters, back-transformation;
+//      form, then one warp per eigenpair (a kernel of its own, so the eigenpairs run on
+//      many SMs): its eigenvalue by multisection on Sturm counts, its eigenvector by
+//      inverse iteration and back-transformation; modified Gram-Schmidt inside clusters;
 //   4. X = the k eigenvectors of the smallest lambda, Y = M X in FP64, Rayleigh quotients
 //      theta_j and the FP64 residual r_j = y_j - theta_j x_j;
 //   5. first-order correction x_j += sum_i v_i (v_i^T r_j) / (theta_j - lambda_i) over the
@@ -29,9 +30,7 @@
 #include "bf_rr.cuh"
 
 #define RR_T 512
-#define RR_LD 97            // padded leading dimension of the m x m work matrices
 #define RR_KLD 33           // padded leading dimension of the m x k work matrices
-#define RR_LDF 97           // leading dimension of the FP32 m x m Jacobi matrices
 #define DEP_TOL 1e-10
 
 namespace {
@@ -189,7 +188,9 @@ __device__ void mul_mx(const double* MA, const double* X, double* Y, int m, cons
   }
 }
 
-__global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
+// Part 1 (one CTA): scaling, Cholesky with the forward solve, standard form, FP32
+// tridiagonal reduction; hands M, R, T and the reflectors to the next kernels.
+__global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
   if (*a.status != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
   double* MA = reinterpret_cast<double*>(smem);           // [96][RR_LD]: A, Y, M (lower) + R^T (upper)
@@ -411,36 +412,157 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   __syncthreads();
   for (int i = tid; i < m; i += RR_T) e2f[i] = ee32[i] * ee32[i];
   __syncthreads();
-  const float tn = fmaxf(fabsf(shlo), fabsf(shhi));
-  // 4b. every eigenvalue of T by multisection on Sturm counts (32 points per warp and round)
-  for (int j = wid; j < m; j += RR_NW) {
-    float lo = shlo, hi = shhi;
-    lo -= 1e-6f * fabsf(lo) + 1e-30f;
-    hi += 1e-6f * fabsf(hi) + 1e-30f;
-    const float stop = 4.0f * 6e-8f * tn + 1e-30f;
-    for (int round = 0; round < 10 && hi - lo > stop; ++round) {
-      const float w = (hi - lo) * (1.0f / 33.0f);
-      const float x = lo + w * (float)(lane + 1);
-      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f(dd32, e2f, m, x) > j);
-      const int first = above ? __ffs(above) - 1 : 32;   // first point with more than j below
-      const float nlo = (first == 0) ? lo : lo + w * (float)first;
-      const float nhi = (first == 32) ? hi : lo + w * (float)(first + 1);
-      lo = nlo;
-      hi = nhi;
+  (void)R32; (void)CC; (void)Wk; (void)D32;
+  RRScratch* S = a.scr;
+  for (int r = wid; r < m; r += RR_NW)
+    for (int c = lane; c < m; c += 32) {
+      S->MA[r * RR_LD + c] = MA[r * RR_LD + c];
+      S->J[r * RR_LDF + c] = J[r * RR_LDF + c];
     }
-    if (lane == 0) lam[j] = 0.5f * (lo + hi);
+  for (int i = tid; i < m; i += RR_T) {
+    S->sc[i] = sc[i];
+    S->rdg[i] = rdg[i];
+    S->dd[i] = dd32[i];
+    S->ee[i] = ee32[i];
+    S->e2[i] = e2f[i];
+    S->bet[i] = bet32[i];
   }
-  __syncthreads();
-  // 4c. an eigenvector of T per eigenvalue by three steps of inverse iteration (start
-  //     vectors differ per index, so a cluster's vectors span the cluster's subspace)
-  const float clus = 1e-3f * tn;                    // eigenvalues closer than this: a cluster
-  if (tid < m) {
+  if (tid == 0) {
+    S->lo = shlo;
+    S->hi = shhi;
+    S->tn = fmaxf(fabsf(shlo), fabsf(shhi));
+    S->m = m;
+    S->dropped = dropped;
+  }
+}
+
+// Part 2 (one warp per eigenpair j of T): the j-th eigenvalue by multisection on Sturm
+// counts (32 points per round), its eigenvector by three steps of inverse iteration, then
+// the back-transformation by the reflectors; writes column j of V.
+__global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
+  if (*a.status != 0) return;
+  RRScratch* S = a.scr;
+  const int m = S->m, j = blockIdx.x, lane = threadIdx.x;
+  if (j >= m) return;
+  __shared__ float dd[RR_MMAX], ee[RR_MMAX], e2[RR_MMAX], v[RR_MMAX];
+  for (int i = lane; i < m; i += 32) {
+    dd[i] = S->dd[i];
+    ee[i] = S->ee[i];
+    e2[i] = S->e2[i];
+  }
+  __syncwarp();
+  const float tn = S->tn;
+  float lo = S->lo, hi = S->hi;
+  lo -= 1e-6f * fabsf(lo) + 1e-30f;
+  hi += 1e-6f * fabsf(hi) + 1e-30f;
+  const float stop = 4.0f * 6e-8f * tn + 1e-30f;
+  for (int round = 0; round < 10 && hi - lo > stop; ++round) {
+    const float w = (hi - lo) * (1.0f / 33.0f);
+    const float x = lo + w * (float)(lane + 1);
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f(dd, e2, m, x) > j);
+    const int first = above ? __ffs(above) - 1 : 32;     // first point with more than j below
+    const float nlo = (first == 0) ? lo : lo + w * (float)first;
+    const float nhi = (first == 32) ? hi : lo + w * (float)(first + 1);
+    lo = nlo;
+    hi = nhi;
+  }
+  const float lamj = 0.5f * (lo + hi);
+  if (lane == 0) {
+    S->lam[j] = lamj;
+    // start vectors differ per index, so a cluster's vectors span the cluster's subspace
     float b[RR_MMAX];
-    for (int i = 0; i < m; ++i) b[i] = 1.0f + 0.25f * (float)(((i + 1) * (tid + 3) * 7919) % 97) / 97.0f;
-    tri_inverse_iteration(dd32, ee32, m, lam[tid], 4.0f * 6e-8f * tn + 1e-30f, 3, b);
-    for (int i = 0; i < m; ++i) V[i * RR_LDF + tid] = b[i];
+    for (int i = 0; i < m; ++i) b[i] = 1.0f + 0.25f * (float)(((i + 1) * (j + 3) * 7919) % 97) / 97.0f;
+    tri_inverse_iteration(dd, ee, m, lamj, 4.0f * 6e-8f * tn + 1e-30f, 3, b);
+    for (int i = 0; i < m; ++i) v[i] = b[i];
+  }
+  __syncwarp();
+  for (int jj = m - 3; jj >= 0; --jj) {
+    const float beta = S->bet[jj];
+    if (beta == 0.0f) continue;
+    const int n1 = m - jj - 1;
+    const float* col = S->J + (jj + 1) * RR_LDF + jj;
+    float sum = 0.0f;
+    for (int r = lane; r < n1; r += 32) sum = fmaf(col[r * RR_LDF], v[jj + 1 + r], sum);
+    sum = beta * warp_sum(sum);
+    for (int r = lane; r < n1; r += 32) v[jj + 1 + r] = fmaf(-col[r * RR_LDF], sum, v[jj + 1 + r]);
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) S->V[i * RR_LDF + j] = v[i];
+}
+
+// Part 3 (one CTA): Gram-Schmidt inside clusters (on the back-transformed vectors, which
+// is the same as before it: the transformation is orthogonal), the FP64 correction, the
+// k x k Rayleigh-Ritz and the coefficients C (and Cp).
+__global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
+  if (*a.status != 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* MA = reinterpret_cast<double*>(smem);           // [96][RR_LD]: A, Y, M (lower) + R^T (upper)
+  double* RB = MA + RR_MMAX * RR_LD;                      // [96][RR_LD]: B, R (lower); then FP32 J, V
+  double* XD = RB + RR_MMAX * RR_LD;                      // [96][RR_KLD]: X, X'
+  double* YD = XD + RR_MMAX * RR_KLD;                     // [96][RR_KLD]: M X, M X', Z, C
+  double* sc = YD + RR_MMAX * RR_KLD;                     // [96] unit-diagonal scaling
+  double* rdg = sc + RR_MMAX;                             // [96] 1 / diag(R)
+  double* fv = rdg + RR_MMAX;                             // [96] multipliers of one step
+  double* th = fv + RR_MMAX;                              // [32] Rayleigh quotients
+  double* csd = th + RR_KMAX;                             // [16] k x k rotations
+  double* snd = csd + RR_KMAX / 2;                        // [16]
+  float* lam = reinterpret_cast<float*>(snd + RR_KMAX / 2);  // [96] FP32 eigenvalues of M
+  float* dd32 = lam + RR_MMAX;                            // [96] tridiagonal: diagonal
+  float* ee32 = dd32 + RR_MMAX;                           // [96] off-diagonal
+  float* e2f = ee32 + RR_MMAX;                            // [96] squared off-diagonal
+  float* bet32 = e2f + RR_MMAX;                           // [96] reflector scalars
+  float* pv32 = bet32 + RR_MMAX;                          // [96] work vector
+  int* sel = reinterpret_cast<int*>(pv32 + RR_MMAX);      // [32]
+  int* perm = sel + RR_KMAX;                              // [32]
+  int* rk = perm + RR_KMAX;                               // [96] rank of each FP32 eigenvalue
+  int* pp = rk + RR_MMAX;                                 // [48] pairs of one Jacobi step
+  int* qq = pp + RR_MMAX / 2;                             // [48]
+  // lower triangle of order 96 in row-major order: entry (r, l), l <= r, packed r << 8 | l;
+  // every smaller triangle is a prefix of it
+  unsigned short* tri = reinterpret_cast<unsigned short*>(qq + RR_MMAX / 2);  // [4656]
+  // FP32 views of the RB region once R has been moved out of it (J, V: 37,248 B each):
+  // J holds float(M), then T and the reflectors; V the eigenvectors of M
+  float* J = reinterpret_cast<float*>(RB);                // [96][RR_LDF]
+  float* V = J + RR_MMAX * RR_LDF;                        // [96][RR_LDF]
+  // after the FP32 sweeps: J's region holds R32 and CC, V's region the k x k work
+  float* R32 = J;                                         // [96][RR_KLD] FP32 residual
+  float* CC = J + RR_MMAX * RR_KLD;                       // [96][RR_KLD] correction coefficients
+  double* H = reinterpret_cast<double*>(V);               // [32][RR_KLD]
+  double* Vk = H + RR_KMAX * RR_KLD;                      // [32][RR_KLD]
+  double* Wk = Vk + RR_KMAX * RR_KLD;                     // [32][RR_KLD]
+  // k x k work of step 8 in the J region (R32 and CC are dead by then)
+  double* D64 = reinterpret_cast<double*>(J);             // [32][RR_KLD]
+  double* K64 = D64 + RR_KMAX * RR_KLD;                   // [32][RR_KLD]
+  float* E32 = reinterpret_cast<float*>(K64 + RR_KMAX * RR_KLD);  // [32][RR_KLD]
+  float* D32 = E32 + RR_KMAX * RR_KLD;                    // [32][RR_KLD]
+  __shared__ int fail, dropped;
+  __shared__ float lmax, shK, shlo, shhi;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int k = a.k;
+  const Tiling tk(k, lane);
+  int m = a.m;
+  if (tid == 0) dropped = 0;
+  for (int r = wid; r < a.m; r += RR_NW)
+    for (int l = lane; l <= r; l += 32) tri[r * (r + 1) / 2 + l] = (unsigned short)((r << 8) | l);
+
+  {
+    const RRScratch* S = a.scr;
+    m = S->m;
+    if (tid == 0) dropped = S->dropped;
+    for (int r = wid; r < m; r += RR_NW)
+      for (int c = lane; c < m; c += 32) {
+        MA[r * RR_LD + c] = S->MA[r * RR_LD + c];
+        V[r * RR_LDF + c] = S->V[r * RR_LDF + c];
+      }
+    for (int i = tid; i < m; i += RR_T) {
+      sc[i] = S->sc[i];
+      rdg[i] = S->rdg[i];
+      lam[i] = S->lam[i];
+    }
   }
   __syncthreads();
+  const float clus = 1e-3f * a.scr->tn;             // eigenvalues closer than this: a cluster
   // 4d. orthonormalise within clusters (modified Gram-Schmidt), normalise the rest
   for (int j = wid; j < m; j += RR_NW) {
     if (j > 0 && lam[j] - lam[j - 1] < clus) continue;   // not the first of its cluster
@@ -463,21 +585,7 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     }
   }
   __syncthreads();
-  // 4e. back-transformation by the reflectors, last to first, one warp per vector
-  for (int i = wid; i < m; i += RR_NW) {
-    for (int j = m - 3; j >= 0; --j) {
-      const float beta = bet32[j];
-      if (beta == 0.0f) continue;
-      const int n1 = m - j - 1;
-      const float* col = J + (j + 1) * RR_LDF + j;
-      float s = 0.0f;
-      for (int r = lane; r < n1; r += 32) s = fmaf(col[r * RR_LDF], V[(j + 1 + r) * RR_LDF + i], s);
-      s = beta * warp_sum(s);
-      for (int r = lane; r < n1; r += 32)
-        V[(j + 1 + r) * RR_LDF + i] = fmaf(-col[r * RR_LDF], s, V[(j + 1 + r) * RR_LDF + i]);
-      __syncwarp();
-    }
-  }
+  __syncthreads();
 
   // ------------------------------------------ 5. the k smallest FP32 eigenpairs
   // (multisection returns the eigenvalues in ascending order)
@@ -785,11 +893,15 @@ size_t rr_smem_bytes() {
 int bf_rr_launch(const RRParams& a, cudaStream_t s) {
   static bool init = false;
   const size_t sm = rr_smem_bytes();
+  if (!a.scr) return bf_fail(BF_EINVAL, "Rayleigh-Ritz: no scratch area");
   if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_rr_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return bf_cuda_fail(e, "cudaFuncSetAttribute(k_rr)");
     init = true;
   }
+  BF_LAUNCH(k_rr_reduce<<<1, RR_T, sm, s>>>(a));
+  BF_LAUNCH(k_rr_vectors<<<a.m, 32, 0, s>>>(a));
   BF_LAUNCH(k_rr<<<1, RR_T, sm, s>>>(a));
   BF_CUDA(cudaGetLastError());
   return BF_OK;
@@ -811,5 +923,12 @@ extern "C" int bf_rayleigh_ritz(const double* G, int m, int k, int m_nop, double
   a.theta_hist = nullptr;
   a.status = flags;
   a.restarts = flags + 1;
+  // one scratch area per process and device for this test entry (kept until exit)
+  static RRScratch* scr[64] = {nullptr};
+  int dev = 0;
+  BF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return bf_fail(BF_EINVAL, "bf_rayleigh_ritz: device index");
+  if (!scr[dev]) BF_CUDA(cudaMalloc(&scr[dev], sizeof(RRScratch)));
+  a.scr = scr[dev];
   return bf_rr_launch(a, (cudaStream_t)stream);
 }
