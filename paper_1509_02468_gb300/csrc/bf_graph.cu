@@ -396,6 +396,180 @@ __global__ void __launch_bounds__(BF_THREADS, 2) k_apply_rb(const Geom<float> g,
   }
 }
 
+// Persistent, double-buffered form of k_apply_rb for the L operator with weights on the
+// fly (unscaled operand): one CTA per SM walks tiles of 32 x th pixels; while it computes
+// one tile the halo of its next tile is copied by cp.async (X in 16-byte pieces, zero
+// outside the image; the guide in 4-byte pieces, +inf outside the image so that the range
+// term gives a zero weight there and no mask is needed).  At K = 16 one thread carries all
+// 16 columns of its 4-pixel strip (each weight computed once, 256 threads, ~200 registers);
+// the other widths split the columns into groups of 8 (512 threads, <= 128 registers), as
+// two halo buffers of a 16-column-per-thread tile would not fit in shared memory at K = 32.
+template <int K>
+struct PipeTile {
+  static constexpr int threads = (K == 16) ? 256 : 512;
+  static constexpr int cs = (K == 16) ? 16 : ((K < RB_CS) ? K : RB_CS);
+  static constexpr int ng = K / cs;
+  static constexpr int strips = threads / (32 * ng);
+  static constexpr int tw = 32, th = RB_P * strips;
+  static constexpr int hw = tw + 6, hh = th + 6, hp = hw * hh;
+  static constexpr int nc4 = K / 4;
+  // column-group stride in float4 units, = 2 (mod 8) so the four groups of one pixel fall
+  // in different bank quads when the halo is written
+  static constexpr int cst = hp + ((10 - hp % 8) % 8);
+  static constexpr size_t xbytes = (size_t)cst * nc4 * 16;
+  static constexpr size_t stage = xbytes + (((size_t)hp * 4 + 15) / 16) * 16;
+  static constexpr size_t smem = 2 * stage;
+};
+
+// 2^a by the SFU's approximate exponential, subnormal results flushed to zero (weights
+// below 2^-126 contribute nothing at FP32 precision); +inf / -inf arguments give +inf / 0.
+__device__ __forceinline__ float rb_exp_ftz(float gi, float gj, float a_r, float ls) {
+  const float dl = gi - gj;
+  const float a = fmaf(-dl * a_r, dl, ls);
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
+template <int K>
+__device__ __forceinline__ void pipe_stage(const Geom<float>& g, const ApplyArgs<float>& a, int bx, int by,
+                                           unsigned char* buf) {
+  typedef PipeTile<K> TT;
+  constexpr int NC4 = TT::nc4;
+  const unsigned sx = (unsigned)__cvta_generic_to_shared(buf);
+  const unsigned sg = sx + (unsigned)TT::xbytes;
+  for (int idx = threadIdx.x; idx < TT::hp * NC4; idx += TT::threads) {
+    const int hp = idx / NC4, c = idx - hp * NC4;
+    const int hy = hp / TT::hw, hx = hp - hy * TT::hw;
+    const int gy = by - 3 + hy, gx = bx - 3 + hx;
+    const bool in = (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny);
+    const float* src = in ? a.X + ((int64_t)gy * g.nx + gx) * a.ldx + c * 4 : a.X;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sx + (unsigned)(c * TT::cst + hp) * 16u),
+                 "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
+  }
+  float* sgp = reinterpret_cast<float*>(buf + TT::xbytes);
+  for (int hp = threadIdx.x; hp < TT::hp; hp += TT::threads) {
+    const int hy = hp / TT::hw, hx = hp - hy * TT::hw;
+    const int gy = by - 3 + hy, gx = bx - 3 + hx;
+    if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sg + (unsigned)hp * 4u),
+                   "l"(a.guide + (int64_t)gy * g.nx + gx)
+                   : "memory");
+    } else {
+      sgp[hp] = __int_as_float(0x7f800000);
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(PipeTile<K>::threads, 1) k_apply_pipe(const Geom<float> g, const ApplyArgs<float> a) {
+  typedef PipeTile<K> TT;
+  constexpr int CS = TT::cs, NG = TT::ng, CS4 = CS / 4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ntx = (g.nx + TT::tw - 1) / TT::tw;
+  const int ntiles = ntx * ((g.ny + TT::th - 1) / TT::th);
+  const int lx = threadIdx.x & 31;
+  const int rest = threadIdx.x >> 5;
+  const int grp = rest % NG, strip = rest / NG;
+  const int row0 = strip * RB_P;
+  int t = blockIdx.x;
+  if (t < ntiles) pipe_stage<K>(g, a, (t % ntx) * TT::tw, (t / ntx) * TT::th, smem);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int b = 0; t < ntiles; t += gridDim.x, b ^= 1) {
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) pipe_stage<K>(g, a, (tn % ntx) * TT::tw, (tn / ntx) * TT::th, smem + (b ^ 1) * TT::stage);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();
+    const float4* sx = reinterpret_cast<const float4*>(smem + b * TT::stage);
+    const float* sg = reinterpret_cast<const float*>(smem + b * TT::stage + TT::xbytes);
+    const int bx = (t % ntx) * TT::tw, by = (t / ntx) * TT::th;
+    const int x = bx + lx;
+    float gi[RB_P];
+    unsigned long long acc2[RB_P][CS / 2], xi2[RB_P][CS / 2];
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+      const int hp = (row0 + p + 3) * TT::hw + lx + 3;
+#pragma unroll
+      for (int c4 = 0; c4 < CS4; ++c4) {
+        const float4 v = sx[(grp * CS4 + c4) * TT::cst + hp];
+        xi2[p][2 * c4] = f2_pack(v.x, v.y);
+        xi2[p][2 * c4 + 1] = f2_pack(v.z, v.w);
+      }
+      gi[p] = sg[hp];
+#pragma unroll
+      for (int c = 0; c < CS / 2; ++c) acc2[p][c] = f2_pack(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int r = 0; r < RB_P + 6; ++r) {
+#pragma unroll
+      for (int dx = -3; dx <= 3; ++dx) {
+        const int hp = (row0 + r) * TT::hw + lx + 3 + dx;
+        unsigned long long xj2[CS / 2];
+#pragma unroll
+        for (int c4 = 0; c4 < CS4; ++c4) {
+          const float4 v = sx[(grp * CS4 + c4) * TT::cst + hp];
+          xj2[2 * c4] = f2_pack(v.x, v.y);
+          xj2[2 * c4 + 1] = f2_pack(v.z, v.w);
+        }
+        const float gj = sg[hp];
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+          const int dy = r - 3 - p;
+          if (dy < -3 || dy > 3 || (dy == 0 && dx == 0)) continue;
+          const float w = rb_exp_ftz(gi[p], gj, g.a_r, g.ls[(dy + 3) * 7 + (dx + 3)]);
+          const unsigned long long w2 = f2_pack(w, w);
+#pragma unroll
+          for (int c = 0; c < CS / 2; ++c) acc2[p][c] = f2_diff_fma(w2, xi2[p][c], xj2[c], acc2[p][c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+      const int y = by + row0 + p;
+      if (x >= g.nx || y >= g.ny) continue;
+      float* yp = a.Y + ((int64_t)y * g.nx + x) * a.ldy + grp * CS;
+#pragma unroll
+      for (int c4 = 0; c4 < CS4; ++c4) {
+        float4 o;
+        f2_unpack(acc2[p][2 * c4], o.x, o.y);
+        f2_unpack(acc2[p][2 * c4 + 1], o.z, o.w);
+        *reinterpret_cast<float4*>(yp + 4 * c4) = o;
+      }
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+static int num_sms() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
+  }
+  return nsm;
+}
+
+template <int K>
+static int launch_apply_pipe(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  typedef PipeTile<K> TT;
+  static_assert(TT::smem <= 227 * 1024, "pipelined apply tile does not fit in shared memory");
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(k_apply_pipe<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::smem);
+  });
+  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply_pipe)");
+  const int64_t ntiles = ((g->nx + TT::tw - 1) / TT::tw) * (int64_t)((g->ny + TT::th - 1) / TT::th);
+  const int grid = (int)std::min<int64_t>(ntiles, num_sms());
+  BF_LAUNCH(k_apply_pipe<K><<<grid, TT::threads, TT::smem, s>>>(g->gf, a));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
 template <int K, bool STORED>
 static int launch_apply_rb(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
   typedef RBTile<K> TT;
@@ -415,6 +589,9 @@ static int launch_apply_rb(const bf_graph* g, const ApplyArgs<float>& a, cudaStr
 
 template <int K>
 static int launch_apply_rb_w(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  if (g->p.weight_mode == BF_W_ONTHEFLY && a.op == BF_OP_L && !a.scale && g->gf.a_r > 0.0f &&
+      ((uintptr_t)a.X & 15) == 0 && ((uintptr_t)a.Y & 15) == 0 && a.ldx % 4 == 0 && a.ldy % 4 == 0)
+    return launch_apply_pipe<K>(g, a, s);
   if (g->p.weight_mode == BF_W_ONTHEFLY) return launch_apply_rb<K, false>(g, a, s);
   return launch_apply_rb<K, true>(g, a, s);
 }

@@ -170,3 +170,53 @@ def test_full_size_image_apply_sampled():
                     w = np.exp(-(dx * dx + dy * dy) / 8.0) * np.exp(-(gg[y, x] - gg[yy, xx]) ** 2 / (2 * 0.08 ** 2))
                     acc += w * (X[i].astype(np.float64) - X[yy * 512 + xx].astype(np.float64))
         assert rel_l2(Y[i], acc) < 1e-5
+
+
+def _l_rows_from_definition(g, X, rows, radius, sigma_s, sigma_r):
+    """(L X)[i] for the sampled pixels i: Eq. 2 weights over the square window, difference
+    form sum_j w_ij (x_i - x_j), FP64."""
+    ny, nx = g.shape
+    gg = g.astype(np.float64)
+    out = np.zeros((len(rows), X.shape[1]))
+    for r, i in enumerate(rows):
+        y, x = divmod(int(i), nx)
+        for dy in range(-radius, radius + 1):
+            for dx in range(-radius, radius + 1):
+                yy, xx = y + dy, x + dx
+                if (dy or dx) and 0 <= yy < ny and 0 <= xx < nx:
+                    w = np.exp(-(dx * dx + dy * dy) / (2 * sigma_s ** 2)) * \
+                        np.exp(-(gg[y, x] - gg[yy, xx]) ** 2 / (2 * sigma_r ** 2))
+                    out[r] += w * (X[i].astype(np.float64) - X[yy * nx + xx].astype(np.float64))
+    return out
+
+
+@pytest.mark.parametrize("k,shape", [(4, (1100, 700)), (8, (1100, 700)), (16, (400, 450)),
+                                     (32, (400, 450)), (48, (300, 333))])
+def test_apply_l_block_widths_sampled(k, shape):
+    """The 7 x 7 L operator with weights on the fly at each register-blocked block width, on
+    images with more tiles than the GPU has SMs (several tiles per CTA, both halo buffers
+    in use) and ragged right and bottom edges; sampled rows against the definition."""
+    _, g = image_case(shape[0], shape[1], 11)
+    G = bf().bf_weights(dev(g), 3, 2.0, 0.08)
+    X = np.random.default_rng(k).standard_normal((g.size, k)).astype(np.float32)
+    X[:, 0] = g.reshape(-1)
+    Y = host(bf().bf_apply(G, "L", dev(X)))
+    assert np.all(np.isfinite(Y))
+    ny, nx = shape
+    rng = np.random.default_rng(2)
+    edge = [0, nx - 1, (ny - 1) * nx, g.size - 1, 31, 32, 33 * nx + 63, (ny - 2) * nx + nx // 2,
+            (ny // 2) * nx + nx - 2, 15 * nx + 16, 16 * nx + 17, 63 * nx + 5, 64 * nx + 5]
+    rows = np.concatenate([rng.integers(0, g.size, 150), edge])
+    ref = _l_rows_from_definition(g, X, rows, 3, 2.0, 0.08)
+    for r, i in enumerate(rows):
+        assert rel_l2(Y[i], ref[r]) < 1e-5, (int(i), rel_l2(Y[i], ref[r]))
+
+
+def test_apply_l_spatial_only_weights():
+    """sigma_r = inf (range term off, pure spatial Gaussian) on the 7 x 7 window."""
+    _, g = image_case(45, 70, 4)
+    G, O = make_pair(g, 3, 2.0, np.inf)
+    X = np.random.default_rng(3).standard_normal((g.size, 16))
+    Xd = dev(X)
+    Y = host(bf().bf_apply(G, "L", Xd))
+    assert rel_l2(Y, O.apply("L", host(Xd))) < 1e-5
