@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
   double* YD = XD + RR_MMAX * RR_KLD;                     // [96][RR_KLD]: M X, M X', Z, C
   double* sc = YD + RR_MMAX * RR_KLD;                     // [96] unit-diagonal scaling
   double* rdg = sc + RR_MMAX;                             // [96] 1 / diag(R)
-  double* fv = rdg + RR_MMAX;                             // [96] multipliers of one step
-  double* th = fv + RR_MMAX;                              // [32] Rayleigh quotients
+  double* fv = rdg + RR_MMAX;                             // [2][96] multipliers (by step parity)
+  double* th = fv + 2 * RR_MMAX;                          // [32] Rayleigh quotients
   double* csd = th + RR_KMAX;                             // [16] k x k rotations
   double* snd = csd + RR_KMAX / 2;                        // [16]
   float* lam = reinterpret_cast<float*>(snd + RR_KMAX / 2);  // [96] FP32 eigenvalues of M
@@ -270,24 +270,40 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
       __syncthreads();
       // Right-looking Cholesky B = R R^T with unscaled columns c (R(:, j) = c / sqrt(piv)),
       // carrying the forward solve Y = R^-1 A along: both updates use f_i = c_i / piv.
+      // Look-ahead: in step j warp 0 updates column j + 1 and forms the multipliers of step
+      // j + 1 (the serial reciprocal chain) while the other warps update the rest, so each
+      // step ends in one barrier.  fv holds two multiplier buffers, by step parity.
+      if (wid == 0 && RB[0] > DEP_TOL) {
+        const double ip = frcp(RB[0]);
+        for (int i = 1 + lane; i < m; i += 32) fv[i] = RB[i * RR_LD] * ip;
+      }
+      __syncthreads();
       for (int j = 0; j < m; ++j) {
-        if (wid == 0) {
-          const double piv = RB[j * RR_LD + j];
-          if (piv > DEP_TOL) {
-            const double ip = frcp(piv);
-            for (int i = j + 1 + lane; i < m; i += 32) fv[i] = RB[i * RR_LD + j] * ip;
-          }
-        }
-        __syncthreads();
         if (!(RB[j * RR_LD + j] > DEP_TOL)) break;       // same value in every thread
-        const int t = m - j - 1, nb = t * (t + 1) / 2;
-        for (int q = tid; q < nb + t * m; q += RR_T) {
-          if (q < nb) {                                  // trailing B: j < l <= i < m
-            const int e = tri[q], i = j + 1 + (e >> 8), l = j + 1 + (e & 255);
-            RB[i * RR_LD + l] = fma(-fv[i], RB[l * RR_LD + j], RB[i * RR_LD + l]);
-          } else {                                       // rows i > j of Y
-            const int q2 = q - nb, i1 = (int)fdv.div((unsigned)q2), c = q2 - i1 * m, i = j + 1 + i1;
-            MA[i * RR_LD + c] = fma(-fv[i], MA[j * RR_LD + c], MA[i * RR_LD + c]);
+        const double* fj = fv + (j & 1) * RR_MMAX;
+        const int t = m - j - 1;
+        if (wid == 0) {
+          if (t > 0) {                                   // column j + 1, then step j + 1's f
+            for (int i = j + 1 + lane; i < m; i += 32)
+              RB[i * RR_LD + j + 1] = fma(-fj[i], RB[(j + 1) * RR_LD + j], RB[i * RR_LD + j + 1]);
+            __syncwarp();
+            const double piv = RB[(j + 1) * RR_LD + j + 1];
+            if (piv > DEP_TOL) {
+              const double ip = frcp(piv);
+              double* fn = fv + ((j + 1) & 1) * RR_MMAX;
+              for (int i = j + 2 + lane; i < m; i += 32) fn[i] = RB[i * RR_LD + j + 1] * ip;
+            }
+          }
+        } else {
+          const int t2 = t - 1, nb = t2 > 0 ? t2 * (t2 + 1) / 2 : 0;
+          for (int q = tid - 32; q < nb + t * m; q += RR_T - 32) {
+            if (q < nb) {                                // trailing B: j + 1 < l <= i < m
+              const int e = tri[q], i = j + 2 + (e >> 8), l = j + 2 + (e & 255);
+              RB[i * RR_LD + l] = fma(-fj[i], RB[l * RR_LD + j], RB[i * RR_LD + l]);
+            } else {                                     // rows i > j of Y
+              const int q2 = q - nb, i1 = (int)fdv.div((unsigned)q2), c = q2 - i1 * m, i = j + 1 + i1;
+              MA[i * RR_LD + c] = fma(-fj[i], MA[j * RR_LD + c], MA[i * RR_LD + c]);
+            }
           }
         }
         __syncthreads();
@@ -316,18 +332,31 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
   __syncthreads();
 
   // ------------------------------------------ 3. M = Y R^-T (lower triangle), columns in order
-  for (int i = 0; i < m; ++i) {
-    if (wid == 0)
-      for (int r = i + lane; r < m; r += 32) {
-        const double v = MA[r * RR_LD + i] * rdg[i];  // final M(r, i)
-        MA[r * RR_LD + i] = v;
-        fv[r] = v;
+  // Look-ahead as in the Cholesky: in step i warp 0 updates and finalises column i + 1
+  // (the multipliers of step i + 1) while the other warps update columns i + 2 ...
+  if (wid == 0)
+    for (int r = lane; r < m; r += 32) {
+      const double v = MA[r * RR_LD] * rdg[0];      // final M(r, 0)
+      MA[r * RR_LD] = v;
+      fv[r] = v;
+    }
+  __syncthreads();
+  for (int i = 0; i + 1 < m; ++i) {
+    const double* fi = fv + (i & 1) * RR_MMAX;
+    if (wid == 0) {
+      double* fn = fv + ((i + 1) & 1) * RR_MMAX;
+      const double rl = RB[(i + 1) * RR_LD + i];
+      for (int r = i + 1 + lane; r < m; r += 32) {
+        const double v = fma(-fi[r], rl, MA[r * RR_LD + i + 1]) * rdg[i + 1];   // final M(r, i + 1)
+        MA[r * RR_LD + i + 1] = v;
+        fn[r] = v;
       }
-    __syncthreads();
-    const int t = m - i - 1;
-    for (int q = tid; q < t * (t + 1) / 2; q += RR_T) {   // i < l <= r < m
-      const int e = tri[q], r = i + 1 + (e >> 8), l = i + 1 + (e & 255);
-      MA[r * RR_LD + l] = fma(-fv[r], RB[l * RR_LD + i], MA[r * RR_LD + l]);
+    } else {
+      const int t2 = m - i - 2;
+      for (int q = tid - 32; q < t2 * (t2 + 1) / 2; q += RR_T - 32) {   // i + 1 < l <= r < m
+        const int e = tri[q], r = i + 2 + (e >> 8), l = i + 2 + (e & 255);
+        MA[r * RR_LD + l] = fma(-fi[r], RB[l * RR_LD + i], MA[r * RR_LD + l]);
+      }
     }
     __syncthreads();
   }
@@ -337,37 +366,49 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
 
   // ------------------------------------------ 4. FP32 eigen-decomposition of M
   // 4a. Householder reduction of float(M) (full storage in J) to a tridiagonal T; the
-  //     reflector vectors stay below the subdiagonal of J
+  //     reflector vectors stay below the subdiagonal of J.  Look-ahead: in step j warp 0
+  //     updates column j + 1 first and forms the reflector of step j + 1 while the other
+  //     warps update the rest of the trailing block; K = beta v^T p / 2 is summed by every
+  //     warp itself (the same lanes and order, so the same value).  Two barriers per step.
   for (int r = wid; r < m; r += RR_NW)
     for (int c = lane; c < m; c += 32) J[r * RR_LDF + c] = (float)symv(MA, r, c);
   __syncthreads();
+  // reflector of column j (warp 0): x = J(j+1:m, j) -> v = x - alpha e_1, beta = 2 / v^T v
+  auto reflector = [&](int j) {
+    const int n1 = m - j - 1;
+    float* col = J + (j + 1) * RR_LDF + j;
+    float s = 0.0f;
+    for (int i = lane; i < n1; i += 32) s = fmaf(col[i * RR_LDF], col[i * RR_LDF], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const float x0 = col[0];
+      const float tail = s - x0 * x0;
+      float al = x0, be = 0.0f;
+      if (tail > 0.0f) {
+        const float nrm = sqrtf(s);
+        al = (x0 >= 0.0f) ? -nrm : nrm;
+        const float v0 = x0 - al;
+        be = 2.0f / fmaf(v0, v0, tail);
+        col[0] = v0;
+      }
+      dd32[j] = J[j * RR_LDF + j];
+      ee32[j] = al;
+      bet32[j] = be;
+    }
+  };
+  if (m >= 3 && wid == 0) reflector(0);
+  __syncthreads();
   for (int j = 0; j + 2 < m; ++j) {
     const int n1 = m - j - 1;
-    float* col = J + (j + 1) * RR_LDF + j;          // x_i = col[i * RR_LDF], i < n1
-    if (wid == 0) {
-      float s = 0.0f;
-      for (int i = lane; i < n1; i += 32) s = fmaf(col[i * RR_LDF], col[i * RR_LDF], s);
-      s = warp_sum(s);
-      if (lane == 0) {
-        const float x0 = col[0];
-        const float tail = s - x0 * x0;
-        float al = x0, be = 0.0f;
-        if (tail > 0.0f) {
-          const float nrm = sqrtf(s);
-          al = (x0 >= 0.0f) ? -nrm : nrm;
-          const float v0 = x0 - al;
-          be = 2.0f / fmaf(v0, v0, tail);
-          col[0] = v0;
-        }
-        dd32[j] = J[j * RR_LDF + j];
-        ee32[j] = al;
-        bet32[j] = be;
-      }
-    }
-    __syncthreads();
+    const bool next = (j + 3 < m);
     const float beta = bet32[j];
-    if (beta == 0.0f) continue;
+    float* col = J + (j + 1) * RR_LDF + j;          // v_i = col[i * RR_LDF], i < n1
     float* A1 = J + (j + 1) * RR_LDF + (j + 1);      // trailing n1 x n1 block
+    if (beta == 0.0f) {                              // nothing to reflect: next column as is
+      if (next && wid == 0) reflector(j + 1);
+      __syncthreads();
+      continue;
+    }
     for (int r = wid; r < n1; r += RR_NW) {           // p = beta A1 v
       float s = 0.0f;
       for (int c = lane; c < n1; c += 32) s = fmaf(A1[r * RR_LDF + c], col[c * RR_LDF], s);
@@ -375,19 +416,24 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
       if (lane == 0) pv32[r] = beta * s;
     }
     __syncthreads();
-    if (wid == 0) {
-      float s = 0.0f;
-      for (int i = lane; i < n1; i += 32) s = fmaf(col[i * RR_LDF], pv32[i], s);
-      s = warp_sum(s);
-      if (lane == 0) shK = 0.5f * beta * s;
-    }
-    __syncthreads();
-    const float K = shK;
-    for (int r = wid; r < n1; r += RR_NW) {           // A1 -= v w^T + w v^T, w = p - K v
-      const float vr = col[r * RR_LDF], wr = fmaf(-K, vr, pv32[r]);
-      for (int c = lane; c < n1; c += 32) {
-        const float vc = col[c * RR_LDF], wc = fmaf(-K, vc, pv32[c]);
-        A1[r * RR_LDF + c] = fmaf(-vr, wc, fmaf(-wr, vc, A1[r * RR_LDF + c]));
+    float K = 0.0f;
+    for (int i = lane; i < n1; i += 32) K = fmaf(col[i * RR_LDF], pv32[i], K);
+    K = 0.5f * beta * warp_sum(K);
+    if (wid == 0) {                                   // column j + 1 of J, then its reflector
+      const float v0 = col[0], w0 = fmaf(-K, v0, pv32[0]);
+      for (int r = lane; r < n1; r += 32) {
+        const float vr = col[r * RR_LDF], wr = fmaf(-K, vr, pv32[r]);
+        A1[r * RR_LDF] = fmaf(-vr, w0, fmaf(-wr, v0, A1[r * RR_LDF]));
+      }
+      __syncwarp();
+      if (next) reflector(j + 1);
+    } else {                                          // A1(1:, 1:) -= v w^T + w v^T, w = p - K v
+      for (int r = wid; r < n1; r += RR_NW - 1) {     // rows 1 .. n1-1 over warps 1 .. RR_NW-1
+        const float vr = col[r * RR_LDF], wr = fmaf(-K, vr, pv32[r]);
+        for (int c = 1 + lane; c < n1; c += 32) {
+          const float vc = col[c * RR_LDF], wc = fmaf(-K, vc, pv32[c]);
+          A1[r * RR_LDF + c] = fmaf(-vr, wc, fmaf(-wr, vc, A1[r * RR_LDF + c]));
+        }
       }
     }
     __syncthreads();
@@ -502,8 +548,8 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   double* YD = XD + RR_MMAX * RR_KLD;                     // [96][RR_KLD]: M X, M X', Z, C
   double* sc = YD + RR_MMAX * RR_KLD;                     // [96] unit-diagonal scaling
   double* rdg = sc + RR_MMAX;                             // [96] 1 / diag(R)
-  double* fv = rdg + RR_MMAX;                             // [96] multipliers of one step
-  double* th = fv + RR_MMAX;                              // [32] Rayleigh quotients
+  double* fv = rdg + RR_MMAX;                             // [2][96] multipliers (by step parity)
+  double* th = fv + 2 * RR_MMAX;                          // [32] Rayleigh quotients
   double* csd = th + RR_KMAX;                             // [16] k x k rotations
   double* snd = csd + RR_KMAX / 2;                        // [16]
   float* lam = reinterpret_cast<float*>(snd + RR_KMAX / 2);  // [96] FP32 eigenvalues of M
@@ -721,6 +767,15 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     const FastDiv fkp(kp);
     const int nblk = kh * (kh + 1) / 2;
     for (int sweep = 0; sweep < 30; ++sweep) {
+      // a sweep that would rotate nothing ends the iteration: every pair is tested at
+      // once (one barrier) instead of round by round (kp - 1 barriers)
+      int need = 0;
+      for (int q2 = tid; q2 < kp * kp; q2 += RR_T) {
+        const int p = (int)fkp.div((unsigned)q2), q = q2 - p * kp;
+        if (p < q && fabs(H[p * RR_KLD + q]) > 1e-13 * (fabs(H[p * RR_KLD + p]) + fabs(H[q * RR_KLD + q])) + 1e-300)
+          need = 1;
+      }
+      if (__syncthreads_or(need) == 0) break;
       int nrot = 0;
       for (int step = 0; step < kp - 1; ++step) {
         int rot = 0;
@@ -826,10 +881,24 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   __syncthreads();
 
   // ------------------------------------------ 9. C = R^-T Z (rows from the bottom), unscale
-  for (int i = m - 1; i >= 0; --i) {
-    if (wid == 0 && lane < k) fv[lane] = YD[i * RR_KLD + lane] * rdg[i];
-    __syncthreads();
-    FOR_RC(tk, i, k, wid) YD[r * RR_KLD + c] = fma(-MA[r * RR_LD + i], fv[c], YD[r * RR_KLD + c]);
+  // Look-ahead: in step i warp 0 updates row i - 1 and forms its multipliers while the
+  // other warps update the rows above it; one barrier per row.
+  if (wid == 0 && lane < k) fv[((m - 1) & 1) * RR_MMAX + lane] = YD[(m - 1) * RR_KLD + lane] * rdg[m - 1];
+  __syncthreads();
+  for (int i = m - 1; i >= 1; --i) {
+    const double* fi = fv + (i & 1) * RR_MMAX;
+    if (wid == 0) {
+      if (lane < k) {
+        const double y = fma(-MA[(i - 1) * RR_LD + i], fi[lane], YD[(i - 1) * RR_KLD + lane]);
+        YD[(i - 1) * RR_KLD + lane] = y;
+        fv[((i - 1) & 1) * RR_MMAX + lane] = y * rdg[i - 1];
+      }
+    } else {
+      for (int r0 = (wid - 1) * tk.rows; r0 < i - 1; r0 += (RR_NW - 1) * tk.rows) {
+        const int r = r0 + tk.lr, c = tk.lc;
+        if (r < i - 1 && c < k) YD[r * RR_KLD + c] = fma(-MA[r * RR_LD + i], fi[c], YD[r * RR_KLD + c]);
+      }
+    }
     __syncthreads();
   }
   FOR_RC(tk, a.m, k, wid) a.C[r * k + c] = (r < m) ? YD[r * RR_KLD + c] * (rdg[r] * sc[r]) : 0.0;
@@ -881,7 +950,7 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
 }
 
 size_t rr_smem_bytes() {
-  return (size_t)(2 * RR_MMAX * RR_LD + 2 * RR_MMAX * RR_KLD + 3 * RR_MMAX + RR_KMAX + RR_KMAX) *
+  return (size_t)(2 * RR_MMAX * RR_LD + 2 * RR_MMAX * RR_KLD + 4 * RR_MMAX + RR_KMAX + RR_KMAX) *
              sizeof(double) +
          (size_t)(6 * RR_MMAX) * sizeof(float) +
          (2 * RR_KMAX + RR_MMAX + RR_MMAX) * sizeof(int) +
