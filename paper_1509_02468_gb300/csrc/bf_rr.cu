@@ -806,37 +806,57 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
         const int nstep = __syncthreads_count(rot);
         nrot += nstep;
         if (nstep == 0) continue;
-        for (int q2 = tid; q2 < nblk + kh * kp; q2 += RR_T) {
-          if (q2 < nblk) {
-            const int e = tri[q2], bb = e >> 8, ba = e & 255;
+        // A warp-wide FP64 instruction holds an SMSP's FP64 pipe for ~64 cycles however
+        // few lanes are active, so the work is packed into full warps spread over the SMSPs:
+        // the first hw warps take the 2 x 2 blocks of H (ba <= bb) as two half-tasks on
+        // lanes 2i, 2i + 1 (one output row of the block each), the other warps Vk.
+        const int hw = (nblk + 15) / 16;
+        if (wid < hw) {
+          const int task = tid >> 1, h = tid & 1;
+          int pa = 0, qa = 0, pb = 0, qb = 0;
+          bool act = false, dg = false;
+          double n0 = 0.0, n1 = 0.0;
+          if (task < nblk) {
+            const int e = tri[task], bb = e >> 8, ba = e & 255;
             const double sa = snd[ba], sb = snd[bb];
-            if (sa == 0.0 && sb == 0.0) continue;
-            const int pa = pp[ba], qa = qq[ba], pb = pp[bb], qb = qq[bb];
-            const double ca = csd[ba], cb = csd[bb];
-            const double j00 = H[pa * RR_KLD + pb], j01 = H[pa * RR_KLD + qb];
-            const double j10 = H[qa * RR_KLD + pb], j11 = H[qa * RR_KLD + qb];
-            const double t00 = ca * j00 - sa * j10, t01 = ca * j01 - sa * j11;
-            const double t10 = sa * j00 + ca * j10, t11 = sa * j01 + ca * j11;
-            const double n00 = cb * t00 - sb * t01, n01 = sb * t00 + cb * t01;
-            const double n10 = cb * t10 - sb * t11, n11 = sb * t10 + cb * t11;
-            if (bb == ba) {
-              const double off = 0.5 * (n01 + n10);
-              H[pa * RR_KLD + pa] = n00;
-              H[qa * RR_KLD + qa] = n11;
-              H[pa * RR_KLD + qa] = off;
-              H[qa * RR_KLD + pa] = off;
-              continue;
+            act = !(sa == 0.0 && sb == 0.0);
+            if (act) {
+              pa = pp[ba], qa = qq[ba], pb = pp[bb], qb = qq[bb];
+              dg = (bb == ba);
+              const double ca = csd[ba], cb = csd[bb];
+              const double j00 = H[pa * RR_KLD + pb], j01 = H[pa * RR_KLD + qb];
+              const double j10 = H[qa * RR_KLD + pb], j11 = H[qa * RR_KLD + qb];
+              double t0, t1;
+              if (h == 0) {
+                t0 = ca * j00 - sa * j10;
+                t1 = ca * j01 - sa * j11;
+              } else {
+                t0 = sa * j00 + ca * j10;
+                t1 = sa * j01 + ca * j11;
+              }
+              n0 = cb * t0 - sb * t1;
+              n1 = sb * t0 + cb * t1;
             }
-            H[pa * RR_KLD + pb] = n00;
-            H[pa * RR_KLD + qb] = n01;
-            H[qa * RR_KLD + pb] = n10;
-            H[qa * RR_KLD + qb] = n11;
-            H[pb * RR_KLD + pa] = n00;
-            H[qb * RR_KLD + pa] = n01;
-            H[pb * RR_KLD + qa] = n10;
-            H[qb * RR_KLD + qa] = n11;
-          } else {
-            const int q3 = q2 - nblk, ba = (int)fkp.div((unsigned)q3), r = q3 - ba * kp;
+          }
+          // diagonal blocks: n01 (lane h = 0) and n10 (lane h = 1) are averaged
+          const double other = __shfl_xor_sync(0xffffffffu, h ? n0 : n1, 1);
+          __syncwarp();                                  // every read of H before any write
+          if (act) {
+            const int ra = h ? qa : pa;
+            if (dg) {
+              const double off = h ? 0.5 * (other + n0) : 0.5 * (n1 + other);
+              H[ra * RR_KLD + ra] = h ? n1 : n0;
+              H[ra * RR_KLD + (h ? pa : qa)] = off;
+            } else {
+              H[ra * RR_KLD + pb] = n0;
+              H[ra * RR_KLD + qb] = n1;
+              H[pb * RR_KLD + ra] = n0;
+              H[qb * RR_KLD + ra] = n1;
+            }
+          }
+        } else {
+          for (int q3 = tid - 32 * hw; q3 < kh * kp; q3 += RR_T - 32 * hw) {
+            const int ba = (int)fkp.div((unsigned)q3), r = q3 - ba * kp;
             const double sa = snd[ba];
             if (sa == 0.0) continue;
             const double ca = csd[ba];
