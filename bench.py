@@ -9,8 +9,12 @@ on the host and resident on the device before the timed region; L2 (126 MB) is f
 writing a 256 MB buffer between timed steps, and each step is timed with CUDA events on
 the launching stream.
 
-Extra keys: `roofline` for the bilateral operator kernel (k = 16 block apply, timed alone
-with an L2 flush before each launch), `cpu_baseline` (the FP64 CPU oracle, one thread, on
+Extra keys: `roofline` for the bilateral operator kernel (L X on a k = 16 block, timed alone
+with an L2 flush before each launch; bound by the FP32 pipe, with its HBM fraction beside),
+`roofline_2048` (the same on a 2048 x 2048 image, X and Y far larger than L2),
+`roofline_dominant` (the Rayleigh-Ritz solve, the largest share of the step's GPU time),
+`batched` (CG on 256 uneven instances, one CUDA graph, against plain calls),
+`cpu_baseline` (the FP64 CPU oracle, one thread, on
 one full step of the same workload), `e2e` (the same pipeline from pinned host memory to
 host results), `clocks` (nvidia-smi sampled during the timed region) and `gpu_launches`
 (kernels the library launched per timed step, from its own counter).
@@ -238,43 +242,28 @@ def run_gpu(args):
         ms = float(t.item())
     value = world * npix / (ms * 1e-3) / 1e6
 
-    # ---- accuracy of the timed configuration (device results vs FP64 oracle, CG output)
-    # checked by the test suite; here only the per-step outputs are kept finite
-    # ---- roofline of the bilateral operator (k = 16 block, on-the-fly weights)
-    G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
-    Xa = torch.randn(npix, 16, device="cuda")
-    Ya = torch.empty_like(Xa)
-    for _ in range(3):
-        bf.bf_apply(G, "L", Xa, Y=Ya)
-    at = []
-    for _ in range(20):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bf.bf_apply(G, "L", Xa, Y=Ya)
-        e1.record(stream)
-        e1.synchronize()
-        at.append(e0.elapsed_time(e1))
-    apply_ms = statistics.mean(at)
-    bytes_per_px = 4 + 8 * 16          # guide + X in + Y out (k = 16, fp32)
-    traffic_alg = bytes_per_px * npix
-    achieved = traffic_alg / (apply_ms * 1e-3) / 1e9
+    # ---- rooflines.  The operator (L X, k = 16, on-the-fly weights) on the step's image and
+    # on a 2048 x 2048 image of the same generator (X and Y far larger than L2); the
+    # Rayleigh-Ritz solve, the largest share of the step's GPU time.
     peak, peak_src = _peaks()
-    roofline = {"kernel": "k_apply_rb<16> (L, 7x7, on-the-fly weights)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": TRAFFIC_APPLY, "algorithmic_bytes": traffic_alg,
-                "ms_per_launch": apply_ms}
-    # ---- the kernel with the largest share of the step: the one-CTA FP64 Rayleigh-Ritz
-    # solve of LOBPCG (m = 48, k = 16), bound by one SM's FP64 issue and latency
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = nsm * FP32_LANES_PER_SM * _sm_max_ghz() * 1e9      # FP32 lane-ops per second
+    roofline = _apply_roofline(bf, torch, stream, flush, guide, w, 16, peak, peak_src, alu_peak,
+                               TRAFFIC_APPLY_512)
+    _, noisy2k = synth.polygon_image(2048, 2048, w["seed"], noise=w["noise"])
+    roofline_2048 = _apply_roofline(bf, torch, stream, flush, torch.as_tensor(noisy2k).cuda(), w, 16,
+                                    peak, peak_src, alu_peak, TRAFFIC_APPLY_2048)
+    del noisy2k
     rr_ms = _time_rr(bf, torch, stream, flush)
     rr_flops = 2.0 * RR_FP64_FMA
-    rr_peak = 2.0 * 2.0 * 2.07      # GFLOP/s: one SM, 2 FP64 FMA per clock, 2.07 GHz
-    roofline_rr = {"kernel": "k_rr (Rayleigh-Ritz, m=48, k=16, one CTA)", "bound": "alu",
-                   "achieved": rr_flops / (rr_ms * 1e-3) / 1e9, "peak": rr_peak,
-                   "unit": "GFLOP/s (FP64, one SM)",
-                   "frac": rr_flops / (rr_ms * 1e-3) / 1e9 / rr_peak, "ms_per_launch": rr_ms,
-                   "share_of_step": RR_SHARE}
+    rr_peak = 2.0 * 2.0 * _sm_max_ghz()      # GFLOP/s: one SM, 2 FP64 FMA per clock
+    roofline_rr = {"kernel": "Rayleigh-Ritz (k_rr_reduce + k_rr_vectors + k_rr; m=48, k=16)",
+                   "bound": "alu", "achieved": rr_flops / (rr_ms * 1e-3) / 1e9, "peak": rr_peak,
+                   "unit": "GFLOP/s (FP64 work, one SM)",
+                   "frac": rr_flops / (rr_ms * 1e-3) / 1e9 / rr_peak, "ms_per_call": rr_ms,
+                   "share_of_step": RR_SHARE,
+                   "note": "latency-bound chain of small dependent steps; FP64 pipe of one SM as "
+                           "the unit-count peak"}
 
     # ---- end to end through the public API from pinned host memory
     gh = torch.as_tensor(noisy).pin_memory()
@@ -333,7 +322,8 @@ def run_gpu(args):
                            "lobpcg_iters": w["lob_iters"], "weights": "on-the-fly fp32",
                            "l2": "flushed between steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "roofline_dominant": roofline_rr, "cpu_baseline": cpu,
+                "roofline": roofline, "roofline_2048": roofline_2048,
+                "roofline_dominant": roofline_rr, "cpu_baseline": cpu,
                 "batched": batched,
                 "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -345,16 +335,64 @@ def run_gpu(args):
     return 0
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_rb<16> launch (512 x 512, k = 16)
-# from an ncu capture of that launch (its 16.8 MB of output stay in L2 during the launch)
-TRAFFIC_APPLY = 17.89e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply_pipe<16> launch from an ncu
+# capture of `bench.py --case apply` (512 x 512: the 16.8 MB of Y stay in L2 during the
+# launch) and of `bench.py --case apply --case-side 2048`
+TRAFFIC_APPLY_512 = 17909760
+TRAFFIC_APPLY_2048 = 499885824
+FP32_LANES_PER_SM = 128
 # FP64 FMAs of one Rayleigh-Ritz call at m = 48, k = 16 (Cholesky with the forward solve
 # 2m^3/3, standard form m^3/6, M X twice 2 m^2 k, Gram/Löwdin/H 3 m k^2, back-substitution
 # m^2 k / 2, next-P coefficients m^2 k + 2 m k^2) and its share of the step's GPU time in
 # an ncu launch list of the timed step
 RR_FP64_FMA = (2 * 48 ** 3 / 3 + 48 ** 3 / 6 + 2 * 48 * 48 * 16 + 3 * 48 * 16 * 16
                + 48 * 48 * 16 / 2 + 48 * 48 * 16 + 2 * 48 * 16 * 16)
-RR_SHARE = 0.506
+RR_SHARE = 0.494
+
+
+def _sm_max_ghz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]) / 1e3
+    except Exception:
+        return 2.07
+
+
+def _apply_roofline(bf, torch, stream, flush, guide, w, k, peak, peak_src, alu_peak, traffic):
+    """L X for a k-column block with weights on the fly: event-timed launches (L2 flushed
+    before each), against the FP32 pipe (its bound: the difference form costs a subtract
+    and an FMA per tap and column, plus three operations per weight) and against HBM."""
+    ny, nx = guide.shape
+    n = ny * nx
+    G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
+    X = torch.randn(n, k, device="cuda")
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        bf.bf_apply(G, "L", X, Y=Y)
+    ts = []
+    for _ in range(20):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bf.bf_apply(G, "L", X, Y=Y)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.mean(ts)
+    r = w["radius"]
+    pairs = sum((ny - abs(dy)) * (nx - abs(dx)) for dy in range(-r, r + 1) for dx in range(-r, r + 1)
+                if dy or dx)                                  # (pixel, neighbour) pairs in the image
+    ops = pairs * (2 * k + 3)
+    byts = (4 + 8 * k) * n
+    achieved = ops / (ms * 1e-3)
+    del G, X, Y
+    return {"kernel": f"k_apply_pipe<{k}> (L, 7x7, on-the-fly weights, {ny}x{nx})", "bound": "alu",
+            "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
+            "frac": achieved / alu_peak, "traffic": traffic, "algorithmic_bytes": byts,
+            "algorithmic_ops": ops, "ms_per_launch": ms,
+            "hbm": {"achieved": byts / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": byts / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_src}}
 
 
 def _time_rr(bf, torch, stream, flush, m=48, k=16, reps=20):
