@@ -149,7 +149,10 @@ __device__ void tc_stage(const TcArgs& a, int64_t c, unsigned char* Ahi, unsigne
       const int cq = tt % kq, rest = tt / kq;
       const int pp = rest % (TC_KT / 2), bk = rest / (TC_KT / 2);
       const int64_t p = p0 + 2 * pp;
-      const float* src = is_as ? a.AS[bk] : a.S[bk];
+      // selects rather than a runtime index into the parameter arrays (which would copy
+      // them to local memory)
+      const float* const* blocks = is_as ? a.AS : a.S;
+      const float* src = bk == 0 ? blocks[0] : (bk == 1 ? blocks[1] : blocks[2]);
       if (p < a.n) v0[u] = __ldg(reinterpret_cast<const float4*>(src + p * a.k + 4 * cq));
       if (p + 1 < a.n) v1[u] = __ldg(reinterpret_cast<const float4*>(src + (p + 1) * a.k + 4 * cq));
     }
@@ -191,7 +194,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const TcArgs a) {
   const uint32_t b_bytes = (uint32_t)a.N * TC_KT * 2;
   const uint32_t half = a_bytes + b_bytes;                   // hi (or lo) part of one buffer
   const uint32_t buf_bytes = (SPLIT ? 2 : 1) * half;
-  unsigned char* bufp[2] = {smem, smem + buf_bytes};
   for (uint32_t i = tid; i < 2 * buf_bytes / 16; i += TC_THREADS)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);   // padding rows stay zero
   if (tid == 0) {
@@ -213,9 +215,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const TcArgs a) {
   const int my = (int)((nch - blockIdx.x + gridDim.x - 1) / gridDim.x);   // chunks blockIdx.x + j * grid
   const uint32_t idesc = idesc_bf16(a.N, TC_M);
   bool ok = true;
-  uint32_t phase[2] = {0u, 0u};
+  uint32_t phase0 = 0u, phase1 = 0u;            // mbarrier phases of the two buffers
   if (my > 0) {
-    unsigned char* b0 = bufp[0];
+    unsigned char* b0 = smem;
     tc_stage<SPLIT>(a, blockIdx.x, b0, b0 + half, b0 + a_bytes, b0 + half + a_bytes);
     proxy_fence();
   }
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const TcArgs a) {
     const int cb = j & 1;
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t base = smem_u32(bufp[cb]);
+      const uint32_t base = smem_u32(smem + cb * buf_bytes);
       const uint32_t Ah = base, Bh = base + a_bytes, Al = base + half, Bl = base + half + a_bytes;
 #pragma unroll
       for (int s = 0; s < TC_KT / 16; ++s) {
@@ -240,10 +242,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const TcArgs a) {
     if (j + 1 < my) {
       const int nb = (j + 1) & 1;
       if (j >= 1) {                       // buffer nb was read by the MMAs of chunk j - 1
-        ok = mbar_wait(&bars[nb], phase[nb]) && ok;
-        phase[nb] ^= 1u;
+        ok = mbar_wait(&bars[nb], nb ? phase1 : phase0) && ok;
+        if (nb) phase1 ^= 1u;
+        else phase0 ^= 1u;
       }
-      unsigned char* bn = bufp[nb];
+      unsigned char* bn = smem + nb * buf_bytes;
       tc_stage<SPLIT>(a, blockIdx.x + (int64_t)(j + 1) * gridDim.x, bn, bn + half, bn + a_bytes,
                       bn + half + a_bytes);
       proxy_fence();
@@ -252,9 +255,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const TcArgs a) {
   }
   if (my > 0) {                           // the last commit covers every MMA issued before it
     const int lb = (my - 1) & 1;
-    if (!mbar_wait(&bars[lb], phase[lb])) {
+    const uint32_t ph = lb ? phase1 : phase0;
+    if (!mbar_wait(&bars[lb], ph)) {
       ok = false;
-      mbar_wait(&bars[lb], phase[lb]);
+      mbar_wait(&bars[lb], ph);
     }
   }
   tc_fence_after();
@@ -281,14 +285,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const TcArgs a) {
   if (!ok && tid == 0 && a.err) atomicExch(a.err, 4);
 }
 
-// G[0] = S^T A S, G[1] = S^T B S (FP64, [2][m][m]) from the CTAs' FP32 partials.
+// G[0] = S^T A S, G[1] = S^T B S (FP64, [2][m][m]) from the CTAs' FP32 partials: one warp
+// per entry, each lane a strided share of the CTAs, combined by shuffles.
 __global__ void k_gram_tc_reduce(const float* partials, int nblocks, int m, double* G, const int* status) {
   if (status && *status != 0) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = gtid >> 5, part = gtid & 31;
   const int m2 = 2 * m;
-  if (e >= m * m2) return;
+  const bool ok = e < m * m2;
   double s = 0.0;
-  for (int bl = 0; bl < nblocks; ++bl) s += (double)partials[(size_t)bl * m * m2 + e];
+  if (ok)
+    for (int bl = part; bl < nblocks; bl += 32) s += (double)partials[(size_t)bl * m * m2 + e];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (!ok || part != 0) return;
   const int i = e / m2, j = e - i * m2;
   if (j < m) G[(size_t)i * m + j] = s;
   else G[(size_t)m * m + (size_t)i * m + (j - m)] = s;
@@ -330,7 +340,7 @@ int bf_gram_tc(const float* const* S, const float* const* AS, const float* b, in
   if (split) BF_LAUNCH((k_gram_tc<true><<<grid, TC_THREADS, sm, s>>>(a)));
   else BF_LAUNCH((k_gram_tc<false><<<grid, TC_THREADS, sm, s>>>(a)));
   const int ne = m * 2 * m;
-  BF_LAUNCH((k_gram_tc_reduce<<<(ne + 255) / 256, 256, 0, s>>>(partials, grid, m, G, status)));
+  BF_LAUNCH((k_gram_tc_reduce<<<(ne * 32 + 255) / 256, 256, 0, s>>>(partials, grid, m, G, status)));
   BF_CUDA(cudaGetLastError());
   return BF_OK;
 }

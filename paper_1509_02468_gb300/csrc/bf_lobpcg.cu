@@ -404,13 +404,13 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
   }
 }
 
-// Sum the Gram partials over blocks in block order (eight lanes per entry, each a strided
-// share, combined by shuffles) and write both triangles: G[2][m][m].
+// Sum the Gram partials over blocks (one warp per entry, each lane a strided share of the
+// blocks, combined by shuffles) and write both triangles: G[2][m][m].
 __global__ void k_gram_reduce(const double* __restrict__ partials, int nblocks, int m, double* G,
                               const LobState* st) {
   if (st->status != LOB_RUN) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int e = gtid >> 3, part = gtid & 7;
+  const int e = gtid >> 5, part = gtid & 31;
   const int nupper = m * (m + 1) / 2;
   const bool ok = e < 2 * nupper;
   int w = 0, r = 0, c = 0;
@@ -423,11 +423,10 @@ __global__ void k_gram_reduce(const double* __restrict__ partials, int nblocks, 
   double s = 0.0;
   if (ok) {
     const size_t off = (size_t)w * m * m + (size_t)r * m + c;
-    for (int b = part; b < nblocks; b += 8) s += partials[(size_t)b * 2 * m * m + off];
+    for (int b = part; b < nblocks; b += 32) s += partials[(size_t)b * 2 * m * m + off];
   }
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (ok && part == 0) {
     G[(size_t)w * m * m + (size_t)r * m + c] = s;
     G[(size_t)w * m * m + (size_t)c * m + r] = s;
@@ -733,7 +732,7 @@ static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
 
 static void run_gram_reduce(const double* partials, int nblocks, int m, double* G,
                             const LobState* st, cudaStream_t s) {
-  const int threads = 2 * (m * (m + 1) / 2) * 8;
+  const int threads = 2 * (m * (m + 1) / 2) * 32;
   BF_LAUNCH(k_gram_reduce<<<(threads + 255) / 256, 256, 0, s>>>(partials, nblocks, m, G, st));
 }
 
