@@ -63,8 +63,14 @@ __device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
   float p0 = 1.0f, p1 = d[0] - x;
   if (p1 == 0.0f) p1 = -0x1p-40f;
   int cnt = (p1 < 0.0f);
+  float dn = (m > 1) ? d[1] : 0.0f, en = e2[0];   // operands of the next step, loaded ahead
   for (int i = 1; i < m; ++i) {
-    float p2 = (d[i] - x) * p1 - e2[i - 1] * p0;
+    const float di = dn, ei = en;
+    if (i + 1 < m) {
+      dn = d[i + 1];
+      en = e2[i];
+    }
+    float p2 = (di - x) * p1 - ei * p0;
     if (p2 == 0.0f) p2 = -p1 * 0x1p-40f;
     cnt += ((p2 < 0.0f) != (p1 < 0.0f));
     p0 = p1;
@@ -83,10 +89,10 @@ __device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
 // working row, entries in columns i, i+1, i+2, against the next original row; the larger
 // entry in column i pivots; zero pivots become `tiny`), then `reps` solves from the start
 // vector b, each normalised by its largest entry.
+// f, ri, u1, u2, sw: work arrays of m entries (shared memory).
 __device__ void tri_inverse_iteration(const float* d, const float* e, int m, float lambda, float tiny,
-                                      int reps, float* b) {
-  float f[RR_MMAX], ri[RR_MMAX], u1[RR_MMAX], u2[RR_MMAX];
-  unsigned char sw[RR_MMAX];
+                                      int reps, float* b, float* f, float* ri, float* u1, float* u2,
+                                      unsigned char* sw) {
   float r0 = d[0] - lambda, r1 = (m > 1) ? e[0] : 0.0f, r2 = 0.0f;
   for (int i = 0; i < m - 1; ++i) {
     const float n0 = e[i], n1 = d[i + 1] - lambda, n2 = (i + 2 < m) ? e[i + 1] : 0.0f;
@@ -118,9 +124,18 @@ __device__ void tri_inverse_iteration(const float* d, const float* e, int m, flo
       b[i] = pb;
       rb = fmaf(-f[i], pb, ob);
     }
-    b[m - 1] = rb * ri[m - 1];
-    if (m > 1) b[m - 2] = fmaf(-u1[m - 2], b[m - 1], b[m - 2]) * ri[m - 2];
-    for (int i = m - 3; i >= 0; --i) b[i] = fmaf(-u2[i], b[i + 2], fmaf(-u1[i], b[i + 1], b[i])) * ri[i];
+    float x2 = rb * ri[m - 1], x1 = x2;              // b[i + 2], b[i + 1] carried in registers
+    b[m - 1] = x2;
+    if (m > 1) {
+      x1 = fmaf(-u1[m - 2], x2, b[m - 2]) * ri[m - 2];
+      b[m - 2] = x1;
+    }
+    for (int i = m - 3; i >= 0; --i) {
+      const float x0 = fmaf(-u2[i], x2, fmaf(-u1[i], x1, b[i])) * ri[i];
+      b[i] = x0;
+      x2 = x1;
+      x1 = x0;
+    }
     float nrm = 0.0f;
     for (int i = 0; i < m; ++i) nrm = fmaxf(nrm, fabsf(b[i]));
     const float inv = (nrm > 0.0f && isfinite(nrm)) ? __fdividef(1.0f, nrm) : 1.0f;
@@ -490,11 +505,36 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
   RRScratch* S = a.scr;
   const int m = S->m, j = blockIdx.x, lane = threadIdx.x;
   if (j >= m) return;
-  __shared__ float dd[RR_MMAX], ee[RR_MMAX], e2[RR_MMAX], v[RR_MMAX];
+  __shared__ float dd[RR_MMAX], ee[RR_MMAX], e2[RR_MMAX], v[RR_MMAX], bet[RR_MMAX];
+  __shared__ float f[RR_MMAX], ri[RR_MMAX], u1[RR_MMAX], u2[RR_MMAX];
+  __shared__ unsigned char sw[RR_MMAX];
+  // reflector vectors, transposed: Jt[c * RR_LDF + r] = J(r, c) for r > c + 1 (J(c + 1, c)
+  // holds v_0); staged by all lanes with their loads in flight together, since J was
+  // written by the previous kernel and every read of it from L2 costs hundreds of cycles
+  __shared__ float Jt[(RR_MMAX - 2) * RR_LDF];
   for (int i = lane; i < m; i += 32) {
     dd[i] = S->dd[i];
     ee[i] = S->ee[i];
     e2[i] = S->e2[i];
+    bet[i] = S->bet[i];
+  }
+  {
+    const int tot = m * m;
+    for (int q0 = 0; q0 < tot; q0 += 24 * 32) {
+      float val[24];
+#pragma unroll
+      for (int u = 0; u < 24; ++u) {
+        const int q = q0 + u * 32 + lane;
+        const int r = q / m, c = q - r * m;
+        val[u] = (q < tot && c + 1 <= r && c + 2 < m) ? S->J[r * RR_LDF + c] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 24; ++u) {
+        const int q = q0 + u * 32 + lane;
+        const int r = q / m, c = q - r * m;
+        if (q < tot && c + 1 <= r && c + 2 < m) Jt[c * RR_LDF + r] = val[u];
+      }
+    }
   }
   __syncwarp();
   const float tn = S->tn;
@@ -513,27 +553,46 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
     hi = nhi;
   }
   const float lamj = 0.5f * (lo + hi);
+  // start vectors differ per index, so a cluster's vectors span the cluster's subspace
+  for (int i = lane; i < m; i += 32) v[i] = 1.0f + 0.25f * (float)(((i + 1) * (j + 3) * 7919) % 97) / 97.0f;
+  __syncwarp();
   if (lane == 0) {
     S->lam[j] = lamj;
-    // start vectors differ per index, so a cluster's vectors span the cluster's subspace
-    float b[RR_MMAX];
-    for (int i = 0; i < m; ++i) b[i] = 1.0f + 0.25f * (float)(((i + 1) * (j + 3) * 7919) % 97) / 97.0f;
-    tri_inverse_iteration(dd, ee, m, lamj, 4.0f * 6e-8f * tn + 1e-30f, 3, b);
-    for (int i = 0; i < m; ++i) v[i] = b[i];
+    tri_inverse_iteration(dd, ee, m, lamj, 4.0f * 6e-8f * tn + 1e-30f, 3, v, f, ri, u1, u2, sw);
   }
   __syncwarp();
-  for (int jj = m - 3; jj >= 0; --jj) {
-    const float beta = S->bet[jj];
-    if (beta == 0.0f) continue;
-    const int n1 = m - jj - 1;
-    const float* col = S->J + (jj + 1) * RR_LDF + jj;
-    float sum = 0.0f;
-    for (int r = lane; r < n1; r += 32) sum = fmaf(col[r * RR_LDF], v[jj + 1 + r], sum);
-    sum = beta * warp_sum(sum);
-    for (int r = lane; r < n1; r += 32) v[jj + 1 + r] = fmaf(-col[r * RR_LDF], sum, v[jj + 1 + r]);
-    __syncwarp();
+  // back-transformation by the reflectors (last first): the vector stays in registers
+  // (entry i in lane i % 32, slot i / 32) and the next reflector column is loaded ahead,
+  // so each reflector costs one FMA, one shuffle reduction and one FMA on the chain
+  float vr[3], cn[3];
+#pragma unroll
+  for (int s3 = 0; s3 < 3; ++s3) {
+    const int i = lane + 32 * s3;
+    vr[s3] = (i < m) ? v[i] : 0.0f;
+    cn[s3] = (m >= 3 && i > m - 3 && i < m) ? Jt[(m - 3) * RR_LDF + i] : 0.0f;
   }
-  for (int i = lane; i < m; i += 32) S->V[i * RR_LDF + j] = v[i];
+  for (int jj = m - 3; jj >= 0; --jj) {
+    float cj[3];
+#pragma unroll
+    for (int s3 = 0; s3 < 3; ++s3) {
+      cj[s3] = cn[s3];
+      const int i = lane + 32 * s3;
+      cn[s3] = (jj >= 1 && i > jj - 1 && i < m) ? Jt[(jj - 1) * RR_LDF + i] : 0.0f;
+    }
+    const float beta = bet[jj];
+    if (beta == 0.0f) continue;
+    float sum = 0.0f;
+#pragma unroll
+    for (int s3 = 0; s3 < 3; ++s3) sum = fmaf(cj[s3], vr[s3], sum);   // cj is 0 outside rows jj+1 .. m-1
+    sum = beta * warp_sum(sum);
+#pragma unroll
+    for (int s3 = 0; s3 < 3; ++s3) vr[s3] = fmaf(-cj[s3], sum, vr[s3]);
+  }
+#pragma unroll
+  for (int s3 = 0; s3 < 3; ++s3) {
+    const int i = lane + 32 * s3;
+    if (i < m) S->V[i * RR_LDF + j] = vr[s3];
+  }
 }
 
 // Part 3 (one CTA): Gram-Schmidt inside clusters (on the back-transformed vectors, which
@@ -609,17 +668,34 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   }
   __syncthreads();
   const float clus = 1e-3f * a.scr->tn;             // eigenvalues closer than this: a cluster
-  // 4d. orthonormalise within clusters (modified Gram-Schmidt), normalise the rest
+  // 4d. orthonormalise within clusters, normalise the rest: classical Gram-Schmidt applied
+  //     twice (orthogonal to working precision like the modified form); lane t forms the
+  //     whole dot product with column j + t of the cluster, so no shuffle reduction is on
+  //     the chain, and the projections are then removed row by row.  The coefficients go
+  //     to the warp's slice of J's region (free until step 7).
   for (int j = wid; j < m; j += RR_NW) {
     if (j > 0 && lam[j] - lam[j - 1] < clus) continue;   // not the first of its cluster
     int e = j + 1;
     while (e < m && lam[e] - lam[e - 1] < clus) ++e;
+    float* dsc = J + wid * RR_MMAX;
     for (int i = j; i < e; ++i) {
-      for (int l = j; l < i; ++l) {
-        float d = 0.0f;
-        for (int r = lane; r < m; r += 32) d = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d);
-        d = warp_sum(d);
-        for (int r = lane; r < m; r += 32) V[r * RR_LDF + i] = fmaf(-d, V[r * RR_LDF + l], V[r * RR_LDF + i]);
+      for (int pass = 0; pass < 2 && i > j; ++pass) {
+        for (int l = j + lane; l < i; l += 32) {
+          float d0 = 0.0f, d1 = 0.0f;
+          int r = 0;
+          for (; r + 1 < m; r += 2) {
+            d0 = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d0);
+            d1 = fmaf(V[(r + 1) * RR_LDF + l], V[(r + 1) * RR_LDF + i], d1);
+          }
+          if (r < m) d0 = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d0);
+          dsc[l - j] = d0 + d1;
+        }
+        __syncwarp();
+        for (int r = lane; r < m; r += 32) {
+          float x = V[r * RR_LDF + i];
+          for (int l = j; l < i; ++l) x = fmaf(-dsc[l - j], V[r * RR_LDF + l], x);
+          V[r * RR_LDF + i] = x;
+        }
         __syncwarp();
       }
       float n2 = 0.0f;
@@ -630,7 +706,6 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
       __syncwarp();
     }
   }
-  __syncthreads();
   __syncthreads();
 
   // ------------------------------------------ 5. the k smallest FP32 eigenpairs
