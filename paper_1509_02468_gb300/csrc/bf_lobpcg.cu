@@ -185,8 +185,13 @@ __global__ void k_project(T* V, int k, int64_t n, const LobState* st) {
 // pixels, then folded by TwoSum into (hi, lo) pairs; groups are combined by a tree of
 // TwoSums, and the block partial hi + lo is written in FP64.
 #define GRAM_T 512
-#define GRAM_PXC 64
-#define GRAM_BUF (GRAM_PXC * 96)  // one buffered chunk: GRAM_PXC pixels x m4 <= 96 columns
+// pixels per shared-memory chunk (two buffers of S and A S chunks, m4 <= 96 columns each):
+// 128 in FP32 (193 KB), 64 in FP64; longer chunks mean fewer CTA barriers per pixel
+template <typename T>
+struct GramChunk {
+  static constexpr int pxc = sizeof(T) == 4 ? 128 : 64;
+  static constexpr int buf = pxc * 96;
+};
 
 template <typename T>
 struct GramArgs {
@@ -198,6 +203,13 @@ struct GramArgs {
   double* partials;  // [gridDim.x][2][m][m] (upper tiles only)
   const LobState* st;
 };
+
+// p[i] for i < 3 by selects (a runtime index into a kernel-parameter array makes the
+// compiler copy the array to local memory)
+template <typename P>
+__device__ __forceinline__ P pick3(const P (&p)[3], int i) {
+  return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
+}
 
 __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
   const float s = hi + x;
@@ -212,6 +224,7 @@ template <typename T>
 __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
   if (a.st->status != LOB_RUN) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int PXC = GramChunk<T>::pxc, BUF = GramChunk<T>::buf;
   const int m = a.m, m4 = a.m4, k = a.k;
   const int ta_n = m4 / 4;
   const int nt = ta_n * (ta_n + 1) / 2;
@@ -226,39 +239,39 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
     ta = row;
     tb = row + t;
   }
-  T* sS = reinterpret_cast<T*>(smem);                 // [2][GRAM_BUF]: chunk of S, [GRAM_PXC][m4]
-  T* sA = sS + 2 * GRAM_BUF;                          // [2][GRAM_BUF]: chunk of A S
-  T* sb = sA + 2 * GRAM_BUF;                          // [2][GRAM_PXC]
+  T* sS = reinterpret_cast<T*>(smem);                 // [2][BUF]: chunk of S, [PXC][m4]
+  T* sA = sS + 2 * BUF;                          // [2][BUF]: chunk of A S
+  T* sb = sA + 2 * BUF;                          // [2][PXC]
   T cA[16], cB[16], hA[16], lA[16], hB[16], lB[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) cA[e] = cB[e] = hA[e] = lA[e] = hB[e] = lB[e] = T(0);
   int since_fold = 0;
   const int fold_every = 16;      // FP32 runs of 16 products (64 cost ~5e-7 in Ritz values on small images)
-  const int64_t nchunks = (a.n + GRAM_PXC - 1) / GRAM_PXC;
+  const int64_t nchunks = (a.n + PXC - 1) / PXC;
   const bool vec = (k % 4 == 0);
   // FP32 blocks with k % 4 == 0: the next chunk is copied into the second shared-memory
   // buffer by cp.async while the current one is processed (zero-filled past n and m).
   const bool pipe = vec && sizeof(T) == 4;
   const int q4 = m4 / 4;
   auto issue = [&](int64_t ch, int buf) {
-    const int64_t i0 = ch * GRAM_PXC;
-    T* dS = sS + (size_t)buf * GRAM_BUF;
-    T* dA = sA + (size_t)buf * GRAM_BUF;
-    T* db = sb + (size_t)buf * GRAM_PXC;
-    for (int q = threadIdx.x; q < GRAM_PXC * q4; q += GRAM_T) {
+    const int64_t i0 = ch * PXC;
+    T* dS = sS + (size_t)buf * BUF;
+    T* dA = sA + (size_t)buf * BUF;
+    T* db = sb + (size_t)buf * PXC;
+    for (int q = threadIdx.x; q < PXC * q4; q += GRAM_T) {
       const int p = q / q4, c4 = q - p * q4;
       const int64_t i = i0 + p;
       const int col = c4 * 4, blk = col / k, c = col - blk * k;
       const bool ok = i < a.n && col < m;
-      const T* gs = ok ? a.S[blk] + i * k + c : a.S[0];
-      const T* ga = ok ? a.AS[blk] + i * k + c : a.AS[0];
+      const T* gs = ok ? pick3(a.S, blk) + i * k + c : a.S[0];
+      const T* ga = ok ? pick3(a.AS, blk) + i * k + c : a.AS[0];
       const unsigned nb = ok ? 16u : 0u;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dS + p * m4 + col)),
                    "l"(gs), "r"(nb) : "memory");
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dA + p * m4 + col)),
                    "l"(ga), "r"(nb) : "memory");
     }
-    if (threadIdx.x < GRAM_PXC) {
+    if (threadIdx.x < PXC) {
       const int64_t i = i0 + threadIdx.x;
       if (a.b) {
         const bool ok = i < a.n;
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
   if (pipe && blockIdx.x < nchunks) issue(blockIdx.x, 0);
   int it_local = 0;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it_local) {
-    const int64_t i0 = ch * GRAM_PXC;
+    const int64_t i0 = ch * PXC;
     const int cur = pipe ? (it_local & 1) : 0;
     __syncthreads();                       // the previous chunk's readers are done
     if (pipe) {
@@ -286,14 +299,14 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
       __syncthreads();
     } else if (vec) {
       const int q4v = m4 / 4;
-      for (int q = threadIdx.x; q < GRAM_PXC * q4v; q += GRAM_T) {
+      for (int q = threadIdx.x; q < PXC * q4v; q += GRAM_T) {
         const int p = q / q4v, c4 = q - p * q4v;
         const int64_t i = i0 + p;
         const int col = c4 * 4, blk = col / k, c = col - blk * k;
         Vec<T, 4> vs, va;
         if (i < a.n && col < m) {
-          vs = *reinterpret_cast<const Vec<T, 4>*>(a.S[blk] + i * k + c);
-          va = *reinterpret_cast<const Vec<T, 4>*>(a.AS[blk] + i * k + c);
+          vs = *reinterpret_cast<const Vec<T, 4>*>(pick3(a.S, blk) + i * k + c);
+          va = *reinterpret_cast<const Vec<T, 4>*>(pick3(a.AS, blk) + i * k + c);
         } else {
           vs.v[0] = vs.v[1] = vs.v[2] = vs.v[3] = T(0);
           va = vs;
@@ -301,35 +314,35 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
         *reinterpret_cast<Vec<T, 4>*>(sS + p * m4 + col) = vs;
         *reinterpret_cast<Vec<T, 4>*>(sA + p * m4 + col) = va;
       }
-      for (int p = threadIdx.x; p < GRAM_PXC; p += GRAM_T) {
+      for (int p = threadIdx.x; p < PXC; p += GRAM_T) {
         const int64_t i = i0 + p;
         sb[p] = (i < a.n) ? (a.b ? a.b[i] : T(1)) : T(0);
       }
       __syncthreads();
     } else {
-      for (int q = threadIdx.x; q < GRAM_PXC * m4; q += GRAM_T) {
+      for (int q = threadIdx.x; q < PXC * m4; q += GRAM_T) {
         const int p = q / m4, col = q - p * m4;
         const int64_t i = i0 + p;
         T vs = T(0), va = T(0);
         if (i < a.n && col < m) {
           const int blk = col / k, c = col - blk * k;
-          vs = a.S[blk][i * k + c];
-          va = a.AS[blk][i * k + c];
+          vs = pick3(a.S, blk)[i * k + c];
+          va = pick3(a.AS, blk)[i * k + c];
         }
         sS[q] = vs;
         sA[q] = va;
       }
-      for (int p = threadIdx.x; p < GRAM_PXC; p += GRAM_T) {
+      for (int p = threadIdx.x; p < PXC; p += GRAM_T) {
         const int64_t i = i0 + p;
         sb[p] = (i < a.n) ? (a.b ? a.b[i] : T(1)) : T(0);
       }
       __syncthreads();
     }
-    const T* cS = sS + (size_t)cur * GRAM_BUF;
-    const T* cA_ = sA + (size_t)cur * GRAM_BUF;
-    const T* cb = sb + (size_t)cur * GRAM_PXC;
+    const T* cS = sS + (size_t)cur * BUF;
+    const T* cA_ = sA + (size_t)cur * BUF;
+    const T* cb = sb + (size_t)cur * PXC;
     if (act) {
-      for (int p = grp; p < GRAM_PXC; p += ng) {
+      for (int p = grp; p < PXC; p += ng) {
         const Vec<T, 4> xa = *reinterpret_cast<const Vec<T, 4>*>(cS + p * m4 + ta * 4);
         const Vec<T, 4> xb = *reinterpret_cast<const Vec<T, 4>*>(cS + p * m4 + tb * 4);
         const Vec<T, 4> yb = *reinterpret_cast<const Vec<T, 4>*>(cA_ + p * m4 + tb * 4);
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
 #pragma unroll
     for (int e = 0; e < CW; ++e) x[e] = xl[e] = pp[e] = T(0);
     for (int blk = 0; blk < a.nblk; ++blk) {
-      const T* row = a.S[blk] + i * k;
+      const T* row = pick3(a.S, blk) + i * k;
       for (int c0 = 0; c0 < k; c0 += CW) {
         Vec<T, CW> sv = *reinterpret_cast<const Vec<T, CW>*>(row + c0);
 #pragma unroll
@@ -718,7 +731,7 @@ static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
   const int nt = ta_n * (ta_n + 1) / 2;
   if (nt > GRAM_T) return bf_fail(BF_EINVAL, "lobpcg_filter: block too wide");
   const int ng = GRAM_T / nt;
-  size_t sm = (size_t)(4 * GRAM_BUF + 2 * GRAM_PXC) * sizeof(T);
+  size_t sm = (size_t)(4 * GramChunk<T>::buf + 2 * GramChunk<T>::pxc) * sizeof(T);
   sm = std::max(sm, (size_t)(ng / 2 + 1) * nt * 64 * sizeof(T));
   static bool init = false;
   if (!init) {
