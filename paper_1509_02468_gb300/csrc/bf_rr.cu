@@ -55,14 +55,14 @@ __device__ __forceinline__ double frsqrt(double x) {
 }
 
 // Number of eigenvalues of the symmetric tridiagonal T (diagonal d, squared off-diagonal
-// e2) smaller than x: sign changes along p_0 = 1, p_1 = d_0 - x,
-// p_i = (d_{i-1} - x) p_{i-1} - e2_{i-2} p_{i-2}.  A zero p_i counts as a sign change (as
-// if it were a tiny number of the opposite sign); the pair (p_{i-1}, p_i) is rescaled by a
-// power of two whenever p_i leaves [2^-60, 2^60].
-__device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
-  float p0 = 1.0f, p1 = d[0] - x;
-  if (p1 == 0.0f) p1 = -0x1p-40f;
-  int cnt = (p1 < 0.0f);
+// e2) smaller than x: negative pivots of the LDL^T factorisation of T - x I,
+// q_0 = d_0 - x, q_i = (d_i - x) - e2_{i-1} / q_{i-1} (the ratio form of the Sturm
+// sequence: no over- or underflow to rescale).  A pivot smaller than pivmin in magnitude
+// is replaced by -pivmin.
+__device__ int sturm_count_f(const float* d, const float* e2, int m, float x, float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = (q < 0.0f);
   float dn = (m > 1) ? d[1] : 0.0f, en = e2[0];   // operands of the next step, loaded ahead
   for (int i = 1; i < m; ++i) {
     const float di = dn, ei = en;
@@ -70,17 +70,9 @@ __device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
       dn = d[i + 1];
       en = e2[i];
     }
-    float p2 = (di - x) * p1 - ei * p0;
-    if (p2 == 0.0f) p2 = -p1 * 0x1p-40f;
-    cnt += ((p2 < 0.0f) != (p1 < 0.0f));
-    p0 = p1;
-    p1 = p2;
-    const float a = fabsf(p1);
-    if (a > 0x1p60f || a < 0x1p-60f) {
-      const float sc = scalbnf(1.0f, -ilogbf(p1));
-      p0 *= sc;
-      p1 *= sc;
-    }
+    q = (di - x) - __fdividef(ei, q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0f);
   }
   return cnt;
 }
@@ -424,11 +416,25 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
       __syncthreads();
       continue;
     }
-    for (int r = wid; r < n1; r += RR_NW) {           // p = beta A1 v
-      float s = 0.0f;
-      for (int c = lane; c < n1; c += 32) s = fmaf(A1[r * RR_LDF + c], col[c * RR_LDF], s);
-      s = warp_sum(s);
-      if (lane == 0) pv32[r] = beta * s;
+    // p = beta A1 v: a warp takes rows r, r + RR_NW, r + 2 RR_NW together, so that their
+    // shuffle reductions are independent and overlap
+    for (int r = wid; r < n1; r += 3 * RR_NW) {
+      const int r1 = r + RR_NW, r2 = r + 2 * RR_NW;
+      float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+      for (int c = lane; c < n1; c += 32) {
+        const float vc = col[c * RR_LDF];
+        s0 = fmaf(A1[r * RR_LDF + c], vc, s0);
+        if (r1 < n1) s1 = fmaf(A1[r1 * RR_LDF + c], vc, s1);
+        if (r2 < n1) s2 = fmaf(A1[r2 * RR_LDF + c], vc, s2);
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        pv32[r] = beta * s0;
+        if (r1 < n1) pv32[r1] = beta * s1;
+        if (r2 < n1) pv32[r2] = beta * s2;
+      }
     }
     __syncthreads();
     float K = 0.0f;
@@ -520,16 +526,16 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
   }
   {
     const int tot = m * m;
-    for (int q0 = 0; q0 < tot; q0 += 24 * 32) {
-      float val[24];
+    for (int q0 = 0; q0 < tot; q0 += 36 * 32) {      // m <= 48: two batches of loads
+      float val[36];
 #pragma unroll
-      for (int u = 0; u < 24; ++u) {
+      for (int u = 0; u < 36; ++u) {
         const int q = q0 + u * 32 + lane;
         const int r = q / m, c = q - r * m;
         val[u] = (q < tot && c + 1 <= r && c + 2 < m) ? S->J[r * RR_LDF + c] : 0.0f;
       }
 #pragma unroll
-      for (int u = 0; u < 24; ++u) {
+      for (int u = 0; u < 36; ++u) {
         const int q = q0 + u * 32 + lane;
         const int r = q / m, c = q - r * m;
         if (q < tot && c + 1 <= r && c + 2 < m) Jt[c * RR_LDF + r] = val[u];
@@ -542,10 +548,12 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
   lo -= 1e-6f * fabsf(lo) + 1e-30f;
   hi += 1e-6f * fabsf(hi) + 1e-30f;
   const float stop = 4.0f * 6e-8f * tn + 1e-30f;
+  // pivots below this are replaced: |e2 / pivmin| stays finite for |T| < 2^12
+  const float pivmin = 0x1p-100f * fmaxf(1.0f, tn * tn);
   for (int round = 0; round < 10 && hi - lo > stop; ++round) {
     const float w = (hi - lo) * (1.0f / 33.0f);
     const float x = lo + w * (float)(lane + 1);
-    const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f(dd, e2, m, x) > j);
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f(dd, e2, m, x, pivmin) > j);
     const int first = above ? __ffs(above) - 1 : 32;     // first point with more than j below
     const float nlo = (first == 0) ? lo : lo + w * (float)first;
     const float nhi = (first == 32) ? hi : lo + w * (float)(first + 1);
