@@ -485,9 +485,10 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
   for (int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x; q < total; q += (int64_t)gridDim.x * 256) {
     const int64_t i = q / ngrp;
     const int g = (int)(q - i * ngrp);
-    // X' is formed in double-float: each product exactly (TwoProd by fma) and the running
-    // sum with TwoSum, so X' is the rounding of S C (an FP32 running sum over 3k terms
-    // moved the Ritz values of small problems by ~1e-6)
+    // X' = X C_x + (W C_w + P C_p): the X-block part in double-float (each product exactly
+    // by TwoProd, the running sum by TwoSum; an FP32 running sum over all 3k terms moved
+    // the Ritz values of small problems by ~1e-6), the W and P terms, which carry the
+    // step's correction, by FMA into the low part
     T x[CW], xl[CW], pp[CW];
 #pragma unroll
     for (int e = 0; e < CW; ++e) x[e] = xl[e] = pp[e] = T(0);
@@ -499,14 +500,19 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
         for (int u = 0; u < CW; ++u) {
           const int r = blk * k + c0 + u;
           const Vec<T, CW> cv = *reinterpret_cast<const Vec<T, CW>*>(sC + r * k + g * CW);
+          if (blk == 0) {
 #pragma unroll
-          for (int e = 0; e < CW; ++e) {
-            const T pr = mul_rn(sv.v[u], cv.v[e]);      // not contracted into the add below
-            const T pe = fma(sv.v[u], cv.v[e], -pr);
-            const T t = x[e] + pr;
-            const T bp = t - x[e];
-            xl[e] += ((x[e] - (t - bp)) + (pr - bp)) + pe;
-            x[e] = t;
+            for (int e = 0; e < CW; ++e) {
+              const T pr = mul_rn(sv.v[u], cv.v[e]);    // not contracted into the add below
+              const T pe = fma(sv.v[u], cv.v[e], -pr);
+              const T t = x[e] + pr;
+              const T bp = t - x[e];
+              xl[e] += ((x[e] - (t - bp)) + (pr - bp)) + pe;
+              x[e] = t;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < CW; ++e) xl[e] = fma(sv.v[u], cv.v[e], xl[e]);
           }
           if (with_p) {
             const Vec<T, CW> pv = *reinterpret_cast<const Vec<T, CW>*>(sCp + r * k + g * CW);
