@@ -28,6 +28,16 @@ int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64
 
 namespace {
 
+int cg_num_sms() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
+  }
+  return nsm;
+}
+
 enum { CG_RUN = 0, CG_CONV = 1, CG_BREAK = 2, CG_NONFINITE = 3 };
 #define CG_POLL 64
 
@@ -304,29 +314,33 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_init_fast(const Geom<float> g
   float* sx = reinterpret_cast<float*>(smem);
   float* sg = sx + SH::hp;
   float* sval = sg + SH::hp;
-  const int bx = blockIdx.x * SH::tw, by = blockIdx.y * SH::th;
-  const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= g.nx && by - SH::ry >= 0 &&
-                      by + SH::th + SH::ry <= g.ny);
-  stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED, [&](int64_t gp) { return a.x0[gp]; });
-  __syncthreads();
+  const int ntx = (g.nx + SH::tw - 1) / SH::tw, ntiles = ntx * ((g.ny + SH::th - 1) / SH::th);
   const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
-  const int x = bx + lx, y = by + ly;
   const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
   float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (x < g.nx && y < g.ny) {
-    const int64_t i = (int64_t)y * g.nx + x;
-    float xi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
-    window_fast<SH, 1, STORED>(g, hp0, i, g.nx, sg, sval, mask,
-                               reinterpret_cast<const Vec<float, 1>*>(sx), a.wf, a.wmode, a.n, xi, acc, ws);
-    const float r = -acc[0];
-    const float sv = a.dinv ? r * a.dinv[i] : r;
-    a.x[i] = xi[0];
-    a.r[i] = r;
-    a.s[i] = sv;
-    v[0] = sv * r;
-    v[1] = sv * sv;
-    v[2] = r * r;
-    v[3] = xi[0] * xi[0];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {      // persistent over the tiles
+    const int bx = (t % ntx) * SH::tw, by = (t / ntx) * SH::th;
+    const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= g.nx && by - SH::ry >= 0 &&
+                        by + SH::th + SH::ry <= g.ny);
+    __syncthreads();                                          // the previous tile is read
+    stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED, [&](int64_t gp) { return a.x0[gp]; });
+    __syncthreads();
+    const int x = bx + lx, y = by + ly;
+    if (x < g.nx && y < g.ny) {
+      const int64_t i = (int64_t)y * g.nx + x;
+      float xi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+      window_fast<SH, 1, STORED>(g, hp0, i, g.nx, sg, sval, mask,
+                                 reinterpret_cast<const Vec<float, 1>*>(sx), a.wf, a.wmode, a.n, xi, acc, ws);
+      const float r = -acc[0];
+      const float sv = a.dinv ? r * a.dinv[i] : r;
+      a.x[i] = xi[0];
+      a.r[i] = r;
+      a.s[i] = sv;
+      v[0] += sv * r;
+      v[1] += sv * sv;
+      v[2] += r * r;
+      v[3] += xi[0] * xi[0];
+    }
   }
   double blk[4], tot[4];
   block_sum<4, float>(v, red, blk);
@@ -353,29 +367,35 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_dir_fast(const Geom<float> g,
   float* sx = reinterpret_cast<float*>(smem);
   float* sg = sx + SH::hp;
   float* sval = sg + SH::hp;
-  const int bx = blockIdx.x * SH::tw, by = blockIdx.y * SH::th;
-  const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= g.nx && by - SH::ry >= 0 &&
-                      by + SH::th + SH::ry <= g.ny);
   const float beta = (float)a.st->beta;
-  if (a.first)
-    stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED, [&](int64_t gp) { return a.s[gp]; });
-  else
-    stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED,
-                    [&](int64_t gp) { return fmaf(beta, a.p_old[gp], a.s[gp]); });
-  __syncthreads();
+  const int ntx = (g.nx + SH::tw - 1) / SH::tw, ntiles = ntx * ((g.ny + SH::th - 1) / SH::th);
   const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
-  const int x = bx + lx, y = by + ly;
   const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
   float v[1] = {0.0f};
-  if (x < g.nx && y < g.ny) {
-    const int64_t i = (int64_t)y * g.nx + x;
-    float pi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
-    window_fast<SH, 1, STORED>(g, hp0, i, g.nx, sg, sval, mask,
-                               reinterpret_cast<const Vec<float, 1>*>(sx), a.wf, a.wmode, a.n, pi, acc, ws);
-    const float q = fmaf(a.shift, pi[0], acc[0]);
-    a.p_new[i] = pi[0];
-    a.q[i] = q;
-    v[0] = pi[0] * q;
+  // persistent over the tiles: one block partial for the whole launch, so the grid
+  // reduction sums a few hundred partials instead of one per tile
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int bx = (t % ntx) * SH::tw, by = (t / ntx) * SH::th;
+    const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= g.nx && by - SH::ry >= 0 &&
+                        by + SH::th + SH::ry <= g.ny);
+    __syncthreads();                                          // the previous tile is read
+    if (a.first)
+      stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED, [&](int64_t gp) { return a.s[gp]; });
+    else
+      stage1_fast<SH>(g, bx, by, sx, sg, sval, a.guide, !STORED,
+                      [&](int64_t gp) { return fmaf(beta, a.p_old[gp], a.s[gp]); });
+    __syncthreads();
+    const int x = bx + lx, y = by + ly;
+    if (x < g.nx && y < g.ny) {
+      const int64_t i = (int64_t)y * g.nx + x;
+      float pi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+      window_fast<SH, 1, STORED>(g, hp0, i, g.nx, sg, sval, mask,
+                                 reinterpret_cast<const Vec<float, 1>*>(sx), a.wf, a.wmode, a.n, pi, acc, ws);
+      const float q = fmaf(a.shift, pi[0], acc[0]);
+      a.p_new[i] = pi[0];
+      a.q[i] = q;
+      v[0] += pi[0] * q;
+    }
   }
   double blk[1], tot[1];
   block_sum<1, float>(v, red, blk);
@@ -398,8 +418,9 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_dir_fast(const Geom<float> g,
 template <class SH, bool STORED>
 static void cg_launch_fast(bool init, dim3 tg, cudaStream_t s, const bf_graph* g, const CgArgs<float>& a) {
   const size_t sm = 3 * SH::hp * sizeof(float);
-  if (init) BF_LAUNCH(k_cg_init_fast<SH, STORED><<<tg, BF_THREADS, sm, s>>>(g->gf, a));
-  else BF_LAUNCH(k_cg_dir_fast<SH, STORED><<<tg, BF_THREADS, sm, s>>>(g->gf, a));
+  const unsigned grid = std::min<unsigned>(tg.x * tg.y, 8u * (unsigned)cg_num_sms());   // persistent, 8 per SM
+  if (init) BF_LAUNCH(k_cg_init_fast<SH, STORED><<<grid, BF_THREADS, sm, s>>>(g->gf, a));
+  else BF_LAUNCH(k_cg_dir_fast<SH, STORED><<<grid, BF_THREADS, sm, s>>>(g->gf, a));
 }
 
 template <class SH>
@@ -431,7 +452,7 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   const size_t vb = ((size_t)n * sizeof(T) + 255) & ~(size_t)255;
   const dim3 tg = tile_grid(g);
   const unsigned nb_tile = tg.x * tg.y;
-  const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 152 * 8);
+  const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms());
   const unsigned nbmax = std::max(nb_tile, nb_elem);
   const size_t pb = ((size_t)nbmax * 4 * sizeof(double) + 255) & ~(size_t)255;
   int rc = bf_ws_reserve(gm, BF_WS_CG, 5 * vb + pb + 256);
@@ -576,7 +597,7 @@ int cg_run_noalloc(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o
   const int64_t n = g->n;
   const dim3 tg = tile_grid(g);
   const unsigned nb_tile = tg.x * tg.y;
-  const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 152 * 8);
+  const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms());
   if (n > BF_NOALLOC_MAX_N)
     return bf_fail(BF_EINVAL, "cg_filter_noalloc: n exceeds the static scratch limit of 262144 samples");
   if (std::max(nb_tile, nb_elem) > BF_NOALLOC_MAX_BLOCKS)
