@@ -855,7 +855,8 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
       int need = 0;
       for (int q2 = tid; q2 < kp * kp; q2 += RR_T) {
         const int p = (int)fkp.div((unsigned)q2), q = q2 - p * kp;
-        if (p < q && fabs(H[p * RR_KLD + q]) > 1e-13 * (fabs(H[p * RR_KLD + p]) + fabs(H[q * RR_KLD + q])) + 1e-300)
+        if (p < q && fabsf((float)H[p * RR_KLD + q]) >
+                         1e-13f * (fabsf((float)H[p * RR_KLD + p]) + fabsf((float)H[q * RR_KLD + q])) + 1e-37f)
           need = 1;
       }
       if (__syncthreads_or(need) == 0) break;
@@ -869,9 +870,12 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
           qq[tid] = q;
           const double apq = H[p * RR_KLD + q], app = H[p * RR_KLD + p], aqq = H[q * RR_KLD + q];
           double c = 1.0, s = 0.0;
-          if (fabs(apq) > 1e-13 * (fabs(app) + fabs(aqq)) + 1e-300) {
+          // the significance test in FP32 (short chain; couplings below 1e-13 of the
+          // diagonal cannot move an eigenvalue beyond rounding)
+          const float apq32 = (float)apq;
+          if (fabsf(apq32) > 1e-13f * (fabsf((float)app) + fabsf((float)aqq)) + 1e-37f) {
             rot = 1;
-            const float tau = __fdividef((float)(aqq - app), 2.0f * (float)apq);
+            const float tau = __fdividef((float)(aqq - app), 2.0f * apq32);
             float t32;
             if (fabsf(tau) > 1e9f) {
               t32 = __fdividef(0.5f, tau);
@@ -879,8 +883,13 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
               const float u = fmaf(tau, tau, 1.0f);
               t32 = copysignf(__fdividef(1.0f, fabsf(tau) + u * rsqrtf(u)), tau);
             }
+            // c = (1 + t^2)^-1/2 from the FP32 seed and one Newton step (relative error
+            // ~2^-44: c^2 + s^2 = 1 to ~6e-14 per rotation, far below the FP32 blocks'
+            // rounding after the ~30 rotations of a call)
             const double t = (double)t32;
-            c = frsqrt(fma(t, t, 1.0));
+            const double x = fma(t, t, 1.0);
+            const double y0 = (double)rsqrtf((float)x);
+            c = y0 * fma(-0.5 * x, y0 * y0, 1.5);
             s = t * c;
           }
           csd[tid] = c;
