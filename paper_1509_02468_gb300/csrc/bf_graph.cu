@@ -810,7 +810,6 @@ extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out,
   fill_geom<double>(g->gd, *p, g->nx, g->ny, g->rx, g->ry, nfwd, fmap);
 
   const size_t nb = (size_t)g->n * esz;
-  int rc = BF_OK;
   int* dflag = nullptr;
   auto cleanup = [&](int code) {
     if (dflag) cudaFree(dflag);
@@ -850,7 +849,6 @@ extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out,
   if (hflag) return cleanup(bf_fail(BF_ENONFINITE, "bf_weights: guide holds NaN or Inf"));
   cudaFree(dflag);
   dflag = nullptr;
-  (void)rc;
   *out = g;
   return BF_OK;
 }

@@ -224,23 +224,11 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
   // lower triangle of order 96 in row-major order: entry (r, l), l <= r, packed r << 8 | l;
   // every smaller triangle is a prefix of it
   unsigned short* tri = reinterpret_cast<unsigned short*>(qq + RR_MMAX / 2);  // [4656]
-  // FP32 views of the RB region once R has been moved out of it (J, V: 37,248 B each):
-  // J holds float(M), then T and the reflectors; V the eigenvectors of M
+  // FP32 view of the RB region once R has been moved out of it (37,248 B): float(M),
+  // then T and the reflectors
   float* J = reinterpret_cast<float*>(RB);                // [96][RR_LDF]
-  float* V = J + RR_MMAX * RR_LDF;                        // [96][RR_LDF]
-  // after the FP32 sweeps: J's region holds R32 and CC, V's region the k x k work
-  float* R32 = J;                                         // [96][RR_KLD] FP32 residual
-  float* CC = J + RR_MMAX * RR_KLD;                       // [96][RR_KLD] correction coefficients
-  double* H = reinterpret_cast<double*>(V);               // [32][RR_KLD]
-  double* Vk = H + RR_KMAX * RR_KLD;                      // [32][RR_KLD]
-  double* Wk = Vk + RR_KMAX * RR_KLD;                     // [32][RR_KLD]
-  // k x k work of step 8 in the J region (R32 and CC are dead by then)
-  double* D64 = reinterpret_cast<double*>(J);             // [32][RR_KLD]
-  double* K64 = D64 + RR_KMAX * RR_KLD;                   // [32][RR_KLD]
-  float* E32 = reinterpret_cast<float*>(K64 + RR_KMAX * RR_KLD);  // [32][RR_KLD]
-  float* D32 = E32 + RR_KMAX * RR_KLD;                    // [32][RR_KLD]
   __shared__ int fail, dropped;
-  __shared__ float lmax, shK, shlo, shhi;
+  __shared__ float shlo, shhi;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int k = a.k;
@@ -479,7 +467,6 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
   __syncthreads();
   for (int i = tid; i < m; i += RR_T) e2f[i] = ee32[i] * ee32[i];
   __syncthreads();
-  (void)R32; (void)CC; (void)Wk; (void)D32;
   RRScratch* S = a.scr;
   for (int r = wid; r < m; r += RR_NW)
     for (int c = lane; c < m; c += 32) {
@@ -648,8 +635,8 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   double* K64 = D64 + RR_KMAX * RR_KLD;                   // [32][RR_KLD]
   float* E32 = reinterpret_cast<float*>(K64 + RR_KMAX * RR_KLD);  // [32][RR_KLD]
   float* D32 = E32 + RR_KMAX * RR_KLD;                    // [32][RR_KLD]
-  __shared__ int fail, dropped;
-  __shared__ float lmax, shK, shlo, shhi;
+  __shared__ int dropped;
+  __shared__ float lmax;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int k = a.k;

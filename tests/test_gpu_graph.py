@@ -220,3 +220,21 @@ def test_apply_l_spatial_only_weights():
     Xd = dev(X)
     Y = host(bf().bf_apply(G, "L", Xd))
     assert rel_l2(Y, O.apply("L", host(Xd))) < 1e-5
+
+
+@pytest.mark.parametrize("offset", [4, 2])
+def test_apply_l_strided_column_slice(offset):
+    """A 16-column slice of a 24-column block (leading dimension 24): at offset 4 the slice
+    is 16-byte aligned and takes the pipelined kernel, at offset 2 it is not and takes the
+    tile-per-CTA one; both against sampled rows of the definition, on an image with more
+    tiles than SMs."""
+    _, g = image_case(420, 390, 12)
+    G = bf().bf_weights(dev(g), 3, 2.0, 0.08)
+    big = np.random.default_rng(offset).standard_normal((g.size, 24)).astype(np.float32)
+    bigd = dev(big)
+    Xv = bigd[:, offset:offset + 16]
+    Y = host(bf().bf_apply(G, "L", Xv))
+    rows = np.concatenate([np.random.default_rng(5).integers(0, g.size, 120), [0, g.size - 1, 389, 419 * 390]])
+    ref = _l_rows_from_definition(g, big[:, offset:offset + 16], rows, 3, 2.0, 0.08)
+    for r, i in enumerate(rows):
+        assert rel_l2(Y[i], ref[r]) < 1e-5, (int(i), offset)
