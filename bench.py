@@ -152,6 +152,21 @@ def run_cpu(side, steps, warmup):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def job_rate(ms_local, units_local, world, dist=None, device="cpu"):
+    """Whole-job throughput of N replicas: the slowest rank's time per step (max over ranks)
+    and the units all ranks processed (sum), in millions per second.  Returns (ms, rate)."""
+    import torch
+    ms, units = float(ms_local), float(units_local)
+    if world > 1:
+        t = torch.tensor([ms, units], dtype=torch.float64, device=device)
+        m = t[:1].clone()
+        u = t[1:].clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(m.item()), float(u.item())
+    return ms, units / (ms * 1e-3) / 1e6
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -235,12 +250,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
     launches = (bf.launch_count() - launches0) / args.steps
     keep.clear()
-    ms = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * npix / (ms * 1e-3) / 1e6
+    ms, value = job_rate(sum(times) / len(times), npix, world, dist, "cuda")
 
     # ---- rooflines.  The operator (L X, k = 16, on-the-fly weights) on the step's image and
     # on a 2048 x 2048 image of the same generator (X and Y far larger than L2); the
