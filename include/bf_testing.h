@@ -1,6 +1,7 @@
 /*
- * bf_testing.h -- extra entry point of libbf.so that exposes one internal step of
- * lobpcg_filter for direct testing (see bf.h for the conventions).
+ * bf_testing.h -- extra entry points of libbf.so that expose internal steps of
+ * lobpcg_filter and its bounded device waits for direct testing (see bf.h for the
+ * conventions).
  */
 #ifndef BF_TESTING_H_
 #define BF_TESTING_H_
@@ -36,6 +37,15 @@ int bf_rayleigh_ritz(const double* G, int m, int k, int m_nop, double* C, double
 int bf_gram_tc_test(const float* S0, const float* S1, const float* S2, const float* AS0,
                     const float* AS1, const float* AS2, const float* b, int nblk, int k,
                     int64_t n, int split, double* G, void* stream);
+
+/* The bounded device wait used by the tensor-core Gram (an mbarrier wait that gives up
+ * after a number of polls, so that a kernel whose producer never signals returns an error
+ * instead of hanging), on a barrier of its own: one CTA of 32 threads waits for phase 0
+ * of an mbarrier with arrival count 1, polling at most iters times (1 <= iters <= 2^20).
+ * arrive != 0: thread 0 arrives first and the call returns BF_OK; arrive == 0: nothing
+ * arrives, every wait gives up and the call returns BF_ETIMEOUT, with the CUDA context
+ * intact.  Synchronises the stream. */
+int bf_wait_test(int iters, int arrive, void* stream);
 
 #ifdef __cplusplus
 }

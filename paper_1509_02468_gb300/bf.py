@@ -90,6 +90,7 @@ def _load():
         "bf_net_grad": [vp, vp, vp, vp],
         "bf_net_adam": [vp, ctypes.c_float, ctypes.c_float, vp],
         "bf_gram_tc_test": [vp, vp, vp, vp, vp, vp, vp, i32, i32, i64, i32, vp, vp],
+        "bf_wait_test": [i32, i32, vp],
         "bf_batch_create": [vp, i32, ctypes.POINTER(vp)],
         "bf_batch_free": [vp],
         "bf_batch_cg": [vp, vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, vp],
@@ -421,6 +422,12 @@ class Batch:
         t, v = ctypes.c_int64(), ctypes.c_int32()
         _check(_lib.bf_batch_tiles(self.handle, ctypes.byref(t), ctypes.byref(v)))
         return t.value, v.value
+
+
+def wait_test(iters: int, arrive: bool, stream=None):
+    """The library's bounded device wait on a barrier of its own (include/bf_testing.h):
+    returns normally when thread 0 arrives, raises BFError(BF_ETIMEOUT) when nothing does."""
+    _check(_lib.bf_wait_test(int(iters), int(bool(arrive)), _stream(stream)))
 
 
 def gram_tc(S_blocks, AS_blocks, b=None, split: bool = False, stream=None):

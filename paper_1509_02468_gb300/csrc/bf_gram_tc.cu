@@ -60,8 +60,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < TC_WAIT_ITERS; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int iters = TC_WAIT_ITERS) {
+  for (int i = 0; i < iters; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -304,7 +304,42 @@ __global__ void k_gram_tc_reduce(const float* partials, int nblocks, int m, doub
   else G[(size_t)m * m + (size_t)i * m + (j - m)] = s;
 }
 
+// The bounded mbarrier wait of k_gram_tc on a barrier of its own (arrival count 1): with
+// `arrive` thread 0 completes phase 0 and every thread's wait succeeds; without it nothing
+// arrives and every wait gives up after `iters` polls.  out = 0 or 4 (timeout).
+__global__ void k_wait_test(int iters, int arrive, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(&bar))
+                 : "memory");
+  const bool ok = mbar_wait(&bar, 0u, iters);
+  const bool all = __syncthreads_and(ok);
+  if (threadIdx.x == 0) *out = all ? 0 : 4;
+}
+
 }  // namespace
+
+extern "C" int bf_wait_test(int iters, int arrive, void* stream) {
+  if (iters < 1 || iters > (1 << 20)) return bf_fail(BF_EINVAL, "bf_wait_test: need 1 <= iters <= 2^20");
+  int* out = nullptr;
+  BF_CUDA(cudaMalloc(&out, sizeof(int)));
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = -1;
+  k_wait_test<<<1, 32, 0, s>>>(iters, arrive, out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, out, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(out);
+  if (e != cudaSuccess) return bf_cuda_fail(e, "bf_wait_test");
+  bf_count_launches(1);
+  if (h == 4) return bf_fail(BF_ETIMEOUT, "bf_wait_test: the bounded wait gave up");
+  return h == 0 ? BF_OK : bf_fail(BF_ECUDA, "bf_wait_test: no result");
+}
 
 // Launch the tensor-core Gram: returns BF_EINVAL for shapes it does not cover (k not a
 // multiple of 4, m > 96), so the caller can use the FP32 kernel instead.

@@ -52,3 +52,19 @@ def test_lobpcg_with_tensor_core_gram(gram):
     # to a nearby trajectory (its Gram carries ~4e-3 relative errors)
     assert err <= (10 * TOL_RITZ if gram == "bf16x3" else 0.2), err
     assert out["info"].status in ("ran", "converged")
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """The bounded mbarrier wait of the tensor-core kernels: with nothing arriving it gives
+    up after its poll limit and the call reports BF_ETIMEOUT; the context still runs work."""
+    bf().wait_test(64, arrive=True)
+    with pytest.raises(bf().BFError) as ei:
+        bf().wait_test(256, arrive=False)
+    assert ei.value.code == -5                      # BF_ETIMEOUT
+    _, g = image_case(40, 45, 3)
+    G, O = make_pair(g, 3, 2.0, 0.08)
+    X = np.random.default_rng(1).standard_normal((g.size, 4))
+    Xd = dev(X)
+    Y = host(bf().bf_apply(G, "L", Xd))
+    assert np.linalg.norm(Y - O.apply("L", host(Xd))) <= 1e-5 * np.linalg.norm(O.apply("L", host(Xd)))
+    bf().wait_test(64, arrive=True)
