@@ -214,16 +214,26 @@ def run_gpu(args):
     x_cg = torch.empty(npix, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
 
+    # the two filters read the same graph and run concurrently: LOBPCG on a high-priority
+    # stream, CG at normal priority, so that the block scheduler gives the SMs to LOBPCG's
+    # data-parallel kernels first and CG fills those its one-CTA Rayleigh-Ritz leaves free
     side = torch.cuda.Stream()
+    lob = torch.cuda.Stream(priority=-1)
+
+    # one graph for the image size; every step recomputes its weights for the step's image
+    # (bf_graph_update: the work of bf_weights into the graph's own buffers)
+    Gs = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
 
     def step():
-        # the two filters read the same graph and run concurrently: CG on a side stream,
-        # LOBPCG (whose one-CTA Rayleigh-Ritz leaves most SMs free) on the main stream
-        G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
+        G = bf.graph_update(Gs, guide)
         side.wait_stream(stream)
+        lob.wait_stream(stream)
+        # LOBPCG (the longer filter) is enqueued first so its first kernels do not wait
+        # behind the host's enqueueing of the CG launches
+        out = bf.lobpcg_filter(G, X0, w["lob_iters"], want_X=False, sync=False, stream=lob)
         bf.cg_filter(G, guide.view(-1), w["cg_iters"], out=x_cg, sync=False, stream=side)
-        out = bf.lobpcg_filter(G, X0, w["lob_iters"], want_X=False, sync=False)
         stream.wait_stream(side)
+        stream.wait_stream(lob)
         return G, out
 
     keep = []
@@ -285,11 +295,13 @@ def run_gpu(args):
     def e2e_step():
         gd = gh.cuda(non_blocking=True)
         Xd = X0p.cuda(non_blocking=True)
-        G = bf.bf_weights(gd, w["radius"], w["sigma_s"], w["sigma_r"])
+        G = bf.graph_update(Gs, gd)
         side.wait_stream(stream)
+        lob.wait_stream(stream)
+        out = bf.lobpcg_filter(G, Xd, w["lob_iters"], want_X=False, sync=False, stream=lob)
         xc, _, _ = bf.cg_filter(G, gd.view(-1), w["cg_iters"], sync=False, stream=side)
-        out = bf.lobpcg_filter(G, Xd, w["lob_iters"], want_X=False, sync=False)
         stream.wait_stream(side)
+        stream.wait_stream(lob)
         xcg_h.copy_(xc, non_blocking=True)
         y_h.copy_(out["y"], non_blocking=True)
         th_h.copy_(out["theta"], non_blocking=True)

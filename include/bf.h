@@ -131,6 +131,14 @@ typedef struct bf_lobpcg_opts {
  * Synchronises `stream` (it reports BF_ENONFINITE if the guide holds NaN or Inf). */
 int bf_weights(const bf_params* params, const void* guide, bf_graph** out, void* stream);
 
+/* Recompute a graph for a new guide of the same shape and dtype (device, n elements):
+ * the same work as bf_weights (Eq. 2 weights, degree, scalings) into the graph's own
+ * buffers, so no device memory is allocated and the filters' workspaces are kept (for a
+ * stream of images of one size).  The guide is copied.  Synchronises `stream`; returns
+ * BF_ENONFINITE if the guide holds NaN or Inf (the graph's values are then undefined
+ * until the next successful update).  Must not overlap filter calls on the same graph. */
+int bf_graph_update(bf_graph* g, const void* guide, void* stream);
+
 /* Release a graph and everything it owns (NULL is allowed). */
 int bf_graph_free(bf_graph* g);
 

@@ -69,6 +69,7 @@ def _load():
     sig = {
         "bf_weights": [ctypes.POINTER(bf_params), vp, ctypes.POINTER(vp), vp],
         "bf_graph_free": [vp],
+        "bf_graph_update": [vp, vp, vp],
         "bf_graph_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
                           ctypes.POINTER(ctypes.c_int32)],
         "bf_graph_degree": [vp, vp, vp],
@@ -196,6 +197,18 @@ def bf_weights(guide: torch.Tensor, radius: int, sigma_s: float, sigma_r: float,
     h = ctypes.c_void_p()
     _check(_lib.bf_weights(ctypes.byref(p), _ptr(guide), ctypes.byref(h), _stream(stream)))
     return Graph(h, p, (ny, nx), guide.dtype, guide.device)
+
+
+def graph_update(g: Graph, guide: torch.Tensor, stream=None) -> Graph:
+    """Recompute g for a new guide of the same shape and dtype (bf_graph_update): the same
+    work as bf_weights into the graph's own buffers, no device allocation."""
+    if not guide.is_cuda or guide.dtype != g.dtype or guide.device != g.device:
+        raise ValueError("guide must be a CUDA tensor of the graph's dtype and device")
+    guide = guide.contiguous()
+    if tuple(guide.shape) != (tuple(g.shape) if guide.dim() == 2 else (g.n,)):
+        raise ValueError("guide must have the graph's shape")
+    _check(_lib.bf_graph_update(g.handle, _ptr(guide), _stream(stream)))
+    return g
 
 
 def graph_degree(g: Graph, stream=None) -> torch.Tensor:

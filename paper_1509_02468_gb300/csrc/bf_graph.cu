@@ -763,6 +763,8 @@ static void fill_geom(Geom<T>& G, const bf_params& p, int nx, int ny, int rx, in
     }
 }
 
+static int compute_weights(bf_graph* g, const void* guide, cudaStream_t s);
+
 extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out, void* stream) {
   if (!p || !guide || !out) return bf_fail(BF_EINVAL, "bf_weights: NULL argument");
   *out = nullptr;
@@ -810,9 +812,7 @@ extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out,
   fill_geom<double>(g->gd, *p, g->nx, g->ny, g->rx, g->ry, nfwd, fmap);
 
   const size_t nb = (size_t)g->n * esz;
-  int* dflag = nullptr;
   auto cleanup = [&](int code) {
-    if (dflag) cudaFree(dflag);
     bf_graph_free(g);
     return code;
   };
@@ -828,34 +828,48 @@ extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out,
     const size_t wb = (size_t)nfwd * g->n * (p->weight_mode == BF_W_STORED_BF16 ? 2 : 4);
     if ((e = cudaMalloc(&g->wf, wb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(weights)"));
   }
-  if ((e = cudaMalloc(&dflag, sizeof(int))) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(flag)"));
-  if ((e = cudaMemsetAsync(dflag, 0, sizeof(int), s)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "memset"));
-  if ((e = cudaMemcpyAsync(g->guide, guide, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-    return cleanup(bf_cuda_fail(e, "cudaMemcpyAsync(guide)"));
-  const unsigned blocks = (unsigned)((g->n + BF_THREADS - 1) / BF_THREADS);
-  if (esz == 4)
-    BF_LAUNCH(k_weights<float><<<blocks, BF_THREADS, 0, s>>>(g->gf, (const float*)g->guide, g->n, (float*)g->d,
-                                                   (float*)g->dinv, (float*)g->dis, (float*)g->dls,
-                                                   g->wf, p->weight_mode, dflag));
-  else
-    BF_LAUNCH(k_weights<double><<<blocks, BF_THREADS, 0, s>>>(g->gd, (const double*)g->guide, g->n, (double*)g->d,
-                                                    (double*)g->dinv, (double*)g->dis, (double*)g->dls,
-                                                    g->wf, p->weight_mode, dflag));
-  if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(bf_cuda_fail(e, "k_weights launch"));
-  int hflag = 0;
-  if ((e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cleanup(bf_cuda_fail(e, "cudaMemcpyAsync(flag)"));
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "bf_weights sync"));
-  if (hflag) return cleanup(bf_fail(BF_ENONFINITE, "bf_weights: guide holds NaN or Inf"));
-  cudaFree(dflag);
-  dflag = nullptr;
+  if ((e = cudaMalloc(&g->flag, sizeof(int))) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(flag)"));
+  const int rc = compute_weights(g, guide, s);
+  if (rc) return cleanup(rc);
   *out = g;
   return BF_OK;
 }
 
+// Copy the guide into the graph and compute the degree, the scalings and (stored modes)
+// the weights; synchronises s to report a non-finite guide.
+static int compute_weights(bf_graph* g, const void* guide, cudaStream_t s) {
+  const size_t nb = (size_t)g->n * g->esize;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(g->flag, 0, sizeof(int), s)) != cudaSuccess) return bf_cuda_fail(e, "memset(flag)");
+  if ((e = cudaMemcpyAsync(g->guide, guide, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return bf_cuda_fail(e, "cudaMemcpyAsync(guide)");
+  const unsigned blocks = (unsigned)((g->n + BF_THREADS - 1) / BF_THREADS);
+  if (g->esize == 4)
+    BF_LAUNCH(k_weights<float><<<blocks, BF_THREADS, 0, s>>>(g->gf, (const float*)g->guide, g->n, (float*)g->d,
+                                                   (float*)g->dinv, (float*)g->dis, (float*)g->dls,
+                                                   g->wf, g->p.weight_mode, g->flag));
+  else
+    BF_LAUNCH(k_weights<double><<<blocks, BF_THREADS, 0, s>>>(g->gd, (const double*)g->guide, g->n, (double*)g->d,
+                                                    (double*)g->dinv, (double*)g->dis, (double*)g->dls,
+                                                    g->wf, g->p.weight_mode, g->flag));
+  if ((e = cudaGetLastError()) != cudaSuccess) return bf_cuda_fail(e, "k_weights launch");
+  int hflag = 0;
+  if ((e = cudaMemcpyAsync(&hflag, g->flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return bf_cuda_fail(e, "cudaMemcpyAsync(flag)");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bf_cuda_fail(e, "weights sync");
+  if (hflag) return bf_fail(BF_ENONFINITE, "bf_weights: guide holds NaN or Inf");
+  return BF_OK;
+}
+
+extern "C" int bf_graph_update(bf_graph* g, const void* guide, void* stream) {
+  if (!g || !guide) return bf_fail(BF_EINVAL, "bf_graph_update: NULL argument");
+  if ((uintptr_t)guide % g->esize) return bf_fail(BF_EINVAL, "bf_graph_update: misaligned guide");
+  return compute_weights(g, guide, (cudaStream_t)stream);
+}
+
 extern "C" int bf_graph_free(bf_graph* g) {
   if (!g) return BF_OK;
-  void* bufs[] = {g->guide, g->d, g->dinv, g->dis, g->dls, g->wf, g->ws[0], g->ws[1], g->ws[2]};
+  void* bufs[] = {g->guide, g->d, g->dinv, g->dis, g->dls, g->wf, g->ws[0], g->ws[1], g->ws[2], g->flag};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete g;

@@ -75,6 +75,7 @@ struct bf_graph {
   Geom<double> gd;
   void* ws[3];           // grow-only workspaces, one per filter family (BF_WS_*)
   size_t ws_bytes[3];
+  int* flag;             // [1] non-finite guide flag of the weights kernel
 };
 
 // Workspace slots: CG and LOBPCG keep their own, so one call of each may run at the same

@@ -238,3 +238,45 @@ def test_apply_l_strided_column_slice(offset):
     ref = _l_rows_from_definition(g, big[:, offset:offset + 16], rows, 3, 2.0, 0.08)
     for r, i in enumerate(rows):
         assert rel_l2(Y[i], ref[r]) < 1e-5, (int(i), offset)
+
+
+@pytest.mark.parametrize("mode", ["onthefly", "stored_bf16"])
+def test_graph_update_equals_a_new_graph(mode):
+    """bf_graph_update recomputes a graph in place for a new guide of the same shape: the
+    operators, the degree and both filters give exactly what a newly built graph gives,
+    also after the filters' workspaces were created on the old guide."""
+    from paper_1509_02468_gb300 import synth
+    _, g1 = image_case(45, 70, 4)
+    _, g2 = image_case(45, 70, 9)
+    G = bf().bf_weights(dev(g1), 3, 2.0, 0.08, weight_mode=mode)
+    bf().cg_filter(G, dev(g1.reshape(-1)), 5)
+    X0 = dev(synth.block_start(g2.reshape(-1), 4, 9))
+    bf().lobpcg_filter(G, X0, 3)
+    bf().graph_update(G, dev(g2))
+    H = bf().bf_weights(dev(g2), 3, 2.0, 0.08, weight_mode=mode)
+    X = dev(np.random.default_rng(2).standard_normal((g2.size, 16)))
+    for op in OPS:
+        assert torch.equal(bf().bf_apply(G, op, X), bf().bf_apply(H, op, X)), op
+    assert torch.equal(bf().graph_degree(G), bf().graph_degree(H))
+    xa = bf().cg_filter(G, dev(g2.reshape(-1)), 7)[0]
+    xb = bf().cg_filter(H, dev(g2.reshape(-1)), 7)[0]
+    assert torch.equal(xa, xb)
+    la, lb = bf().lobpcg_filter(G, X0, 4), bf().lobpcg_filter(H, X0, 4)
+    assert torch.equal(la["theta"], lb["theta"]) and torch.equal(la["y"], lb["y"])
+
+
+def test_graph_update_rejects_and_reports():
+    _, g = image_case(30, 40, 2)
+    G = bf().bf_weights(dev(g), 3, 2.0, 0.08)
+    with pytest.raises(ValueError):
+        bf().graph_update(G, dev(g[:, :39]))                         # wrong shape
+    with pytest.raises(ValueError):
+        bf().graph_update(G, dev(g, torch.float64))                  # wrong dtype
+    bad = g.copy()
+    bad[3, 5] = np.nan
+    with pytest.raises(bf().BFError) as ei:
+        bf().graph_update(G, dev(bad))
+    assert ei.value.code == bf().BF_ENONFINITE
+    bf().graph_update(G, dev(g))                                     # a valid guide recovers it
+    H = bf().bf_weights(dev(g), 3, 2.0, 0.08)
+    assert torch.equal(bf().graph_degree(G), bf().graph_degree(H))
