@@ -42,6 +42,7 @@ struct BInst {
   float* q;
   float* p[2];
   int job0, njobs;        // range in the class work list (per tile shape)
+  int upd0, nupd;         // range in the class update list (chunks of BUPD_CHUNK samples)
   unsigned counter;
   BState st;
 };
@@ -60,16 +61,17 @@ struct BArgs {
   int beta_mode;
 };
 
-// Last block of an instance: sums the instance's partials (job0 .. job0 + njobs) in order.
+// Last block of an instance: sums the instance's partials (j0 .. j0 + nj of the launch's
+// list) in order.
 template <int NV>
 __device__ __forceinline__ bool inst_sum_last(const double (&blk)[NV], const BArgs& a, BInst& in, int job,
-                                              double (&tot)[NV], int* is_last) {
+                                              double (&tot)[NV], int* is_last, int j0, int nj) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) a.partials[(size_t)job * 4 + j] = blk[j];
     __threadfence();
     const unsigned prev = atomicAdd(&in.counter, 1u);
-    *is_last = (prev == (unsigned)in.njobs - 1);
+    *is_last = (prev == (unsigned)nj - 1);
   }
   __syncthreads();
   if (!*is_last) return false;
@@ -77,9 +79,9 @@ __device__ __forceinline__ bool inst_sum_last(const double (&blk)[NV], const BAr
   double v[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) v[j] = 0.0;
-  for (int q = threadIdx.x; q < in.njobs; q += BF_THREADS) {
+  for (int q = threadIdx.x; q < nj; q += BF_THREADS) {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] += ((volatile double*)a.partials)[(size_t)(in.job0 + q) * 4 + j];
+    for (int j = 0; j < NV; ++j) v[j] += ((volatile double*)a.partials)[(size_t)(j0 + q) * 4 + j];
   }
   __shared__ double red2[NV * (BF_THREADS / 32)];
   block_sum<NV, double>(v, red2, tot);
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_init(const Geom<float> g, co
   }
   double blk[4], tot[4];
   block_sum<4, float>(v, red, blk);
-  if (inst_sum_last<4>(blk, a, in, job, tot, &last)) {
+  if (inst_sum_last<4>(blk, a, in, job, tot, &last, in.job0, in.njobs)) {
     BState& st = in.st;
     st.sr = tot[0];
     st.ss = tot[1];
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_dir(const Geom<float> g, con
   }
   double blk[1], tot[1];
   block_sum<1, float>(v, red, blk);
-  if (inst_sum_last<1>(blk, a, in, job, tot, &last)) {
+  if (inst_sum_last<1>(blk, a, in, job, tot, &last, in.job0, in.njobs)) {
     BState& st = in.st;
     st.pq = tot[0];
     if (st.sr == 0.0) st.status = B_CONV;
@@ -209,6 +211,7 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_dir(const Geom<float> g, con
 // x += alpha p, r -= alpha q, s = T r on the tile; sums; beta and the stopping tests.
 template <class SH>
 __global__ void __launch_bounds__(BF_THREADS) k_bcg_update(const BArgs a) {
+  // one block per chunk of up to BUPD_CHUNK consecutive samples of one instance
   const int job = blockIdx.x;
   const BJob jb = a.jobs[job];
   BInst& in = a.inst[jb.inst];
@@ -217,25 +220,23 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_update(const BArgs a) {
   __shared__ int last;
   const float alpha = (float)in.st.alpha;
   const float* p = in.p[(in.st.iter + 1) & 1];
-  const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
-  const int x = jb.bx + lx, y = jb.by + ly;
+  const int64_t i0 = jb.bx, i1 = i0 + jb.by;
   float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (x < in.nx && y < in.ny) {
-    const int64_t i = (int64_t)y * in.nx + x;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += BF_THREADS) {
     const float pi = p[i], q = in.q[i];
     in.x[i] = fmaf(alpha, pi, in.x[i]);
     const float r = fmaf(-alpha, q, in.r[i]);
     const float sv = in.dinv ? r * in.dinv[i] : r;
     in.r[i] = r;
     in.s[i] = sv;
-    v[0] = sv * r;
-    v[1] = sv * q;
-    v[2] = sv * sv;
-    v[3] = r * r;
+    v[0] += sv * r;
+    v[1] += sv * q;
+    v[2] += sv * sv;
+    v[3] += r * r;
   }
   double blk[4], tot[4];
   block_sum<4, float>(v, red, blk);
-  if (inst_sum_last<4>(blk, a, in, job, tot, &last)) {
+  if (inst_sum_last<4>(blk, a, in, job, tot, &last, in.upd0, in.nupd)) {
     BState& st = in.st;
     st.iter += 1;
     const double den = (a.beta_mode == BF_BETA_PRINTED) ? st.ss : st.sr;
@@ -253,6 +254,7 @@ typedef WinShapeT<3, 3, false, 32, 8> R3_32x8;
 typedef WinShapeT<3, 3, false, 64, 4> R3_64x4;
 typedef WinShapeT<3, 3, false, 16, 16> R3_16x16;
 enum { CLS_R3 = 0, CLS_R5 = 1, CLS_X1 = 2, NCLS = 3 };
+#define BUPD_CHUNK 4096           // samples per block of the update kernel (16 per thread)
 const int R3_TW[3] = {32, 64, 16}, R3_TH[3] = {8, 4, 16};
 
 }  // namespace
@@ -266,8 +268,10 @@ struct bf_batch {
   bool has[NCLS];
   int r3_variant;                    // tile shape of the image class (autotuned)
   int njobs[NCLS];
+  int nupd[NCLS];                    // update chunks per class
   BInst* d_inst;                     // [count]
   BJob* d_jobs[NCLS];
+  BJob* d_upd[NCLS];                 // update chunks {instance, first sample, count}
   double* d_part[NCLS];
   void* d_vec;                       // r, s, q, p0, p1 of every instance
   std::vector<BInst> h_inst;
@@ -285,7 +289,7 @@ template <class SH>
 size_t bsmem() { return 3 * SH::hp * sizeof(float); }
 
 int build_jobs(bf_batch* b) {
-  std::vector<BJob> jobs[NCLS];
+  std::vector<BJob> jobs[NCLS], upd[NCLS];
   for (int c = 0; c < NCLS; ++c) jobs[c].clear();
   for (int i = 0; i < b->count; ++i) {
     const int c = b->cls[i];
@@ -296,17 +300,27 @@ int build_jobs(bf_batch* b) {
     for (int by = 0; by < in.ny; by += th)
       for (int bx = 0; bx < in.nx; bx += tw) jobs[c].push_back(BJob{i, bx, by});
     in.njobs = (int)jobs[c].size() - in.job0;
+    in.upd0 = (int)upd[c].size();
+    for (int64_t i0 = 0; i0 < in.n; i0 += BUPD_CHUNK)
+      upd[c].push_back(BJob{i, (int)i0, (int)std::min<int64_t>(BUPD_CHUNK, in.n - i0)});
+    in.nupd = (int)upd[c].size() - in.upd0;
   }
   for (int c = 0; c < NCLS; ++c) {
     if (b->d_jobs[c]) cudaFree(b->d_jobs[c]);
+    if (b->d_upd[c]) cudaFree(b->d_upd[c]);
     if (b->d_part[c]) cudaFree(b->d_part[c]);
     b->d_jobs[c] = nullptr;
+    b->d_upd[c] = nullptr;
     b->d_part[c] = nullptr;
     b->njobs[c] = (int)jobs[c].size();
+    b->nupd[c] = (int)upd[c].size();
     if (jobs[c].empty()) continue;
+    const size_t np = std::max(jobs[c].size(), upd[c].size());
     BF_CUDA(cudaMalloc(&b->d_jobs[c], jobs[c].size() * sizeof(BJob)));
-    BF_CUDA(cudaMalloc(&b->d_part[c], jobs[c].size() * 4 * sizeof(double)));
+    BF_CUDA(cudaMalloc(&b->d_upd[c], upd[c].size() * sizeof(BJob)));
+    BF_CUDA(cudaMalloc(&b->d_part[c], np * 4 * sizeof(double)));
     BF_CUDA(cudaMemcpy(b->d_jobs[c], jobs[c].data(), jobs[c].size() * sizeof(BJob), cudaMemcpyHostToDevice));
+    BF_CUDA(cudaMemcpy(b->d_upd[c], upd[c].data(), upd[c].size() * sizeof(BJob), cudaMemcpyHostToDevice));
   }
   return BF_OK;
 }
@@ -328,7 +342,11 @@ void launch_phase(int phase, const bf_batch* b, int c, const BArgs& a, cudaStrea
   if (!nj) return;
   if (phase == 0) BF_LAUNCH(k_bcg_init<SH><<<nj, BF_THREADS, bsmem<SH>(), s>>>(b->geom[c], a));
   else if (phase == 1) BF_LAUNCH(k_bcg_dir<SH><<<nj, BF_THREADS, bsmem<SH>(), s>>>(b->geom[c], a));
-  else BF_LAUNCH(k_bcg_update<SH><<<nj, BF_THREADS, 0, s>>>(a));
+  else {
+    BArgs au = a;
+    au.jobs = b->d_upd[c];
+    BF_LAUNCH(k_bcg_update<SH><<<(unsigned)b->nupd[c], BF_THREADS, 0, s>>>(au));
+  }
 }
 
 void launch_all(int phase, const bf_batch* b, const bf_cg_opts& o, int r3v, cudaStream_t s) {
@@ -381,8 +399,10 @@ extern "C" int bf_batch_create(const bf_graph* const* graphs, int count, bf_batc
   for (int c = 0; c < NCLS; ++c) {
     b->has[c] = false;
     b->d_jobs[c] = nullptr;
+    b->d_upd[c] = nullptr;
     b->d_part[c] = nullptr;
     b->njobs[c] = 0;
+    b->nupd[c] = 0;
   }
   cudaGetDevice(&b->device);
   size_t vtot = 0;
@@ -451,6 +471,7 @@ extern "C" int bf_batch_free(bf_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (int c = 0; c < NCLS; ++c) {
     if (b->d_jobs[c]) cudaFree(b->d_jobs[c]);
+    if (b->d_upd[c]) cudaFree(b->d_upd[c]);
     if (b->d_part[c]) cudaFree(b->d_part[c]);
   }
   if (b->d_inst) cudaFree(b->d_inst);
