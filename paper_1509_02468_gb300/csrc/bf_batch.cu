@@ -49,7 +49,8 @@ struct BInst {
 
 struct BJob {
   int inst;
-  int bx, by;
+  int bx, by;             // operator jobs: first tile; update jobs: first sample, count
+  int nt;                 // operator jobs: tiles in the group (consecutive along x)
 };
 
 struct BArgs {
@@ -119,28 +120,32 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_init(const Geom<float> g, co
   const int job = blockIdx.x;
   const BJob jb = a.jobs[job];
   BInst& in = a.inst[jb.inst];
-  const bool mask = !(jb.bx - SH::rx >= 0 && jb.bx + SH::tw + SH::rx <= in.nx && jb.by - SH::ry >= 0 &&
-                      jb.by + SH::th + SH::ry <= in.ny);
-  bstage<SH>(in, jb.bx, jb.by, sx, sg, sval, [&](int64_t gp) { return in.x0[gp]; });
-  __syncthreads();
   const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
-  const int x = jb.bx + lx, y = jb.by + ly;
   const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
   float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (x < in.nx && y < in.ny) {
-    const int64_t i = (int64_t)y * in.nx + x;
-    float xi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
-    window_fast<SH, 1, false>(g, hp0, i, in.nx, sg, sval, mask, reinterpret_cast<const Vec<float, 1>*>(sx),
-                              nullptr, BF_W_ONTHEFLY, in.n, xi, acc, ws);
-    const float r = -acc[0];
-    const float sv = in.dinv ? r * in.dinv[i] : r;
-    in.x[i] = xi[0];
-    in.r[i] = r;
-    in.s[i] = sv;
-    v[0] = sv * r;
-    v[1] = sv * sv;
-    v[2] = r * r;
-    v[3] = xi[0] * xi[0];
+  for (int t = 0; t < jb.nt; ++t) {                 // the group's tiles, one after another
+    const int bx = jb.bx + t * SH::tw;
+    const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= in.nx && jb.by - SH::ry >= 0 &&
+                        jb.by + SH::th + SH::ry <= in.ny);
+    if (t) __syncthreads();                         // the previous tile is read
+    bstage<SH>(in, bx, jb.by, sx, sg, sval, [&](int64_t gp) { return in.x0[gp]; });
+    __syncthreads();
+    const int x = bx + lx, y = jb.by + ly;
+    if (x < in.nx && y < in.ny) {
+      const int64_t i = (int64_t)y * in.nx + x;
+      float xi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+      window_fast<SH, 1, false>(g, hp0, i, in.nx, sg, sval, mask, reinterpret_cast<const Vec<float, 1>*>(sx),
+                                nullptr, BF_W_ONTHEFLY, in.n, xi, acc, ws);
+      const float r = -acc[0];
+      const float sv = in.dinv ? r * in.dinv[i] : r;
+      in.x[i] = xi[0];
+      in.r[i] = r;
+      in.s[i] = sv;
+      v[0] += sv * r;
+      v[1] += sv * sv;
+      v[2] += r * r;
+      v[3] += xi[0] * xi[0];
+    }
   }
   double blk[4], tot[4];
   block_sum<4, float>(v, red, blk);
@@ -174,27 +179,31 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_dir(const Geom<float> g, con
   const int it = in.st.iter;
   const float* p_old = in.p[it & 1];
   float* p_new = in.p[(it + 1) & 1];
-  const bool mask = !(jb.bx - SH::rx >= 0 && jb.bx + SH::tw + SH::rx <= in.nx && jb.by - SH::ry >= 0 &&
-                      jb.by + SH::th + SH::ry <= in.ny);
   const float beta = (float)in.st.beta;
-  if (it == 0)
-    bstage<SH>(in, jb.bx, jb.by, sx, sg, sval, [&](int64_t gp) { return in.s[gp]; });
-  else
-    bstage<SH>(in, jb.bx, jb.by, sx, sg, sval, [&](int64_t gp) { return fmaf(beta, p_old[gp], in.s[gp]); });
-  __syncthreads();
   const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
-  const int x = jb.bx + lx, y = jb.by + ly;
   const int hp0 = (ly + SH::ry) * SH::hw + (lx + SH::rx);
   float v[1] = {0.0f};
-  if (x < in.nx && y < in.ny) {
-    const int64_t i = (int64_t)y * in.nx + x;
-    float pi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
-    window_fast<SH, 1, false>(g, hp0, i, in.nx, sg, sval, mask, reinterpret_cast<const Vec<float, 1>*>(sx),
-                              nullptr, BF_W_ONTHEFLY, in.n, pi, acc, ws);
-    const float q = fmaf(a.shift, pi[0], acc[0]);
-    p_new[i] = pi[0];
-    in.q[i] = q;
-    v[0] = pi[0] * q;
+  for (int t = 0; t < jb.nt; ++t) {                 // the group's tiles, one after another
+    const int bx = jb.bx + t * SH::tw;
+    const bool mask = !(bx - SH::rx >= 0 && bx + SH::tw + SH::rx <= in.nx && jb.by - SH::ry >= 0 &&
+                        jb.by + SH::th + SH::ry <= in.ny);
+    if (t) __syncthreads();                         // the previous tile is read
+    if (it == 0)
+      bstage<SH>(in, bx, jb.by, sx, sg, sval, [&](int64_t gp) { return in.s[gp]; });
+    else
+      bstage<SH>(in, bx, jb.by, sx, sg, sval, [&](int64_t gp) { return fmaf(beta, p_old[gp], in.s[gp]); });
+    __syncthreads();
+    const int x = bx + lx, y = jb.by + ly;
+    if (x < in.nx && y < in.ny) {
+      const int64_t i = (int64_t)y * in.nx + x;
+      float pi[1] = {sx[hp0]}, acc[1] = {0.0f}, ws = 0.0f;
+      window_fast<SH, 1, false>(g, hp0, i, in.nx, sg, sval, mask, reinterpret_cast<const Vec<float, 1>*>(sx),
+                                nullptr, BF_W_ONTHEFLY, in.n, pi, acc, ws);
+      const float q = fmaf(a.shift, pi[0], acc[0]);
+      p_new[i] = pi[0];
+      in.q[i] = q;
+      v[0] += pi[0] * q;
+    }
   }
   double blk[1], tot[1];
   block_sum<1, float>(v, red, blk);
@@ -255,6 +264,7 @@ typedef WinShapeT<3, 3, false, 64, 4> R3_64x4;
 typedef WinShapeT<3, 3, false, 16, 16> R3_16x16;
 enum { CLS_R3 = 0, CLS_R5 = 1, CLS_X1 = 2, NCLS = 3 };
 #define BUPD_CHUNK 4096           // samples per block of the update kernel (16 per thread)
+#define BTILE_GROUP 8             // consecutive tiles of one row per block of the operator kernels
 const int R3_TW[3] = {32, 64, 16}, R3_TH[3] = {8, 4, 16};
 
 }  // namespace
@@ -267,7 +277,8 @@ struct bf_batch {
   Geom<float> geom[NCLS];
   bool has[NCLS];
   int r3_variant;                    // tile shape of the image class (autotuned)
-  int njobs[NCLS];
+  int njobs[NCLS];                   // operator jobs (groups of tiles) per class
+  int64_t ntiles[NCLS];              // operator tiles per class
   int nupd[NCLS];                    // update chunks per class
   BInst* d_inst;                     // [count]
   BJob* d_jobs[NCLS];
@@ -290,7 +301,7 @@ size_t bsmem() { return 3 * SH::hp * sizeof(float); }
 
 int build_jobs(bf_batch* b) {
   std::vector<BJob> jobs[NCLS], upd[NCLS];
-  for (int c = 0; c < NCLS; ++c) jobs[c].clear();
+  for (int c = 0; c < NCLS; ++c) b->ntiles[c] = 0;
   for (int i = 0; i < b->count; ++i) {
     const int c = b->cls[i];
     const int tw = (c == CLS_R3) ? R3_TW[b->r3_variant] : (c == CLS_R5 ? ShapeR5::tw : ShapeX1::tw);
@@ -298,11 +309,15 @@ int build_jobs(bf_batch* b) {
     BInst& in = b->h_inst[i];
     in.job0 = (int)jobs[c].size();
     for (int by = 0; by < in.ny; by += th)
-      for (int bx = 0; bx < in.nx; bx += tw) jobs[c].push_back(BJob{i, bx, by});
+      for (int bx = 0; bx < in.nx; bx += BTILE_GROUP * tw) {
+        const int nt = std::min(BTILE_GROUP, (in.nx - bx + tw - 1) / tw);
+        jobs[c].push_back(BJob{i, bx, by, nt});
+        b->ntiles[c] += nt;
+      }
     in.njobs = (int)jobs[c].size() - in.job0;
     in.upd0 = (int)upd[c].size();
     for (int64_t i0 = 0; i0 < in.n; i0 += BUPD_CHUNK)
-      upd[c].push_back(BJob{i, (int)i0, (int)std::min<int64_t>(BUPD_CHUNK, in.n - i0)});
+      upd[c].push_back(BJob{i, (int)i0, (int)std::min<int64_t>(BUPD_CHUNK, in.n - i0), 0});
     in.nupd = (int)upd[c].size() - in.upd0;
   }
   for (int c = 0; c < NCLS; ++c) {
@@ -402,6 +417,7 @@ extern "C" int bf_batch_create(const bf_graph* const* graphs, int count, bf_batc
     b->d_upd[c] = nullptr;
     b->d_part[c] = nullptr;
     b->njobs[c] = 0;
+    b->ntiles[c] = 0;
     b->nupd[c] = 0;
   }
   cudaGetDevice(&b->device);
@@ -482,7 +498,7 @@ extern "C" int bf_batch_free(bf_batch* b) {
 
 extern "C" int bf_batch_tiles(const bf_batch* b, int64_t* tiles_out, int* variant_out) {
   if (!b) return bf_fail(BF_EINVAL, "bf_batch_tiles: NULL batch");
-  if (tiles_out) *tiles_out = (int64_t)b->njobs[0] + b->njobs[1] + b->njobs[2];
+  if (tiles_out) *tiles_out = b->ntiles[0] + b->ntiles[1] + b->ntiles[2];
   if (variant_out) *variant_out = b->r3_variant;
   return BF_OK;
 }
