@@ -543,9 +543,7 @@ __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T*
                                                const T* __restrict__ tinv, T* __restrict__ Wn,
                                                double* __restrict__ partials, const LobState* st) {
   if (st->status != LOB_RUN) return;
-  __shared__ double sums[3 * LOB_KMAX];
-  for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) sums[q] = 0.0;
-  __syncthreads();
+  __shared__ T sred[3][256];                  // the threads' sums (blockDim.x = 256)
   const int lanes = blockDim.x / k;
   const int pl = threadIdx.x / k, c = threadIdx.x - pl * k;
   T r2 = T(0), bx2 = T(0), bw = T(0);
@@ -564,29 +562,21 @@ __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T*
       bw = fma(bi, w, bw);
     }
   }
-  // lanes that share a column (lane = c mod k when k divides 32) are summed by shuffles
-  // before one shared-memory add per column and warp
-  const int lane = threadIdx.x & 31;
-  if ((32 % k) == 0) {
-    for (int o = 16; o >= k; o >>= 1) {
-      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-      bx2 += __shfl_xor_sync(0xffffffffu, bx2, o);
-      bw += __shfl_xor_sync(0xffffffffu, bw, o);
-    }
-    if (lane < k && pl < lanes) {
-      atomicAdd(&sums[c], (double)r2);
-      atomicAdd(&sums[k + c], (double)bx2);
-      atomicAdd(&sums[2 * k + c], (double)bw);
-    }
-  } else if (pl < lanes) {
-    atomicAdd(&sums[c], (double)r2);
-    atomicAdd(&sums[k + c], (double)bx2);
-    atomicAdd(&sums[2 * k + c], (double)bw);
-  }
   // block partials only, summed by the next kernels (a kernel boundary instead of a fence,
-  // an arrival counter and a last block, which cost more than the pass itself)
+  // an arrival counter and a last block, which cost more than the pass itself); inside
+  // the block the threads' sums go through shared memory and are added in FP64 in a
+  // fixed order (no shared-memory FP64 atomics)
+  const bool own = pl < lanes;
+  sred[0][threadIdx.x] = own ? r2 : T(0);
+  sred[1][threadIdx.x] = own ? bx2 : T(0);
+  sred[2][threadIdx.x] = own ? bw : T(0);
   __syncthreads();
-  for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) partials[(size_t)blockIdx.x * 3 * k + q] = sums[q];
+  for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) {
+    const int which = q / k, cc = q - which * k;
+    double t = 0.0;
+    for (int p = 0; p < lanes; ++p) t += (double)sred[which][p * k + cc];
+    partials[(size_t)blockIdx.x * 3 * k + q] = t;
+  }
 }
 
 // Column sums of k_resid's block partials: block j sums value j over all blocks (each
