@@ -369,7 +369,7 @@ FP32_LANES_PER_SM = 128
 # an ncu launch list of the timed step
 RR_FP64_FMA = (2 * 48 ** 3 / 3 + 48 ** 3 / 6 + 2 * 48 * 48 * 16 + 3 * 48 * 16 * 16
                + 48 * 48 * 16 / 2 + 48 * 48 * 16 + 2 * 48 * 16 * 16)
-RR_SHARE = 0.469
+RR_SHARE = 0.467
 
 
 def _sm_max_ghz():
@@ -549,7 +549,7 @@ def main():
         return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
