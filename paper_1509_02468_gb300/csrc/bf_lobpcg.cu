@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bf_internal.cuh"
 #include "bf_rr.cuh"
@@ -209,6 +210,34 @@ struct GramArgs {
 template <typename P>
 __device__ __forceinline__ P pick3(const P (&p)[3], int i) {
   return i == 0 ? p[0] : (i == 1 ? p[1] : p[2]);
+}
+
+// Two FP32 lanes in one 64-bit register (f32x2 arithmetic, round to nearest per lane).
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
 }
 
 __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
@@ -466,6 +495,110 @@ struct UpdArgs {
 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// FP32 update for a block width KT known at compile time: one pixel per thread, all KT
+// columns, so that every coefficient load is the same address across the warp (a shared-
+// memory broadcast); persistent, the coefficients staged once per CTA.  The arithmetic is
+// that of k_update (double-float X-block part, FMA for the W and P terms) on packed column
+// pairs, entry by entry in the same order, so the result is the same bit for bit.
+template <int KT>
+__global__ void __launch_bounds__(256, 2) k_update_f32(const UpdArgs<float> a) {
+  if (a.st->status != LOB_RUN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NV = KT / 4, NP = KT / 2;
+  const int m = a.m;
+  const bool with_p = a.Pn != nullptr;
+  float* sC = reinterpret_cast<float*>(smem);     // [m][KT]
+  float* sCp = sC + m * KT;                       // [m][KT]
+  for (int q = threadIdx.x; q < m * KT; q += 256) {
+    sC[q] = (float)a.C[q];
+    sCp[q] = with_p ? (float)a.Cp[q] : 0.0f;
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * 256) {
+    // the pixel's row of block blk + 1 is loaded while block blk is processed
+    Vec<float, 4> sv[NV], sn[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) sv[c] = *reinterpret_cast<const Vec<float, 4>*>(a.S[0] + i * KT + 4 * c);
+    f2_t x2[NP], xl2[NP], pp2[NP];
+#pragma unroll
+    for (int h = 0; h < NP; ++h) x2[h] = xl2[h] = pp2[h] = 0ull;
+#pragma unroll
+    for (int blk = 0; blk < 3; ++blk) {
+      if (blk >= a.nblk) break;
+      if (blk + 1 < a.nblk) {
+        const float* row = pick3(a.S, blk + 1) + i * KT;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) sn[c] = *reinterpret_cast<const Vec<float, 4>*>(row + 4 * c);
+      }
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float sx = sv[c].v[u];
+          const int r = blk * KT + 4 * c + u;
+          const ulonglong2* cr = reinterpret_cast<const ulonglong2*>(sC + r * KT);
+          const f2_t s2 = f2(sx, sx);
+          if (blk == 0) {
+            const f2_t ns2 = f2(-sx, -sx);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+              const ulonglong2 cv = cr[q];
+#pragma unroll
+              for (int l = 0; l < 2; ++l) {
+                const int h = 2 * q + l;
+                const f2_t c2 = l ? cv.y : cv.x;
+                const f2_t pr = f2_mul(s2, c2);
+                const f2_t pen = f2_fma(ns2, c2, pr);
+                const f2_t t = f2_add(x2[h], pr);
+                const f2_t bp = f2_sub(t, x2[h]);
+                const f2_t lo = f2_add(f2_sub(x2[h], f2_sub(t, bp)), f2_sub(pr, bp));
+                xl2[h] = f2_add(xl2[h], f2_sub(lo, pen));
+                x2[h] = t;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+              const ulonglong2 cv = cr[q];
+              xl2[2 * q] = f2_fma(s2, cv.x, xl2[2 * q]);
+              xl2[2 * q + 1] = f2_fma(s2, cv.y, xl2[2 * q + 1]);
+            }
+          }
+          if (with_p) {
+            const ulonglong2* pr = reinterpret_cast<const ulonglong2*>(sCp + r * KT);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+              const ulonglong2 pv = pr[q];
+              pp2[2 * q] = f2_fma(s2, pv.x, pp2[2 * q]);
+              pp2[2 * q + 1] = f2_fma(s2, pv.y, pp2[2 * q + 1]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NV; ++c) sv[c] = sn[c];
+    }
+    ulonglong2* xo = reinterpret_cast<ulonglong2*>(a.Xn + i * KT);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      ulonglong2 o;
+      o.x = f2_add(x2[2 * q], xl2[2 * q]);
+      o.y = f2_add(x2[2 * q + 1], xl2[2 * q + 1]);
+      xo[q] = o;
+    }
+    if (with_p) {
+      ulonglong2* po = reinterpret_cast<ulonglong2*>(a.Pn + i * KT);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        ulonglong2 o;
+        o.x = pp2[2 * q];
+        o.y = pp2[2 * q + 1];
+        po[q] = o;
+      }
+    }
+  }
+}
 
 template <typename T, int CW>
 __global__ void __launch_bounds__(256) k_update(const UpdArgs<T> a) {
@@ -758,8 +891,30 @@ static void launch_update_cw(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
   BF_LAUNCH(k_update<T, CW><<<grid, 256, sm, s>>>(ua));
 }
 
+template <int KT>
+static void launch_update_f32(const UpdArgs<float>& ua, cudaStream_t s) {
+  const size_t sm = (size_t)(2 * ua.m * KT) * sizeof(float);
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(k_update_f32<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_f32<KT>, 256, 2 * 3 * KT * KT * sizeof(float)) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const int grid = (int)std::min<int64_t>((ua.n + 255) / 256, (int64_t)per_sm * sm_count());
+  BF_LAUNCH(k_update_f32<KT><<<grid, 256, sm, s>>>(ua));
+}
+
 template <typename T>
 static int run_update(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (ua.k == 16 || ua.k == 8) {
+      if (ua.k == 16) launch_update_f32<16>(ua, s);
+      else launch_update_f32<8>(ua, s);
+      BF_CUDA(cudaGetLastError());
+      return BF_OK;
+    }
+  }
   if (ua.k % 4 == 0) launch_update_cw<T, 4>(ua, grid, s);
   else launch_update_cw<T, 1>(ua, grid, s);
   BF_CUDA(cudaGetLastError());
