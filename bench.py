@@ -369,7 +369,7 @@ FP32_LANES_PER_SM = 128
 # an ncu launch list of the timed step
 RR_FP64_FMA = (2 * 48 ** 3 / 3 + 48 ** 3 / 6 + 2 * 48 * 48 * 16 + 3 * 48 * 16 * 16
                + 48 * 48 * 16 / 2 + 48 * 48 * 16 + 2 * 48 * 16 * 16)
-RR_SHARE = 0.467
+RR_SHARE = 0.476
 
 
 def _sm_max_ghz():
