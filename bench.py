@@ -323,6 +323,8 @@ def run_gpu(args):
 
     # ---- batching: the 256-instance workload, batched (one CUDA graph) against plain
     batched = None if args.no_batch else _run_batched(bf, torch, stream)
+    # ---- the nonlinear (re-guided) BF iteration of Section 2
+    reguided = None if args.no_batch else _run_reguided(bf, torch, stream, flush, peak)
 
     # ---- CPU baseline: the oracle on one full step (rank 0, N = 1 only)
     cpu = None
@@ -346,7 +348,7 @@ def run_gpu(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_2048": roofline_2048,
                 "roofline_dominant": roofline_rr, "cpu_baseline": cpu,
-                "batched": batched,
+                "batched": batched, "reguided": reguided,
                 "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "clocks": clk.summary(), "gpu_launches": launches}
@@ -445,6 +447,68 @@ def _time_rr(bf, torch, stream, flush, m=48, k=16, reps=20):
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+# algorithmic bytes per pixel of one re-guided BF step: the iterate copied in as the guide
+# (read 4, write 4), Eq. 2 degree and scalings (read the guide 4, write d, 1/d, d^-1/2 and
+# the diag-L scaling 16), one step D^-1 W x at k = 1 (read x 4, guide 4, 1/d 4, write 4)
+REGUIDED_BYTES_PER_PX = 8 + 20 + 16
+# the step is bound by its Eq. 2 exponentials, one per (pixel, neighbour) pair of the 7 x 7
+# window, against the SFU's nominal 16 ex2 per clock per SM
+REGUIDED_EXPS_PER_PX = 48
+SFU_EX2_PER_SM_CLK = 16
+
+
+def _run_reguided(bf, torch, stream, flush, peak, iters=10, reps=5):
+    """The nonlinear BF iteration of Section 2 (weights rebuilt from every iterate;
+    bf_reguided_filter), iters steps on the step's 512 x 512 image and on the 2048 x 2048
+    image, inputs resident, L2 flushed before every timed run; the FP64 oracle timed on
+    one step of a 128 x 128 image (scaled per pixel)."""
+    import numpy as np
+
+    from paper_1509_02468_gb300 import synth
+    out = {"workload": f"nonlinear BF, {iters} steps re-guided by the iterate, 7x7, "
+                       "sigma_s 2, sigma_r 0.08, FP32 on-the-fly weights", "iters": iters}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sfu_peak = nsm * SFU_EX2_PER_SM_CLK * _sm_max_ghz() * 1e9 / 1e12
+    for side, seed in ((512, 2), (2048, 3)):
+        _, noisy = synth.polygon_image(side, side, seed)
+        x = torch.as_tensor(noisy).cuda()
+        G = bf.bf_weights(x, 3, 2.0, 0.08)
+        xv = x.reshape(-1)
+        y = torch.empty_like(xv)
+        bf.reguided_filter(G, xv, iters, out=y, stream=stream)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            bf.reguided_filter(G, xv, iters, out=y, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = sum(ts) / len(ts)
+        npx = side * side
+        gbs = REGUIDED_BYTES_PER_PX * npx * iters / (ms * 1e-3) / 1e9
+        exps = REGUIDED_EXPS_PER_PX * npx * iters / (ms * 1e-3) / 1e12
+        out[f"{side}x{side}"] = {"ms": ms, "us_per_step": 1e3 * ms / iters,
+                                 "mpix_steps_per_s": npx * iters / (ms * 1e-3) / 1e6,
+                                 "sfu": {"achieved": exps, "peak": sfu_peak, "unit": "T exp/s",
+                                         "frac": exps / sfu_peak, "peak_source": "nominal",
+                                         "exps_per_px_step": REGUIDED_EXPS_PER_PX},
+                                 "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s",
+                                         "frac": gbs / peak,
+                                         "bytes_per_px_step": REGUIDED_BYTES_PER_PX}}
+        G.free()
+    from oracle import solvers
+    _, small = synth.polygon_image(128, 128, 2)
+    t0 = time.perf_counter()
+    solvers.reguided_iteration(small.astype(np.float64), small.shape, 3, 2.0, 0.08, 1)
+    t = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": 128 * 128 / t / 1e6, "unit": "Mpix-steps/s", "cores": 1,
+                           "kind": "oracle", "sample": "one step on a 128x128 image"}
+    return out
 
 
 def _batch_inputs(seed=4):
@@ -553,7 +617,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-CG measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-CG and re-guided measurements")
     ap.add_argument("--case", choices=["apply", "cg", "lobpcg"], default=None,
                     help="only launch one kernel family (for profiler captures)")
     ap.add_argument("--case-side", type=int, default=0, help="image side for --case")

@@ -168,6 +168,17 @@ int bf_apply(const bf_graph* g, int op, const void* X, int64_t ldx, int k, void*
 int bf_simple_filter(const bf_graph* g, const void* x0, int iters, void* x_out,
                      void* stream);
 
+/* iters steps of the nonlinear bilateral filter (Section 2, the first way of iterating
+ * it): each step takes the current iterate as the guide of Eq. 2 and applies one step,
+ * x_{t+1} = D(x_t)^-1 W(x_t) x_t.  g gives the shape, window, sigmas, dtype and weight
+ * mode; its weights, degree and scalings are overwritten: after the call (iters > 0) it
+ * is the graph of the guide x_{iters-1}.  x0 and x_out hold n elements of g's dtype
+ * (device, element-aligned) and may be the same array; iters = 0 copies.  Uses g's
+ * simple-iteration workspace (two n-vectors).  Errors: BF_EINVAL for NULL or misaligned
+ * arguments or iters < 0, BF_ENONFINITE if an iterate held NaN or Inf (read after the
+ * last step, which synchronises the stream). */
+int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* x_out, void* stream);
+
 /* ---- Krylov filters --------------------------------------------------------------- */
 
 /* Algorithm 2 (Section 5): kmax iterations of preconditioned CG for A x = b, A = L +

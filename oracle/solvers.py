@@ -3,6 +3,8 @@
 Test infrastructure only (see ``oracle/__init__``).
 
 * ``simple_iteration`` -- x_{k+1} = D^-1 W x_k = x_k - D^-1 L x_k (Section 4, Eq. 3).
+* ``reguided_iteration`` -- the nonlinear iteration of Section 2: the weights are rebuilt
+                          from each iterate, x_{k+1} = D(x_k)^-1 W(x_k) x_k.
 * ``cg``               -- Algorithm 2: preconditioned CG for L x = 0 started at x0, with the
                           flexible beta of Section 5; optionally the shifted system
                           (L + sigma I) x = sigma x0 (a Tikhonov graph filter) and a
@@ -41,6 +43,8 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
+from .graph import Graph
+
 DEP_TOL = 1e-10
 
 
@@ -49,6 +53,19 @@ def simple_iteration(G, x0, iters: int):
     """iters BF steps with fixed weights: x <- D^-1 W x (Eq. 3)."""
     x = np.asarray(x0, dtype=np.float64).copy()
     for _ in range(iters):
+        x = G.DINV_W @ x
+    return x
+
+
+def reguided_iteration(x0, shape, radius: int, sigma_s: float, sigma_r: float, iters: int,
+                       window: str = "square"):
+    """iters BF steps that change the weights every step (Section 2, the first of the two
+    ways to iterate the filter): the graph of Eq. 2 is built from the current iterate as
+    guide, then one step x <- D(x)^-1 W(x) x is taken.  A nonlinear filter: no fixed
+    Laplacian describes the whole cascade."""
+    x = np.asarray(x0, dtype=np.float64).reshape(-1).copy()
+    for _ in range(iters):
+        G = Graph(x, shape, radius, sigma_s, sigma_r, window=window)
         x = G.DINV_W @ x
     return x
 

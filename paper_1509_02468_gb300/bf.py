@@ -76,6 +76,7 @@ def _load():
         "bf_graph_export_weights": [vp, vp, vp],
         "bf_apply": [vp, i32, vp, i64, i32, vp, i64, dp, vp],
         "bf_simple_filter": [vp, vp, i32, vp, vp],
+        "bf_reguided_filter": [vp, vp, i32, vp, vp],
         "cg_filter": [vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, ctypes.POINTER(bf_info), vp],
         "lobpcg_filter": [vp, vp, i64, i32, i32, ctypes.POINTER(bf_lobpcg_opts), vp, dp, dp, vp,
                           ctypes.POINTER(bf_info), vp],
@@ -247,6 +248,16 @@ def bf_apply(g: Graph, op: str, X: torch.Tensor, Y: torch.Tensor | None = None,
 def bf_simple_filter(g: Graph, x0: torch.Tensor, iters: int, out=None, stream=None):
     out = torch.empty_like(x0) if out is None else out
     _check(_lib.bf_simple_filter(g.handle, _ptr(x0), iters, _ptr(out), _stream(stream)))
+    return out
+
+
+def reguided_filter(g: Graph, x0: torch.Tensor, iters: int, out=None, stream=None):
+    """iters steps of the nonlinear BF iteration (bf_reguided_filter): each step guides
+    Eq. 2 by the current iterate.  g is overwritten with the graph of the last guide."""
+    if not x0.is_cuda or x0.dtype != g.dtype or x0.numel() != g.n or not x0.is_contiguous():
+        raise ValueError("x0 must be a contiguous CUDA tensor of the graph's dtype and size")
+    out = torch.empty_like(x0) if out is None else out
+    _check(_lib.bf_reguided_filter(g.handle, _ptr(x0), iters, _ptr(out), _stream(stream)))
     return out
 
 

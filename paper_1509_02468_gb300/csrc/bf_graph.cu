@@ -230,7 +230,9 @@ __global__ void __launch_bounds__(BF_THREADS) k_apply(const Geom<T> g, const App
   }
 }
 
-// Laplacian-type operators (L, NSYM, NDIAGL) of float graphs with a specialised window.
+// Laplacian-type operators (L, NSYM, NDIAGL) and the BF step D^-1 W of float graphs with a
+// specialised window; the step in difference form, y_i = x_i - sum_j w_ij (x_i - x_j) / d_i
+// with d_i = 1 + sum_{j != i} w_ij (Eqs. 1, 3).
 template <class SH, int K, bool STORED>
 __global__ void __launch_bounds__(BF_THREADS) k_apply_fast(const Geom<float> g, const ApplyArgs<float> a) {
   constexpr int V = VecW<float, K>::value;
@@ -262,8 +264,14 @@ __global__ void __launch_bounds__(BF_THREADS) k_apply_fast(const Geom<float> g, 
   if (active) {
     window_fast<SH, K, STORED>(g, hp0, i, g.nx, sg, sval, mask, sx, a.wf, a.wmode, a.n, xi, acc, wsum);
     const float s_i = a.scale ? a.scale[i] : 1.0f;
+    if (a.op == BF_OP_DINV_W) {
+      const float di = 1.0f / (1.0f + wsum);
 #pragma unroll
-    for (int c = 0; c < K; ++c) yv[c] = a.scale ? s_i * acc[c] : acc[c];
+      for (int c = 0; c < K; ++c) yv[c] = fmaf(-acc[c], di, xi[c]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < K; ++c) yv[c] = a.scale ? s_i * acc[c] : acc[c];
+    }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       Vec<float, V> o;
@@ -632,8 +640,8 @@ static int apply_fast_shape(const bf_graph* g, int K, const ApplyArgs<float>& a,
 }
 
 static int try_apply_fast(const bf_graph* g, int K, const ApplyArgs<float>& a, cudaStream_t s, int* rc) {
-  if (!(a.op == BF_OP_L || a.op == BF_OP_NSYM || a.op == BF_OP_NDIAGL)) return 0;
-  if (fast_shape(g) == FAST_R3_2D && !a.dots) {
+  if (!(a.op == BF_OP_L || a.op == BF_OP_NSYM || a.op == BF_OP_NDIAGL || a.op == BF_OP_DINV_W)) return 0;
+  if (fast_shape(g) == FAST_R3_2D && !a.dots && a.op != BF_OP_DINV_W) {
     switch (K) {
       case 4: *rc = launch_apply_rb_w<4>(g, a, s); return 1;
       case 8: *rc = launch_apply_rb_w<8>(g, a, s); return 1;
@@ -737,6 +745,25 @@ int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k,
   return apply_block<double>(g, op, X, ldx, k, Y, ldy, dots, s);
 }
 
+// One BF step y = D^-1 W x (one column) whose on-the-fly weights take `guide` instead of
+// the graph's own guide (the re-guided iteration: guide = x).
+template <typename T>
+static int apply_step_guided(const bf_graph* g, const T* guide, const T* X, T* Y, cudaStream_t s) {
+  ApplyArgs<T> a;
+  a.guide = guide;
+  a.scale = nullptr;
+  a.wf = g->wf;
+  a.wmode = g->p.weight_mode;
+  a.op = BF_OP_DINV_W;
+  a.n = g->n;
+  a.ldx = 1;
+  a.ldy = 1;
+  a.X = X;
+  a.Y = Y;
+  a.dots = nullptr;
+  return apply_chunk<T>(g, 1, a, s);
+}
+
 // ================================================================== host: graph
 template <typename T>
 static void fill_geom(Geom<T>& G, const bf_params& p, int nx, int ny, int rx, int ry,
@@ -837,10 +864,11 @@ extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out,
 
 // Copy the guide into the graph and compute the degree, the scalings and (stored modes)
 // the weights; synchronises s to report a non-finite guide.
-static int compute_weights(bf_graph* g, const void* guide, cudaStream_t s) {
+// Eq. 2 weights, degree and scalings of g for a new guide, enqueued on s; a non-finite
+// guide value sets g->flag (which the caller clears and reads).
+static int launch_weights(bf_graph* g, const void* guide, cudaStream_t s) {
   const size_t nb = (size_t)g->n * g->esize;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(g->flag, 0, sizeof(int), s)) != cudaSuccess) return bf_cuda_fail(e, "memset(flag)");
   if ((e = cudaMemcpyAsync(g->guide, guide, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return bf_cuda_fail(e, "cudaMemcpyAsync(guide)");
   const unsigned blocks = (unsigned)((g->n + BF_THREADS - 1) / BF_THREADS);
@@ -853,18 +881,77 @@ static int compute_weights(bf_graph* g, const void* guide, cudaStream_t s) {
                                                     (double*)g->dinv, (double*)g->dis, (double*)g->dls,
                                                     g->wf, g->p.weight_mode, g->flag));
   if ((e = cudaGetLastError()) != cudaSuccess) return bf_cuda_fail(e, "k_weights launch");
+  return BF_OK;
+}
+
+static int read_flag(bf_graph* g, cudaStream_t s, const char* what) {
+  cudaError_t e;
   int hflag = 0;
   if ((e = cudaMemcpyAsync(&hflag, g->flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return bf_cuda_fail(e, "cudaMemcpyAsync(flag)");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bf_cuda_fail(e, "weights sync");
-  if (hflag) return bf_fail(BF_ENONFINITE, "bf_weights: guide holds NaN or Inf");
+  if (hflag) return bf_fail(BF_ENONFINITE, what);
   return BF_OK;
+}
+
+static int compute_weights(bf_graph* g, const void* guide, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(g->flag, 0, sizeof(int), s)) != cudaSuccess) return bf_cuda_fail(e, "memset(flag)");
+  const int rc = launch_weights(g, guide, s);
+  if (rc) return rc;
+  return read_flag(g, s, "bf_weights: guide holds NaN or Inf");
 }
 
 extern "C" int bf_graph_update(bf_graph* g, const void* guide, void* stream) {
   if (!g || !guide) return bf_fail(BF_EINVAL, "bf_graph_update: NULL argument");
   if ((uintptr_t)guide % g->esize) return bf_fail(BF_EINVAL, "bf_graph_update: misaligned guide");
   return compute_weights(g, guide, (cudaStream_t)stream);
+}
+
+// Section 2, the first way of iterating the filter: every step takes the current iterate
+// as the guide of Eq. 2, then applies one step x <- D^-1 W x; g ends up holding the graph
+// (weights, degree, scalings) of the last guide.  The non-finite check of that guide is
+// read once, after the last step (a NaN or Inf in an earlier iterate reaches it through
+// the window sums).
+extern "C" int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* x_out, void* stream) {
+  if (!g || !x0 || !x_out) return bf_fail(BF_EINVAL, "bf_reguided_filter: NULL argument");
+  if (iters < 0) return bf_fail(BF_EINVAL, "bf_reguided_filter: iters < 0");
+  if ((uintptr_t)x0 % g->esize || (uintptr_t)x_out % g->esize)
+    return bf_fail(BF_EINVAL, "bf_reguided_filter: misaligned vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nb = (size_t)g->n * g->esize;
+  if (iters == 0) {
+    if (x0 != x_out) BF_CUDA(cudaMemcpyAsync(x_out, x0, nb, cudaMemcpyDeviceToDevice, s));
+    return BF_OK;
+  }
+  const size_t nba = (nb + 255) & ~(size_t)255;
+  int rc = bf_ws_reserve(g, BF_WS_SIMPLE, 2 * nba);
+  if (rc) return rc;
+  void* tmp[2] = {g->ws[BF_WS_SIMPLE], (char*)g->ws[BF_WS_SIMPLE] + nba};
+  BF_CUDA(cudaMemsetAsync(g->flag, 0, sizeof(int), s));
+  // on-the-fly weights: one kernel per step, the iterate staged as its own guide; the graph
+  // is rebuilt once, for the last guide.  Stored weights: rebuilt every step.
+  const bool otf = g->p.weight_mode == BF_W_ONTHEFLY;
+  const void* src = x0;
+  for (int it = 0; it < iters; ++it) {
+    const bool last = (it == iters - 1);
+    void* dst = (last && x_out != src) ? x_out : tmp[it & 1];
+    if (!otf) {
+      rc = launch_weights(g, src, s);
+      if (rc) return rc;
+    }
+    rc = (g->esize == 4)
+             ? apply_step_guided<float>(g, (const float*)src, (const float*)src, (float*)dst, s)
+             : apply_step_guided<double>(g, (const double*)src, (const double*)src, (double*)dst, s);
+    if (rc) return rc;
+    if (last && otf) {
+      rc = launch_weights(g, src, s);              // src is intact: dst differs from it
+      if (rc) return rc;
+    }
+    if (last && dst != x_out) BF_CUDA(cudaMemcpyAsync(x_out, dst, nb, cudaMemcpyDeviceToDevice, s));
+    src = dst;
+  }
+  return read_flag(g, s, "bf_reguided_filter: an iterate holds NaN or Inf");
 }
 
 extern "C" int bf_graph_free(bf_graph* g) {

@@ -150,6 +150,49 @@ def test_simple_filter(iters):
     assert rel_l2(host(xin), ref) < 1e-5
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("case", ["1d", "2d"])
+@pytest.mark.parametrize("iters", [0, 1, 3])
+def test_reguided_filter(dtype, case, iters):
+    """The nonlinear iteration of Section 2 (weights rebuilt from each iterate) against the
+    oracle; in place too.  FP32: each re-guide moves the weights by about
+    2 |g_i - g_j| / sigma_r^2 times the iterate's rounding (a few 1e-6 relative here), so
+    three steps stay inside the FP32 bar."""
+    if case == "1d":
+        _, g = signal_case(1500, 4)
+        r, ss, sr = 5, 3.0, 0.1
+        shape = (1, g.size)
+    else:
+        _, g = image_case(37, 52, 11)
+        r, ss, sr = 3, 2.0, 0.08
+        shape = g.shape
+    x = dev(g.reshape(-1) if case == "1d" else g, dtype)
+    G = bf().bf_weights(x, r, ss, sr)
+    xv = x.reshape(-1)
+    y = bf().reguided_filter(G, xv, iters)
+    ref = solvers.reguided_iteration(host(xv), shape, r, ss, sr, iters)
+    assert rel_l2(host(y), ref) < tol_for(dtype)
+    xin = xv.clone()
+    bf().reguided_filter(G, xin, iters, out=xin)
+    assert rel_l2(host(xin), ref) < tol_for(dtype)
+    if iters >= 1:
+        # g is left holding the graph of the last guide x_{iters-1}
+        prev = solvers.reguided_iteration(host(xv), shape, r, ss, sr, iters - 1)
+        O = Graph(prev, shape, r, ss, sr)
+        assert rel_l2(host(bf().graph_degree(G)), O.d) < (1e-12 if dtype == torch.float64 else 1e-5)
+
+
+def test_reguided_filter_reports_nonfinite():
+    _, g = image_case(16, 16, 3)
+    x = dev(g)
+    G = bf().bf_weights(x, 1, 1.0, 0.1)
+    bad = x.reshape(-1).clone()
+    bad[40] = float("inf")
+    with pytest.raises(bf().BFError) as e:
+        bf().reguided_filter(G, bad, 2)
+    assert e.value.code == bf().BF_ENONFINITE
+
+
 def test_full_size_image_apply_sampled():
     """The 512 x 512, 7 x 7 window operator at k = 16 (the block width LOBPCG uses on this
     image), checked on sampled rows computed one by one from the oracle's definition."""

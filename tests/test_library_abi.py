@@ -21,7 +21,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ["bf_weights", "bf_apply", "cg_filter", "lobpcg_filter", "bf_graph_free",
-              "bf_last_error", "bf_simple_filter"]:
+              "bf_last_error", "bf_simple_filter", "bf_reguided_filter"]:
         assert n in names
 
 
@@ -45,3 +45,5 @@ def test_argument_validation_needs_no_gpu():
     assert lib.bf_weights(None, None, None, None) == -1
     lib.cg_filter.restype = ctypes.c_int
     assert lib.cg_filter(None, None, 3, None, None, None, None) == -1
+    lib.bf_reguided_filter.restype = ctypes.c_int
+    assert lib.bf_reguided_filter(None, None, 2, None, None) == -1

@@ -41,6 +41,10 @@ MUTATIONS = [
     # Section 4 simple iteration, Section 5 polynomial recurrence
     ("oracle/solvers.py", "x = G.DINV_W @ x", "x = G.W @ x"),
     ("oracle/spectral.py", "chi = chi + a * pi", "chi = chi + a * sig"),
+    # Section 2's nonlinear iteration: guided by x0 instead of the iterate; a step without D^-1
+    ("oracle/solvers.py", "G = Graph(x, shape, radius, sigma_s, sigma_r, window=window)",
+     "G = Graph(x0, shape, radius, sigma_s, sigma_r, window=window)"),
+    ("oracle/solvers.py", "window=window)\n        x = G.DINV_W @ x", "window=window)\n        x = x - G.L @ x"),
     # the conv-net preconditioner: input scaling, adjoint shift, ReLU mask of the wrong layer
     ("oracle/convnet.py", "c0 = np.asarray(r, np.float64) / np.asarray(d, np.float64)",
      "c0 = np.asarray(r, np.float64)"),

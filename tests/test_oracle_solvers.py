@@ -33,6 +33,63 @@ def test_simple_iteration_is_spectral_power_filter():
     np.testing.assert_allclose(xk, ref, rtol=1e-10, atol=1e-12)
 
 
+# ------------------------------------------------------------------ re-guided iteration
+def _bf_step_brute(x, shape, r, ss, sr):
+    """One step of Eq. 1 written out pixel by pixel: y_i = sum_j w_ij x_j / sum_j w_ij with
+    w_ij of Eq. 2 over the in-image square window, guided by x itself."""
+    ny, nx = shape
+    X = np.asarray(x, dtype=np.float64).reshape(ny, nx)
+    Y = np.zeros_like(X)
+    ry = r if ny > 1 else 0
+    for yi in range(ny):
+        for xi in range(nx):
+            num = den = 0.0
+            for dy in range(-ry, ry + 1):
+                for dx in range(-r, r + 1):
+                    yj, xj = yi + dy, xi + dx
+                    if 0 <= yj < ny and 0 <= xj < nx:
+                        w = math.exp(-(dx * dx + dy * dy) / (2 * ss * ss)) * \
+                            math.exp(-(X[yi, xi] - X[yj, xj]) ** 2 / (2 * sr * sr))
+                        num += w * X[yj, xj]
+                        den += w
+            Y[yi, xi] = num / den
+    return Y.reshape(-1)
+
+
+@pytest.mark.parametrize("shape,r", [((1, 23), 2), ((7, 6), 1)])
+def test_reguided_iteration_brute_force(shape, r):
+    """Section 2, first way: every step re-guides by the previous result; three steps of the
+    pixel-by-pixel Eq. 1 with the weights taken from the current iterate."""
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0.0, 1.0, shape[0] * shape[1])
+    ref = x.copy()
+    for _ in range(3):
+        ref = _bf_step_brute(ref, shape, r, 1.3, 0.25)
+    got = solvers.reguided_iteration(x, shape, r, 1.3, 0.25, 3)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-14)
+
+
+def test_reguided_iteration_without_range_term_is_linear():
+    """With sigma_r = inf the weights of Eq. 2 do not depend on the guide, so re-guiding
+    changes nothing: the cascade equals the fixed-weight iteration (Section 2, second way)."""
+    G, x0 = _graph_2d(sr=np.inf)
+    got = solvers.reguided_iteration(x0, G.shape, 1, 1.0, np.inf, 4)
+    np.testing.assert_allclose(got, solvers.simple_iteration(G, x0, 4), rtol=1e-13, atol=1e-14)
+
+
+def test_reguided_iteration_differs_from_fixed_weights_and_stays_in_range():
+    """With a finite sigma_r the two ways of iterating differ (the nonlinear one re-weights),
+    and every step is a convex combination: the iterates stay within [min x0, max x0]; a
+    constant signal is a fixed point."""
+    G, x0 = _graph_2d()
+    nl = solvers.reguided_iteration(x0, G.shape, 1, 1.0, 0.2, 5)
+    lin = solvers.simple_iteration(G, x0, 5)
+    assert np.max(np.abs(nl - lin)) > 1e-6
+    assert nl.min() >= x0.min() - 1e-15 and nl.max() <= x0.max() + 1e-15
+    c = np.full(G.n, 0.37)
+    np.testing.assert_allclose(solvers.reguided_iteration(c, G.shape, 1, 1.0, 0.2, 3), c, rtol=0, atol=1e-15)
+
+
 def test_simple_iteration_keeps_d_weighted_mean():
     """e^T D (D^-1 W x) = d^T x: the BF step preserves the d-weighted sum."""
     G, x0 = _graph_2d()
