@@ -15,6 +15,8 @@ Plain numpy / scipy.sparse in float64, written step by step from the paper
 * ``spectral`` -- dense eigendecompositions (Eq. 8) used as pins: the CG polynomial
                   filter evaluated spectrally, and exact low-pass projections.
 * ``convnet``  -- the small conv net used as a learned preconditioner (forward, backward).
+* ``guided``   -- Section 3's guided filter: Algorithm 1 with truncated mean filters and
+                  the matrix of Eq. 6 it applies (degree, Laplacian) as explicit CSR.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against facts the paper or the
 mathematics fixes (symmetry, row sums, null vector, closed-form spectra, Krylov

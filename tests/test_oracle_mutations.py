@@ -45,6 +45,14 @@ MUTATIONS = [
     ("oracle/solvers.py", "G = Graph(x, shape, radius, sigma_s, sigma_r, window=window)",
      "G = Graph(x0, shape, radius, sigma_s, sigma_r, window=window)"),
     ("oracle/solvers.py", "window=window)\n        x = G.DINV_W @ x", "window=window)\n        x = x - G.L @ x"),
+    # Section 3's guided filter: Algorithm 1 and the matrix of Eq. 6
+    ("oracle/guided.py", "var_g = corr_g - mean_g * mean_g", "var_g = corr_g - mean_g"),
+    ("oracle/guided.py", "b = mean_x - a * mean_g", "b = mean_x + a * mean_g"),
+    ("oracle/guided.py", "return mean_a * g + mean_b", "return mean_a * x + mean_b"),
+    ("oracle/guided.py", "block = (1.0 + np.outer(dev, dev) / (var + eps)) / nk",
+     "block = (1.0 + np.outer(dev, dev) / (var + eps)) / nk ** 2"),
+    ("oracle/guided.py", "acc[ys0:ys1, xs0:xs1] += V[ys0 + dy:ys1 + dy, xs0 + dx:xs1 + dx]",
+     "acc[ys0:ys1, xs0:xs1] += V[ys0 - dy:ys1 - dy, xs0 - dx:xs1 - dx]"),
     # the conv-net preconditioner: input scaling, adjoint shift, ReLU mask of the wrong layer
     ("oracle/convnet.py", "c0 = np.asarray(r, np.float64) / np.asarray(d, np.float64)",
      "c0 = np.asarray(r, np.float64)"),
@@ -68,6 +76,6 @@ def test_pins_catch_planted_mistake(tmp_path, path, old, new):
     target.write_text(src.replace(old, new, 1))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         "tests/test_oracle_graph.py", "tests/test_oracle_solvers.py",
-                        "tests/test_oracle_convnet.py"],
+                        "tests/test_oracle_convnet.py", "tests/test_oracle_guided.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake not caught: {path}: {new!r}\n{r.stdout[-2000:]}"
