@@ -90,6 +90,17 @@ typedef struct bf_params {
   double  sigma_r;       /* range width of Eq. 2   (> 0; +inf: factor 1)                    */
 } bf_params;
 
+/* The guided filter's graph (Section 3): window radius r (width rho = 2r + 1) and the
+ * epsilon of Algorithm 1. */
+typedef struct bf_guided_params {
+  int32_t ndim;          /* 1: signal (ny must be 1); 2: image                             */
+  int32_t radius;        /* window radius r, 1..8 (2D) or 1..32 (1D)                        */
+  int64_t nx, ny;        /* samples per row, rows                                           */
+  int32_t dtype;         /* BF_F32 or BF_F64                                                */
+  int32_t reserved;      /* must be 0                                                       */
+  double  eps;           /* epsilon of Algorithm 1 (> 0, finite)                            */
+} bf_guided_params;
+
 typedef struct bf_graph bf_graph;   /* opaque */
 typedef struct bf_net bf_net;       /* opaque: the learned preconditioner (see below) */
 
@@ -138,6 +149,26 @@ int bf_weights(const bf_params* params, const void* guide, bf_graph** out, void*
  * BF_ENONFINITE if the guide holds NaN or Inf (the graph's values are then undefined
  * until the next successful update).  Must not overlap filter calls on the same graph. */
 int bf_graph_update(bf_graph* g, const void* guide, void* stream);
+
+/* The guided filter as a graph (Section 3: Algorithm 1 is the transform y = W(g) x of
+ * Eq. 5 with W of Eq. 6).  Square windows (1D: intervals) of radius r are truncated at
+ * the border: window k holds N_k in-image pixels with guide mean mu_k and variance
+ * sigma_k^2, and the graph is
+ *   Wt_ij = sum over windows k containing i and j of (1 + (g_i - mu_k)(g_j - mu_k) /
+ *           (sigma_k^2 + eps)) / N_k,
+ * whose rows sum to N_i (the in-image pixels of the window centred at i): D = diag(N),
+ * L = D - Wt, and Algorithm 1 with truncated mean filters is exactly D^-1 Wt.  In the
+ * interior N = |omega| and Wt / |omega| is Eq. 6 (the paper's D = I).  The returned graph
+ * works with bf_apply (ops W, L, D^-1 W = Algorithm 1, D, D^-1/2 L D^-1/2; not the
+ * (diag L) form), bf_simple_filter (the linear GF iteration), bf_reguided_filter (the
+ * nonlinear GF iteration of Section 3), cg_filter (Jacobi or identity preconditioner)
+ * and lobpcg_filter (pencil (L, D) or (L, I), Jacobi or identity preconditioner), and
+ * with bf_graph_update / bf_graph_degree / bf_graph_free; not with the learned
+ * preconditioner, the batched driver, cg_filter_noalloc or bf_graph_export_weights
+ * (BF_EINVAL).  The guide (device, n elements of dtype) is copied.  Synchronises
+ * `stream`; BF_ENONFINITE if the guide holds NaN or Inf; BF_EINVAL for a bad parameter. */
+int bf_guided_graph(const bf_guided_params* params, const void* guide, bf_graph** out,
+                    void* stream);
 
 /* Release a graph and everything it owns (NULL is allowed). */
 int bf_graph_free(bf_graph* g);

@@ -41,6 +41,13 @@ class bf_params(ctypes.Structure):
                 ("sigma_s", ctypes.c_double), ("sigma_r", ctypes.c_double)]
 
 
+class bf_guided_params(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("eps", ctypes.c_double)]
+
+
 class bf_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("restarts", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -68,6 +75,7 @@ def _load():
     vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
     sig = {
         "bf_weights": [ctypes.POINTER(bf_params), vp, ctypes.POINTER(vp), vp],
+        "bf_guided_graph": [ctypes.POINTER(bf_guided_params), vp, ctypes.POINTER(vp), vp],
         "bf_graph_free": [vp],
         "bf_graph_update": [vp, vp, vp],
         "bf_graph_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32),
@@ -197,6 +205,26 @@ def bf_weights(guide: torch.Tensor, radius: int, sigma_s: float, sigma_r: float,
                   sigma_s=float(sigma_s), sigma_r=float(sigma_r))
     h = ctypes.c_void_p()
     _check(_lib.bf_weights(ctypes.byref(p), _ptr(guide), ctypes.byref(h), _stream(stream)))
+    return Graph(h, p, (ny, nx), guide.dtype, guide.device)
+
+
+def guided_graph(guide: torch.Tensor, radius: int, eps: float, stream=None) -> Graph:
+    """The guided filter's graph of Section 3 (bf_guided_graph): Algorithm 1 as the
+    operator D^-1 Wt, Wt of Eq. 6, from a 1D signal (shape (n,)) or an image (ny, nx)."""
+    if not guide.is_cuda or guide.dtype not in (torch.float32, torch.float64):
+        raise ValueError("guide must be a float32/float64 CUDA tensor")
+    guide = guide.contiguous()
+    if guide.dim() == 1:
+        ndim, ny, nx = 1, 1, guide.shape[0]
+    elif guide.dim() == 2:
+        ndim, ny, nx = 2, guide.shape[0], guide.shape[1]
+    else:
+        raise ValueError("guide must be 1D or 2D")
+    p = bf_guided_params(ndim=ndim, radius=radius, nx=nx, ny=ny,
+                         dtype=F64 if guide.dtype == torch.float64 else F32, reserved=0,
+                         eps=float(eps))
+    h = ctypes.c_void_p()
+    _check(_lib.bf_guided_graph(ctypes.byref(p), _ptr(guide), ctypes.byref(h), _stream(stream)))
     return Graph(h, p, (ny, nx), guide.dtype, guide.device)
 
 

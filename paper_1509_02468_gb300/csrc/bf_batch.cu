@@ -399,6 +399,9 @@ bool same_opts(const bf_cg_opts& a, const bf_cg_opts& b) {
 extern "C" int bf_batch_create(const bf_graph* const* graphs, int count, bf_batch** out) {
   if (!graphs || !out || count < 1) return bf_fail(BF_EINVAL, "bf_batch_create: need graphs and count >= 1");
   *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (!graphs[i] || graphs[i]->kind != BF_KIND_BILATERAL)
+      return bf_fail(BF_EINVAL, "bf_batch_create: the batched driver takes bilateral graphs");
   bf_batch* b = new bf_batch();
   b->count = count;
   b->graphs.assign(graphs, graphs + count);

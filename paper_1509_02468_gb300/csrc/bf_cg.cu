@@ -285,6 +285,82 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_sdots(const CgArgs<T> a, int 
   }
 }
 
+// ---- operator applied by its own kernel (guided graphs): q holds L x0, then L p
+// x = x0, r = -L x0, s = T r and the sums of k_cg_init.
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_init_lx(const CgArgs<T> a) {
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * BF_THREADS) {
+    const T x0 = a.x0[i], r = -a.q[i];
+    const T s = a.dinv ? r * a.dinv[i] : r;
+    a.x[i] = x0;
+    a.r[i] = r;
+    a.s[i] = s;
+    v[0] += s * r;
+    v[1] += s * s;
+    v[2] += r * r;
+    v[3] += x0 * x0;
+  }
+  double blk[4], tot[4];
+  block_sum<4, T>(v, red, blk);
+  if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->sr = tot[0];
+    st->ss = tot[1];
+    st->rr = tot[2];
+    const double b2 = (double)a.shift * (double)a.shift * tot[3];
+    st->ref2 = b2 > 0.0 ? b2 : tot[2];
+    st->beta = 0.0;
+    st->alpha = 0.0;
+    st->iter = 0;
+    st->status = (isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2])) ? CG_RUN : CG_NONFINITE;
+  }
+}
+
+// p = s + beta p_old (first: p = s).
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_pdir(const CgArgs<T> a) {
+  if (a.st->status != CG_RUN) return;
+  const T beta = (T)a.st->beta;
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * BF_THREADS)
+    a.p_new[i] = a.first ? a.s[i] : fma(beta, a.p_old[i], a.s[i]);
+}
+
+// q = L p (in q) + shift p, p^T q, alpha: the tail of k_cg_dir.
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_cg_pq(const CgArgs<T> a) {
+  if (a.st->status != CG_RUN) return;
+  __shared__ double red[1 * (BF_THREADS / 32)];
+  __shared__ int last;
+  T v[1] = {T(0)};
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * BF_THREADS) {
+    const T p = a.p_new[i];
+    const T q = fma(a.shift, p, a.q[i]);
+    a.q[i] = q;
+    v[0] += p * q;
+  }
+  double blk[1], tot[1];
+  block_sum<1, T>(v, red, blk);
+  if (grid_sum_last<1>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->pq = tot[0];
+    if (st->sr == 0.0) {
+      st->status = CG_CONV;
+    } else if (!isfinite(tot[0])) {
+      st->status = CG_NONFINITE;
+    } else if (!(tot[0] > 0.0)) {
+      st->status = CG_BREAK;
+    } else {
+      st->alpha = st->sr / tot[0];
+    }
+  }
+}
+
 // ---- specialised-window versions of k_cg_init / k_cg_dir (float graphs, common windows)
 template <class SH, class F>
 __device__ __forceinline__ void stage1_fast(const Geom<float>& g, int bx, int by, float* sx,
@@ -487,7 +563,13 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
   const size_t sm = hp * 2 * sizeof(T);
   const bool net = (o.precond == BF_PRECOND_NET);
-  cg_launch_window<T>(true, tg, sm, s, g, a);
+  const bool guided = (g->kind == BF_KIND_GUIDED);
+  if (guided) {
+    if ((rc = bf_guided_apply<T>(g, BF_OP_L, x0, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
+    BF_LAUNCH(k_cg_init_lx<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+  } else {
+    cg_launch_window<T>(true, tg, sm, s, g, a);
+  }
   BF_CUDA(cudaGetLastError());
   if (net) {
     if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
@@ -497,7 +579,13 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
     a.first = (it == 0);
     a.p_old = pbuf[it & 1];
     a.p_new = pbuf[(it + 1) & 1];
-    cg_launch_window<T>(false, tg, sm, s, g, a);
+    if (guided) {
+      BF_LAUNCH(k_cg_pdir<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+      if ((rc = bf_guided_apply<T>(g, BF_OP_L, a.p_new, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
+      BF_LAUNCH(k_cg_pq<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+    } else {
+      cg_launch_window<T>(false, tg, sm, s, g, a);
+    }
     if (net) {
       BF_LAUNCH(k_cg_xr<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
       if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
@@ -542,8 +630,8 @@ extern "C" int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_c
   if (opts) o = *opts;
   if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET)
     return bf_fail(BF_EINVAL, "cg_filter: bad precond");
-  if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4))
-    return bf_fail(BF_EINVAL, "cg_filter: BF_PRECOND_NET needs a net and an FP32 graph");
+  if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4 || g->kind != BF_KIND_BILATERAL))
+    return bf_fail(BF_EINVAL, "cg_filter: BF_PRECOND_NET needs a net and an FP32 bilateral graph");
   if (o.beta != BF_BETA_FLEXIBLE && o.beta != BF_BETA_PRINTED)
     return bf_fail(BF_EINVAL, "cg_filter: bad beta");
   if (!(o.shift >= 0.0) || !(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "cg_filter: shift and tol must be >= 0");
@@ -667,6 +755,7 @@ extern "C" int cg_filter_noalloc(const bf_graph* g, const void* x0, int kmax,
                                  void* stream) {
   if (!g || !x0 || !x_out) return bf_fail(BF_EINVAL, "cg_filter_noalloc: NULL argument");
   if (kmax < 0) return bf_fail(BF_EINVAL, "cg_filter_noalloc: kmax < 0");
+  if (g->kind != BF_KIND_BILATERAL) return bf_fail(BF_EINVAL, "cg_filter_noalloc: takes bilateral graphs");
   bf_cg_opts o;
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;

@@ -702,6 +702,7 @@ static int apply_chunk(const bf_graph* g, int K, const ApplyArgs<T>& a, cudaStre
 template <typename T>
 static int apply_block(const bf_graph* g, int op, const T* X, int64_t ldx, int k, T* Y,
                        int64_t ldy, double* dots, cudaStream_t s) {
+  if (g->kind == BF_KIND_GUIDED) return bf_guided_apply<T>(g, op, X, ldx, k, Y, ldy, dots, nullptr, s);
   ApplyArgs<T> a;
   a.guide = (const T*)g->guide;
   a.scale = op == BF_OP_NSYM ? (const T*)g->dis : (op == BF_OP_NDIAGL ? (const T*)g->dls : nullptr);
@@ -867,6 +868,7 @@ extern "C" int bf_weights(const bf_params* p, const void* guide, bf_graph** out,
 // Eq. 2 weights, degree and scalings of g for a new guide, enqueued on s; a non-finite
 // guide value sets g->flag (which the caller clears and reads).
 static int launch_weights(bf_graph* g, const void* guide, cudaStream_t s) {
+  if (g->kind == BF_KIND_GUIDED) return bf_guided_prep(g, guide, s);
   const size_t nb = (size_t)g->n * g->esize;
   cudaError_t e;
   if ((e = cudaMemcpyAsync(g->guide, guide, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -908,6 +910,62 @@ extern "C" int bf_graph_update(bf_graph* g, const void* guide, void* stream) {
   return compute_weights(g, guide, (cudaStream_t)stream);
 }
 
+// The guided filter's graph (Section 3, Algorithm 1, Eq. 6): window statistics of the
+// guide; the operator itself is applied matrix-free (bf_guided.cu).
+extern "C" int bf_guided_graph(const bf_guided_params* p, const void* guide, bf_graph** out, void* stream) {
+  if (!p || !guide || !out) return bf_fail(BF_EINVAL, "bf_guided_graph: NULL argument");
+  *out = nullptr;
+  if (p->ndim != 1 && p->ndim != 2) return bf_fail(BF_EINVAL, "bf_guided_graph: ndim must be 1 or 2");
+  if (p->nx < 1 || p->ny < 1) return bf_fail(BF_EINVAL, "bf_guided_graph: empty signal");
+  if (p->ndim == 1 && p->ny != 1) return bf_fail(BF_EINVAL, "bf_guided_graph: ndim 1 needs ny = 1");
+  if (p->nx > INT32_MAX || p->ny > INT32_MAX || p->nx * p->ny > ((int64_t)1 << 40))
+    return bf_fail(BF_EINVAL, "bf_guided_graph: signal too large");
+  const int rmax = p->ndim == 2 ? BF_GF_MAX_R2D : BF_GF_MAX_R1D;
+  if (p->radius < 1 || p->radius > rmax) return bf_fail(BF_EINVAL, "bf_guided_graph: radius out of range");
+  if (p->dtype != BF_F32 && p->dtype != BF_F64) return bf_fail(BF_EINVAL, "bf_guided_graph: bad dtype");
+  if (p->reserved != 0) return bf_fail(BF_EINVAL, "bf_guided_graph: reserved must be 0");
+  if (!(p->eps > 0) || !std::isfinite(p->eps)) return bf_fail(BF_EINVAL, "bf_guided_graph: eps must be > 0");
+  const size_t esz = p->dtype == BF_F64 ? 8 : 4;
+  if ((uintptr_t)guide % esz) return bf_fail(BF_EINVAL, "bf_guided_graph: misaligned guide");
+  cudaStream_t s = (cudaStream_t)stream;
+  bf_graph* g = new bf_graph();
+  memset(g, 0, sizeof(*g));
+  g->kind = BF_KIND_GUIDED;
+  g->eps = p->eps;
+  g->p.ndim = p->ndim;
+  g->p.radius = p->radius;
+  g->p.nx = p->nx;
+  g->p.ny = p->ny;
+  g->p.window = BF_WINDOW_SQUARE;
+  g->p.weight_mode = BF_W_ONTHEFLY;
+  g->p.dtype = p->dtype;
+  g->p.sigma_s = g->p.sigma_r = INFINITY;
+  g->nx = (int)p->nx;
+  g->ny = (int)p->ny;
+  g->n = p->nx * p->ny;
+  g->rx = p->radius;
+  g->ry = p->ndim == 2 ? p->radius : 0;
+  g->ntaps = (2 * g->rx + 1) * (2 * g->ry + 1);
+  g->esize = esz;
+  cudaGetDevice(&g->device);
+  const size_t nb = (size_t)g->n * esz;
+  auto cleanup = [&](int code) {
+    bf_graph_free(g);
+    return code;
+  };
+  cudaError_t e;
+  void** bufs[] = {&g->guide, &g->d, &g->dinv, &g->dis, &g->dls, &g->gmu, &g->givar};
+  for (void** b : bufs)
+    if ((e = cudaMalloc(b, nb)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(guided graph)"));
+  if ((e = cudaMalloc(&g->flag, sizeof(int))) != cudaSuccess) return cleanup(bf_cuda_fail(e, "cudaMalloc(flag)"));
+  if ((e = cudaMemsetAsync(g->flag, 0, sizeof(int), s)) != cudaSuccess) return cleanup(bf_cuda_fail(e, "memset(flag)"));
+  int rc = bf_guided_prep(g, guide, s);
+  if (!rc) rc = read_flag(g, s, "bf_guided_graph: guide holds NaN or Inf");
+  if (rc) return cleanup(rc);
+  *out = g;
+  return BF_OK;
+}
+
 // Section 2, the first way of iterating the filter: every step takes the current iterate
 // as the guide of Eq. 2, then applies one step x <- D^-1 W x; g ends up holding the graph
 // (weights, degree, scalings) of the last guide.  The non-finite check of that guide is
@@ -931,7 +989,7 @@ extern "C" int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* 
   BF_CUDA(cudaMemsetAsync(g->flag, 0, sizeof(int), s));
   // on-the-fly weights: one kernel per step, the iterate staged as its own guide; the graph
   // is rebuilt once, for the last guide.  Stored weights: rebuilt every step.
-  const bool otf = g->p.weight_mode == BF_W_ONTHEFLY;
+  const bool otf = g->p.weight_mode == BF_W_ONTHEFLY && g->kind == BF_KIND_BILATERAL;
   const void* src = x0;
   for (int it = 0; it < iters; ++it) {
     const bool last = (it == iters - 1);
@@ -940,9 +998,14 @@ extern "C" int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* 
       rc = launch_weights(g, src, s);
       if (rc) return rc;
     }
-    rc = (g->esize == 4)
-             ? apply_step_guided<float>(g, (const float*)src, (const float*)src, (float*)dst, s)
-             : apply_step_guided<double>(g, (const double*)src, (const double*)src, (double*)dst, s);
+    if (g->kind == BF_KIND_GUIDED)                   // the window statistics of src are in g
+      rc = (g->esize == 4)
+               ? bf_guided_apply<float>(g, BF_OP_DINV_W, (const float*)src, 1, 1, (float*)dst, 1, nullptr, nullptr, s)
+               : bf_guided_apply<double>(g, BF_OP_DINV_W, (const double*)src, 1, 1, (double*)dst, 1, nullptr, nullptr, s);
+    else
+      rc = (g->esize == 4)
+               ? apply_step_guided<float>(g, (const float*)src, (const float*)src, (float*)dst, s)
+               : apply_step_guided<double>(g, (const double*)src, (const double*)src, (double*)dst, s);
     if (rc) return rc;
     if (last && otf) {
       rc = launch_weights(g, src, s);              // src is intact: dst differs from it
@@ -956,7 +1019,8 @@ extern "C" int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* 
 
 extern "C" int bf_graph_free(bf_graph* g) {
   if (!g) return BF_OK;
-  void* bufs[] = {g->guide, g->d, g->dinv, g->dis, g->dls, g->wf, g->ws[0], g->ws[1], g->ws[2], g->flag};
+  void* bufs[] = {g->guide, g->d, g->dinv, g->dis, g->dls, g->wf, g->ws[0], g->ws[1], g->ws[2], g->flag,
+                  g->gmu, g->givar};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete g;
@@ -980,6 +1044,8 @@ extern "C" int bf_graph_degree(const bf_graph* g, void* d_out, void* stream) {
 
 extern "C" int bf_graph_export_weights(const bf_graph* g, void* out, void* stream) {
   if (!g || !out) return bf_fail(BF_EINVAL, "bf_graph_export_weights: NULL argument");
+  if (g->kind == BF_KIND_GUIDED)
+    return bf_fail(BF_EINVAL, "bf_graph_export_weights: a guided graph has no per-tap weights");
   if ((uintptr_t)out % g->esize) return bf_fail(BF_EINVAL, "bf_graph_export_weights: misaligned output");
   const unsigned blocks = (unsigned)((g->n + BF_THREADS - 1) / BF_THREADS);
   cudaStream_t s = (cudaStream_t)stream;

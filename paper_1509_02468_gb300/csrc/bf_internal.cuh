@@ -76,7 +76,24 @@ struct bf_graph {
   void* ws[3];           // grow-only workspaces, one per filter family (BF_WS_*)
   size_t ws_bytes[3];
   int* flag;             // [1] non-finite guide flag of the weights kernel
+  int kind;              // BF_KIND_*
+  double eps;            // guided: epsilon of Algorithm 1
+  void* gmu;             // guided: [n] mean of the guide over each window
+  void* givar;           // guided: [n] 1 / (variance of the guide over each window + eps)
 };
+
+#define BF_KIND_BILATERAL 0   // Eq. 2 weights (bf_weights)
+#define BF_KIND_GUIDED    1   // the guided filter's matrix, Eq. 6 (bf_guided_graph)
+#define BF_GF_MAX_R2D 8
+#define BF_GF_MAX_R1D 32
+
+// Guided graphs (bf_guided.cu): Y = op X for ops W, L, D^-1 W, D, NSYM (dots: x^T y per
+// column, zeroed by the caller; guide NULL: the graph's own), and the window statistics
+// for a new guide (a non-finite value sets g->flag).
+template <typename T>
+int bf_guided_apply(const bf_graph* g, int op, const T* X, int64_t ldx, int k, T* Y, int64_t ldy,
+                    double* dots, const T* guide, cudaStream_t s);
+int bf_guided_prep(bf_graph* g, const void* guide, cudaStream_t s);
 
 // Workspace slots: CG and LOBPCG keep their own, so one call of each may run at the same
 // time on different streams.

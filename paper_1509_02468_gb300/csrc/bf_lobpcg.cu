@@ -1151,8 +1151,8 @@ extern "C" int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, in
   if (o.pencil != BF_PENCIL_D && o.pencil != BF_PENCIL_I) return bf_fail(BF_EINVAL, "lobpcg_filter: bad pencil");
   if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET)
     return bf_fail(BF_EINVAL, "lobpcg_filter: bad precond");
-  if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4))
-    return bf_fail(BF_EINVAL, "lobpcg_filter: BF_PRECOND_NET needs a net and an FP32 graph");
+  if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4 || g->kind != BF_KIND_BILATERAL))
+    return bf_fail(BF_EINVAL, "lobpcg_filter: BF_PRECOND_NET needs a net and an FP32 bilateral graph");
   if (!(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "lobpcg_filter: tol must be >= 0");
   if (o.gram != BF_GRAM_FP32 && o.gram != BF_GRAM_BF16 && o.gram != BF_GRAM_BF16X3)
     return bf_fail(BF_EINVAL, "lobpcg_filter: bad gram mode");

@@ -21,7 +21,8 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ["bf_weights", "bf_apply", "cg_filter", "lobpcg_filter", "bf_graph_free",
-              "bf_last_error", "bf_simple_filter", "bf_reguided_filter"]:
+              "bf_last_error", "bf_simple_filter", "bf_reguided_filter",
+              "bf_guided_graph"]:
         assert n in names
 
 
@@ -47,3 +48,5 @@ def test_argument_validation_needs_no_gpu():
     assert lib.cg_filter(None, None, 3, None, None, None, None) == -1
     lib.bf_reguided_filter.restype = ctypes.c_int
     assert lib.bf_reguided_filter(None, None, 2, None, None) == -1
+    lib.bf_guided_graph.restype = ctypes.c_int
+    assert lib.bf_guided_graph(None, None, None, None) == -1
