@@ -325,6 +325,8 @@ def run_gpu(args):
     batched = None if args.no_batch else _run_batched(bf, torch, stream)
     # ---- the nonlinear (re-guided) BF iteration of Section 2
     reguided = None if args.no_batch else _run_reguided(bf, torch, stream, flush, peak)
+    # ---- the guided filter's graph (Section 3)
+    guided = None if args.no_batch else _run_guided(bf, torch, stream, flush, peak, alu_peak)
 
     # ---- CPU baseline: the oracle on one full step (rank 0, N = 1 only)
     cpu = None
@@ -348,7 +350,7 @@ def run_gpu(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_2048": roofline_2048,
                 "roofline_dominant": roofline_rr, "cpu_baseline": cpu,
-                "batched": batched, "reguided": reguided,
+                "batched": batched, "reguided": reguided, "guided": guided,
                 "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "clocks": clk.summary(), "gpu_launches": launches}
@@ -511,6 +513,75 @@ def _run_reguided(bf, torch, stream, flush, peak, iters=10, reps=5):
     return out
 
 
+# the guided filter's apply (Section 3) at window radius r: per column and pixel, stage A
+# takes 3 lane-ops per (window, member) pair (difference, sum, FMA) and stage B 4 per
+# (pixel, window) pair, over (2r + 1)^2 pairs each; HBM: X in and Y out (8k B) plus the
+# guide, window mean, 1 / (variance + eps) and count (16 B)
+def _guided_ops_per_px(r, k):
+    return 7 * (2 * r + 1) ** 2 * k
+
+
+def _run_guided(bf, torch, stream, flush, peak, alu_peak, r=2, eps=1e-2, k=16, reps=5):
+    """The guided-filter graph of Section 3 (Algorithm 1, Eq. 6; bf_guided_graph): the L
+    apply at k = 16 on the 512 x 512 and 2048 x 2048 images (L2 flushed before every
+    launch), and CG 50 and LOBPCG k = 16 x 30 on the 512 x 512 image; the FP64 oracle's
+    Algorithm 1 timed on the 512 x 512 image."""
+    import numpy as np
+
+    from paper_1509_02468_gb300 import synth
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n=reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            flush.fill_(1.0)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts)
+
+    out = {"workload": f"guided filter graph, window {2 * r + 1}x{2 * r + 1}, eps {eps}, FP32",
+           "radius": r, "eps": eps}
+    for side, seed in ((512, 2), (2048, 3)):
+        _, noisy = synth.polygon_image(side, side, seed)
+        x = torch.as_tensor(noisy).cuda()
+        G = bf.guided_graph(x, r, eps, stream=stream)
+        X = torch.randn(side * side, k, device="cuda")
+        Y = torch.empty_like(X)
+        ms = timed(lambda: bf.bf_apply(G, "L", X, Y=Y, stream=stream))
+        npx = side * side
+        ops = _guided_ops_per_px(r, k) * npx / (ms * 1e-3)
+        gbs = (8 * k + 16) * npx / (ms * 1e-3) / 1e9
+        out[f"apply_L_k{k}_{side}x{side}"] = {
+            "us": 1e3 * ms,
+            "alu": {"achieved": ops / 1e12, "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
+                    "frac": ops / alu_peak, "ops_per_px": _guided_ops_per_px(r, k)},
+            "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "bytes_per_px": 8 * k + 16}}
+        if side == 512:
+            xv = x.reshape(-1)
+            xo = torch.empty_like(xv)
+            ms_cg = timed(lambda: bf.cg_filter(G, xv, 50, out=xo, sync=False, stream=stream), 3)
+            X0 = torch.as_tensor(synth.block_start(noisy.reshape(-1), 16, seed=2, dtype=np.float32)).cuda()
+            ms_lob = timed(lambda: bf.lobpcg_filter(G, X0, 30, want_X=False, sync=False, stream=stream), 3)
+            out["cg50_512x512"] = {"ms": ms_cg, "mpix_s": npx / (ms_cg * 1e-3) / 1e6}
+            out["lobpcg_k16x30_512x512"] = {"ms": ms_lob, "mpix_s": npx / (ms_lob * 1e-3) / 1e6}
+            from oracle import guided
+            t0 = time.perf_counter()
+            guided.guided_filter(noisy.reshape(-1).astype(np.float64), noisy.reshape(-1).astype(np.float64),
+                                 noisy.shape, r, eps)
+            t = time.perf_counter() - t0
+            out["cpu_baseline"] = {"value": npx / t / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                                   "sample": "Algorithm 1 once (one column) on the 512x512 image"}
+        G.free()
+    return out
+
+
 def _batch_inputs(seed=4):
     """The 256 instances: 192 images with sides log-uniform in [64, 1024] (polygon
     generator, noise 0.05) and 64 signals with lengths log-uniform in [1e3, 1e6]
@@ -579,7 +650,8 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
 def run_case(args):
     """Launch one kernel family of the timed step a few times on the benchmark workload, for
     an ncu capture (no timing, no JSON line): `apply` (k = 16 operator), `cg` (the CG
-    filter), `lobpcg` (one LOBPCG run)."""
+    filter), `lobpcg` (one LOBPCG run), `guided` (the guided filter's L at k = 16, window
+    5 x 5, eps 0.01)."""
     import numpy as np
     import torch
 
@@ -597,6 +669,12 @@ def run_case(args):
     elif args.case == "cg":
         for _ in range(args.steps):
             bf.cg_filter(G, guide.view(-1), w["cg_iters"], sync=False)
+    elif args.case == "guided":
+        Gg = bf.guided_graph(guide, 2, 1e-2)
+        X = torch.randn(noisy.size, 16, device="cuda")
+        Y = torch.empty_like(X)
+        for _ in range(args.steps):
+            bf.bf_apply(Gg, "L", X, Y=Y)
     elif args.case == "lobpcg":
         X0 = torch.as_tensor(synth.block_start(noisy.reshape(-1), w["lob_k"], seed=w["seed"],
                                                dtype=np.float32)).cuda()
@@ -617,8 +695,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-CG and re-guided measurements")
-    ap.add_argument("--case", choices=["apply", "cg", "lobpcg"], default=None,
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-CG, re-guided and guided-filter measurements")
+    ap.add_argument("--case", choices=["apply", "cg", "lobpcg", "guided"], default=None,
                     help="only launch one kernel family (for profiler captures)")
     ap.add_argument("--case-side", type=int, default=0, help="image side for --case")
     args = ap.parse_args()

@@ -75,22 +75,80 @@ struct GfApply {
   double* dots;             // [k] or NULL: x^T y per column
 };
 
+// Stage A sum of window k (staged at sk): ds = sum_j (x_j - x_k), cs = sum_j (g_j - mu_k)(x_j - x_k)
+// over the window's in-image members (CHECK: near the border; else all are in the image).
+template <typename T, int RT, bool ONED, bool CHECK>
+__device__ __forceinline__ int gf_stage_a(int r, int hw, int nx, int ny, int kx, int ky, const Vec<T, GF_KC>* sx,
+                                          const T* sg, int sk, T muk, Vec<T, GF_KC>& ds, Vec<T, GF_KC>& cs) {
+  const int rr = RT > 0 ? RT : r;
+  const int ry = ONED ? 0 : rr;
+  const Vec<T, GF_KC> xk = sx[sk];
+  int cnt = 0;
+#pragma unroll
+  for (int dy = -ry; dy <= ry; ++dy) {
+    if (CHECK && (ky + dy < 0 || ky + dy >= ny)) continue;
+#pragma unroll
+    for (int dx = -rr; dx <= rr; ++dx) {
+      if (CHECK && (kx + dx < 0 || kx + dx >= nx)) continue;
+      const int sj = sk + dy * hw + dx;
+      const T gd = sg[sj] - muk;
+      const Vec<T, GF_KC> xj = sx[sj];
+#pragma unroll
+      for (int c = 0; c < GF_KC; ++c) {
+        const T xd = xj.v[c] - xk.v[c];
+        ds.v[c] += xd;
+        cs.v[c] = fma(gd, xd, cs.v[c]);
+      }
+      ++cnt;
+    }
+  }
+  return cnt;
+}
+
+// Stage B sum of pixel i (staged at si, region-A position qi): the windows containing it.
+template <typename T, int RT, bool ONED, bool CHECK>
+__device__ __forceinline__ void gf_stage_b(int r, int hw, int aw, int nx, int ny, int ix, int iy, const Vec<T, GF_KC>* sx,
+                                           const Vec<T, GF_KC>* sdk, const Vec<T, GF_KC>* sak, const T* smu,
+                                           int si, int qi, T gi, const Vec<T, GF_KC>& xi, T (&lv)[GF_KC]) {
+  const int rr = RT > 0 ? RT : r;
+  const int ry = ONED ? 0 : rr;
+#pragma unroll
+  for (int dy = -ry; dy <= ry; ++dy) {
+    if (CHECK && (iy + dy < 0 || iy + dy >= ny)) continue;
+#pragma unroll
+    for (int dx = -rr; dx <= rr; ++dx) {
+      if (CHECK && (ix + dx < 0 || ix + dx >= nx)) continue;
+      const int qa = qi + dy * aw + dx;
+      const int sk = si + dy * hw + dx;
+      const T gdi = gi - smu[qa];
+      const Vec<T, GF_KC> xk = sx[sk], dk = sdk[qa], ak = sak[qa];
+#pragma unroll
+      for (int c = 0; c < GF_KC; ++c) lv[c] += ((xi.v[c] - xk.v[c]) - dk.v[c]) - gdi * ak.v[c];
+    }
+  }
+}
+
 // One TW x TH tile of outputs (one per thread); x and g staged on the tile plus a halo of
-// 2r, the windows' d_k and a_k on the tile plus r, GF_KC columns per pass.
-template <typename T, int TW, int TH>
+// 2r, the windows' d_k and a_k on the tile plus r, GF_KC columns per pass interleaved in
+// shared memory (one vector load per tap).  RT > 0: the radius at compile time.  Tiles
+// whose staged region lies inside the image skip all border tests.
+template <typename T, int TW, int TH, int RT>
 __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const GfApply<T> a) {
   static_assert(TW * TH == 256, "one output per thread");
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int r = gg.r, ry = gg.ry, nx = gg.nx, ny = gg.ny;
+  constexpr bool ONED = (TH == 1);
+  typedef Vec<T, GF_KC> V;
+  extern __shared__ __align__(32) unsigned char smem[];
+  const int r = RT > 0 ? RT : gg.r, ry = ONED ? 0 : r, nx = gg.nx, ny = gg.ny;
   const int hw = TW + 4 * r, hh = TH + 4 * ry, hp = hw * hh;
   const int aw = TW + 2 * r, ah = TH + 2 * ry, ap = aw * ah;
-  T* sg = reinterpret_cast<T*>(smem);           // [hp]   guide
-  T* sx = sg + hp;                              // [KC][hp] operand
-  T* smu = sx + GF_KC * hp;                     // [ap]   mu_k
-  T* siv = smu + ap;                            // [ap]   1 / (sigma_k^2 + eps)
-  T* sdk = siv + ap;                            // [KC][ap] d_k
-  T* sak = sdk + GF_KC * ap;                    // [KC][ap] a_k
+  V* sx = reinterpret_cast<V*>(smem);           // [hp] operand, GF_KC columns
+  V* sdk = sx + hp;                             // [ap] d_k
+  V* sak = sdk + ap;                            // [ap] a_k
+  T* sg = reinterpret_cast<T*>(sak + ap);       // [hp] guide
+  T* smu = sg + hp;                             // [ap] mu_k
+  T* siv = smu + ap;                            // [ap] 1 / (sigma_k^2 + eps)
   const int bx = blockIdx.x * TW, by = blockIdx.y * TH;
+  const bool interior = bx - 2 * r >= 0 && bx + TW + 2 * r <= nx && by - 2 * ry >= 0 && by + TH + 2 * ry <= ny;
   for (int q = threadIdx.x; q < hp; q += TW * TH) {
     const int hy = q / hw, hx = q - hy * hw;
     const int gy = by - 2 * ry + hy, gx = bx - 2 * r + hx;
@@ -108,7 +166,9 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
   const bool act = ix < nx && iy < ny;
   const int64_t i = (int64_t)iy * nx + ix;
   const int si = (ly + 2 * ry) * hw + (lx + 2 * r);
+  const int qi = (ly + ry) * aw + (lx + r);
   const bool nsym = (a.op == BF_OP_NSYM);
+  T* sxs = reinterpret_cast<T*>(sx);
   for (int c0 = 0; c0 < a.k; c0 += GF_KC) {
     __syncthreads();                            // the previous pass's readers are done
     for (int q = threadIdx.x; q < hp * GF_KC; q += TW * TH) {
@@ -121,80 +181,47 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
         v = a.X[gp * a.ldx + c0 + c];
         if (nsym) v *= a.dis[gp];
       }
-      sx[c * hp + p] = v;
+      sxs[q] = v;                               // = sx[p].v[c]
     }
     __syncthreads();
     // stage A: the windows centred on the tile plus r
     for (int q = threadIdx.x; q < ap; q += TW * TH) {
       const int ay = q / aw, ax = q - ay * aw;
       const int ky = by - ry + ay, kx = bx - r + ax;
-      T dsum[GF_KC], csum[GF_KC];
+      V ds, cs;
 #pragma unroll
-      for (int c = 0; c < GF_KC; ++c) dsum[c] = csum[c] = T(0);
+      for (int c = 0; c < GF_KC; ++c) ds.v[c] = cs.v[c] = T(0);
       if (kx >= 0 && kx < nx && ky >= 0 && ky < ny) {
-        const T muk = smu[q];
         const int sk = (ay + ry) * hw + (ax + r);
-        T xk[GF_KC];
-#pragma unroll
-        for (int c = 0; c < GF_KC; ++c) xk[c] = sx[c * hp + sk];
-        int cnt = 0;
-        for (int dy = -ry; dy <= ry; ++dy) {
-          if (ky + dy < 0 || ky + dy >= ny) continue;
-          for (int dx = -r; dx <= r; ++dx) {
-            if (kx + dx < 0 || kx + dx >= nx) continue;
-            const int sj = sk + dy * hw + dx;
-            const T gd = sg[sj] - muk;
-#pragma unroll
-            for (int c = 0; c < GF_KC; ++c) {
-              const T xd = sx[c * hp + sj] - xk[c];
-              dsum[c] += xd;
-              csum[c] = fma(gd, xd, csum[c]);
-            }
-            ++cnt;
-          }
-        }
+        const int cnt = interior ? gf_stage_a<T, RT, ONED, false>(r, hw, nx, ny, kx, ky, sx, sg, sk, smu[q], ds, cs)
+                                 : gf_stage_a<T, RT, ONED, true>(r, hw, nx, ny, kx, ky, sx, sg, sk, smu[q], ds, cs);
         const T inv = T(1) / (T)cnt, ivk = siv[q] * inv;
 #pragma unroll
         for (int c = 0; c < GF_KC; ++c) {
-          dsum[c] *= inv;
-          csum[c] *= ivk;
+          ds.v[c] *= inv;
+          cs.v[c] *= ivk;
         }
       }
-#pragma unroll
-      for (int c = 0; c < GF_KC; ++c) {
-        sdk[c * ap + q] = dsum[c];
-        sak[c * ap + q] = csum[c];
-      }
+      sdk[q] = ds;
+      sak[q] = cs;
     }
     __syncthreads();
     // stage B: (L x)_i over the windows that contain i, then the operator's epilogue
-    T xi[GF_KC], lv[GF_KC], yv[GF_KC];
+    const V xi = sx[si];
+    T lv[GF_KC], yv[GF_KC];
 #pragma unroll
-    for (int c = 0; c < GF_KC; ++c) {
-      xi[c] = sx[c * hp + si];
-      lv[c] = yv[c] = T(0);
-    }
+    for (int c = 0; c < GF_KC; ++c) lv[c] = yv[c] = T(0);
     if (act) {
       const T gi = sg[si];
-      for (int dy = -ry; dy <= ry; ++dy) {
-        if (iy + dy < 0 || iy + dy >= ny) continue;
-        for (int dx = -r; dx <= r; ++dx) {
-          if (ix + dx < 0 || ix + dx >= nx) continue;
-          const int qa = (ly + ry + dy) * aw + (lx + r + dx);
-          const int sk = si + dy * hw + dx;
-          const T gdi = gi - smu[qa];
-#pragma unroll
-          for (int c = 0; c < GF_KC; ++c)
-            lv[c] += ((xi[c] - sx[c * hp + sk]) - sdk[c * ap + qa]) - gdi * sak[c * ap + qa];
-        }
-      }
+      if (interior) gf_stage_b<T, RT, ONED, false>(r, hw, aw, nx, ny, ix, iy, sx, sdk, sak, smu, si, qi, gi, xi, lv);
+      else          gf_stage_b<T, RT, ONED, true>(r, hw, aw, nx, ny, ix, iy, sx, sdk, sak, smu, si, qi, gi, xi, lv);
       const T ni = a.d[i];
 #pragma unroll
       for (int c = 0; c < GF_KC; ++c) {
         switch (a.op) {
-          case BF_OP_W:      yv[c] = fma(ni, xi[c], -lv[c]); break;
-          case BF_OP_DINV_W: yv[c] = xi[c] - lv[c] / ni; break;
-          case BF_OP_D:      yv[c] = ni * xi[c]; break;
+          case BF_OP_W:      yv[c] = fma(ni, xi.v[c], -lv[c]); break;
+          case BF_OP_DINV_W: yv[c] = xi.v[c] - lv[c] / ni; break;
+          case BF_OP_D:      yv[c] = ni * xi.v[c]; break;
           case BF_OP_NSYM:   yv[c] = a.dis[i] * lv[c]; break;
           default:           yv[c] = lv[c]; break;        // L
         }
@@ -205,7 +232,7 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
 #pragma unroll
       for (int c = 0; c < GF_KC; ++c) {
         if (c0 + c >= a.k) break;                 // the same in every thread
-        const T xu = (act && nsym) ? a.X[i * a.ldx + c0 + c] : xi[c];
+        const T xu = (act && nsym) ? a.X[i * a.ldx + c0 + c] : xi.v[c];
         const T s = warp_sum(act ? xu * yv[c] : T(0));
         if ((threadIdx.x & 31) == 0) atomicAdd(&a.dots[c0 + c], (double)s);
       }
@@ -213,7 +240,7 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
   }
 }
 
-template <typename T, int TW, int TH>
+template <typename T, int TW, int TH, int RT>
 static int launch_guided(const bf_graph* g, const GfApply<T>& a, cudaStream_t s) {
   const GfGeom gg{g->nx, g->ny, g->rx, g->ry};
   const size_t hp = (size_t)(TW + 4 * gg.r) * (TH + 4 * gg.ry);
@@ -222,13 +249,13 @@ static int launch_guided(const bf_graph* g, const GfApply<T>& a, cudaStream_t s)
   if (sm > 227 * 1024) return bf_fail(BF_EINVAL, "guided apply: window too large for shared memory");
   static bool init = false;
   if (!init) {
-    const cudaError_t e = cudaFuncSetAttribute(k_guided_apply<T, TW, TH>,
+    const cudaError_t e = cudaFuncSetAttribute(k_guided_apply<T, TW, TH, RT>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return bf_cuda_fail(e, "cudaFuncSetAttribute(k_guided_apply)");
     init = true;
   }
   const dim3 grid((unsigned)((g->nx + TW - 1) / TW), (unsigned)((g->ny + TH - 1) / TH), 1);
-  BF_LAUNCH(k_guided_apply<T, TW, TH><<<grid, TW * TH, sm, s>>>(gg, a));
+  BF_LAUNCH(k_guided_apply<T, TW, TH, RT><<<grid, TW * TH, sm, s>>>(gg, a));
   BF_CUDA(cudaGetLastError());
   return BF_OK;
 }
@@ -254,8 +281,16 @@ int bf_guided_apply(const bf_graph* g, int op, const T* X, int64_t ldx, int k, T
   a.d = (const T*)g->d;
   a.dis = (const T*)g->dis;
   a.dots = dots;                                  // zeroed by the caller
-  if (g->ny == 1 && g->ry == 0) return launch_guided<T, 256, 1>(g, a, s);
-  return launch_guided<T, 32, 8>(g, a, s);
+  if (g->ny == 1 && g->ry == 0) {
+    if (g->rx == 2) return launch_guided<T, 256, 1, 2>(g, a, s);
+    return launch_guided<T, 256, 1, 0>(g, a, s);
+  }
+  switch (g->rx) {
+    case 1: return launch_guided<T, 32, 8, 1>(g, a, s);
+    case 2: return launch_guided<T, 32, 8, 2>(g, a, s);
+    case 3: return launch_guided<T, 32, 8, 3>(g, a, s);
+  }
+  return launch_guided<T, 32, 8, 0>(g, a, s);
 }
 template int bf_guided_apply<float>(const bf_graph*, int, const float*, int64_t, int, float*, int64_t,
                                     double*, const float*, cudaStream_t);
