@@ -50,3 +50,26 @@ def test_argument_validation_needs_no_gpu():
     assert lib.bf_reguided_filter(None, None, 2, None, None) == -1
     lib.bf_guided_graph.restype = ctypes.c_int
     assert lib.bf_guided_graph(None, None, None, None) == -1
+
+
+def test_guided_graph_parameter_checks_need_no_gpu():
+    """bf_guided_graph rejects bad parameters with BF_EINVAL before touching the device."""
+    from paper_1509_02468_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.bf_guided_graph.restype = ctypes.c_int
+
+    class P(ctypes.Structure):
+        _fields_ = [("ndim", ctypes.c_int32), ("radius", ctypes.c_int32),
+                    ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                    ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                    ("eps", ctypes.c_double)]
+
+    fake_guide = ctypes.c_void_p(256)            # never dereferenced: the checks come first
+    out = ctypes.c_void_p()
+    good = dict(ndim=2, radius=2, nx=64, ny=48, dtype=0, reserved=0, eps=0.01)
+    bad = [dict(ndim=3), dict(radius=0), dict(radius=9), dict(nx=0), dict(ndim=1, ny=2),
+           dict(dtype=7), dict(reserved=1), dict(eps=0.0), dict(eps=float("inf")), dict(eps=float("nan"))]
+    for change in bad:
+        p = P(**{**good, **change})
+        assert lib.bf_guided_graph(ctypes.byref(p), fake_guide, ctypes.byref(out), None) == -1, change
+        assert not out.value
