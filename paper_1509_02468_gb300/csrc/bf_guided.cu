@@ -19,7 +19,7 @@
 
 #include "bf_internal.cuh"
 
-#define GF_KC 4             // columns per pass of the apply
+#define GF_KC 4             // columns per pass of the apply (1 for a single column)
 
 namespace {
 
@@ -77,12 +77,12 @@ struct GfApply {
 
 // Stage A sum of window k (staged at sk): ds = sum_j (x_j - x_k), cs = sum_j (g_j - mu_k)(x_j - x_k)
 // over the window's in-image members (CHECK: near the border; else all are in the image).
-template <typename T, int RT, bool ONED, bool CHECK>
-__device__ __forceinline__ int gf_stage_a(int r, int hw, int nx, int ny, int kx, int ky, const Vec<T, GF_KC>* sx,
-                                          const T* sg, int sk, T muk, Vec<T, GF_KC>& ds, Vec<T, GF_KC>& cs) {
+template <typename T, int KC, int RT, bool ONED, bool CHECK>
+__device__ __forceinline__ int gf_stage_a(int r, int hw, int nx, int ny, int kx, int ky, const Vec<T, KC>* sx,
+                                          const T* sg, int sk, T muk, Vec<T, KC>& ds, Vec<T, KC>& cs) {
   const int rr = RT > 0 ? RT : r;
   const int ry = ONED ? 0 : rr;
-  const Vec<T, GF_KC> xk = sx[sk];
+  const Vec<T, KC> xk = sx[sk];
   int cnt = 0;
 #pragma unroll
   for (int dy = -ry; dy <= ry; ++dy) {
@@ -92,9 +92,9 @@ __device__ __forceinline__ int gf_stage_a(int r, int hw, int nx, int ny, int kx,
       if (CHECK && (kx + dx < 0 || kx + dx >= nx)) continue;
       const int sj = sk + dy * hw + dx;
       const T gd = sg[sj] - muk;
-      const Vec<T, GF_KC> xj = sx[sj];
+      const Vec<T, KC> xj = sx[sj];
 #pragma unroll
-      for (int c = 0; c < GF_KC; ++c) {
+      for (int c = 0; c < KC; ++c) {
         const T xd = xj.v[c] - xk.v[c];
         ds.v[c] += xd;
         cs.v[c] = fma(gd, xd, cs.v[c]);
@@ -106,10 +106,10 @@ __device__ __forceinline__ int gf_stage_a(int r, int hw, int nx, int ny, int kx,
 }
 
 // Stage B sum of pixel i (staged at si, region-A position qi): the windows containing it.
-template <typename T, int RT, bool ONED, bool CHECK>
-__device__ __forceinline__ void gf_stage_b(int r, int hw, int aw, int nx, int ny, int ix, int iy, const Vec<T, GF_KC>* sx,
-                                           const Vec<T, GF_KC>* sdk, const Vec<T, GF_KC>* sak, const T* smu,
-                                           int si, int qi, T gi, const Vec<T, GF_KC>& xi, T (&lv)[GF_KC]) {
+template <typename T, int KC, int RT, bool ONED, bool CHECK>
+__device__ __forceinline__ void gf_stage_b(int r, int hw, int aw, int nx, int ny, int ix, int iy, const Vec<T, KC>* sx,
+                                           const Vec<T, KC>* sdk, const Vec<T, KC>* sak, const T* smu,
+                                           int si, int qi, T gi, const Vec<T, KC>& xi, T (&lv)[KC]) {
   const int rr = RT > 0 ? RT : r;
   const int ry = ONED ? 0 : rr;
 #pragma unroll
@@ -121,27 +121,27 @@ __device__ __forceinline__ void gf_stage_b(int r, int hw, int aw, int nx, int ny
       const int qa = qi + dy * aw + dx;
       const int sk = si + dy * hw + dx;
       const T gdi = gi - smu[qa];
-      const Vec<T, GF_KC> xk = sx[sk], dk = sdk[qa], ak = sak[qa];
+      const Vec<T, KC> xk = sx[sk], dk = sdk[qa], ak = sak[qa];
 #pragma unroll
-      for (int c = 0; c < GF_KC; ++c) lv[c] += ((xi.v[c] - xk.v[c]) - dk.v[c]) - gdi * ak.v[c];
+      for (int c = 0; c < KC; ++c) lv[c] += ((xi.v[c] - xk.v[c]) - dk.v[c]) - gdi * ak.v[c];
     }
   }
 }
 
 // One TW x TH tile of outputs (one per thread); x and g staged on the tile plus a halo of
-// 2r, the windows' d_k and a_k on the tile plus r, GF_KC columns per pass interleaved in
+// 2r, the windows' d_k and a_k on the tile plus r, KC columns per pass interleaved in
 // shared memory (one vector load per tap).  RT > 0: the radius at compile time.  Tiles
 // whose staged region lies inside the image skip all border tests.
-template <typename T, int TW, int TH, int RT>
+template <typename T, int KC, int TW, int TH, int RT>
 __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const GfApply<T> a) {
   static_assert(TW * TH == 256, "one output per thread");
   constexpr bool ONED = (TH == 1);
-  typedef Vec<T, GF_KC> V;
+  typedef Vec<T, KC> V;
   extern __shared__ __align__(32) unsigned char smem[];
   const int r = RT > 0 ? RT : gg.r, ry = ONED ? 0 : r, nx = gg.nx, ny = gg.ny;
   const int hw = TW + 4 * r, hh = TH + 4 * ry, hp = hw * hh;
   const int aw = TW + 2 * r, ah = TH + 2 * ry, ap = aw * ah;
-  V* sx = reinterpret_cast<V*>(smem);           // [hp] operand, GF_KC columns
+  V* sx = reinterpret_cast<V*>(smem);           // [hp] operand, KC columns
   V* sdk = sx + hp;                             // [ap] d_k
   V* sak = sdk + ap;                            // [ap] a_k
   T* sg = reinterpret_cast<T*>(sak + ap);       // [hp] guide
@@ -169,10 +169,10 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
   const int qi = (ly + ry) * aw + (lx + r);
   const bool nsym = (a.op == BF_OP_NSYM);
   T* sxs = reinterpret_cast<T*>(sx);
-  for (int c0 = 0; c0 < a.k; c0 += GF_KC) {
+  for (int c0 = 0; c0 < a.k; c0 += KC) {
     __syncthreads();                            // the previous pass's readers are done
-    for (int q = threadIdx.x; q < hp * GF_KC; q += TW * TH) {
-      const int p = q / GF_KC, c = q - p * GF_KC;
+    for (int q = threadIdx.x; q < hp * KC; q += TW * TH) {
+      const int p = q / KC, c = q - p * KC;
       const int hy = p / hw, hx = p - hy * hw;
       const int gy = by - 2 * ry + hy, gx = bx - 2 * r + hx;
       T v = T(0);
@@ -190,14 +190,14 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
       const int ky = by - ry + ay, kx = bx - r + ax;
       V ds, cs;
 #pragma unroll
-      for (int c = 0; c < GF_KC; ++c) ds.v[c] = cs.v[c] = T(0);
+      for (int c = 0; c < KC; ++c) ds.v[c] = cs.v[c] = T(0);
       if (kx >= 0 && kx < nx && ky >= 0 && ky < ny) {
         const int sk = (ay + ry) * hw + (ax + r);
-        const int cnt = interior ? gf_stage_a<T, RT, ONED, false>(r, hw, nx, ny, kx, ky, sx, sg, sk, smu[q], ds, cs)
-                                 : gf_stage_a<T, RT, ONED, true>(r, hw, nx, ny, kx, ky, sx, sg, sk, smu[q], ds, cs);
+        const int cnt = interior ? gf_stage_a<T, KC, RT, ONED, false>(r, hw, nx, ny, kx, ky, sx, sg, sk, smu[q], ds, cs)
+                                 : gf_stage_a<T, KC, RT, ONED, true>(r, hw, nx, ny, kx, ky, sx, sg, sk, smu[q], ds, cs);
         const T inv = T(1) / (T)cnt, ivk = siv[q] * inv;
 #pragma unroll
-        for (int c = 0; c < GF_KC; ++c) {
+        for (int c = 0; c < KC; ++c) {
           ds.v[c] *= inv;
           cs.v[c] *= ivk;
         }
@@ -208,16 +208,16 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
     __syncthreads();
     // stage B: (L x)_i over the windows that contain i, then the operator's epilogue
     const V xi = sx[si];
-    T lv[GF_KC], yv[GF_KC];
+    T lv[KC], yv[KC];
 #pragma unroll
-    for (int c = 0; c < GF_KC; ++c) lv[c] = yv[c] = T(0);
+    for (int c = 0; c < KC; ++c) lv[c] = yv[c] = T(0);
     if (act) {
       const T gi = sg[si];
-      if (interior) gf_stage_b<T, RT, ONED, false>(r, hw, aw, nx, ny, ix, iy, sx, sdk, sak, smu, si, qi, gi, xi, lv);
-      else          gf_stage_b<T, RT, ONED, true>(r, hw, aw, nx, ny, ix, iy, sx, sdk, sak, smu, si, qi, gi, xi, lv);
+      if (interior) gf_stage_b<T, KC, RT, ONED, false>(r, hw, aw, nx, ny, ix, iy, sx, sdk, sak, smu, si, qi, gi, xi, lv);
+      else          gf_stage_b<T, KC, RT, ONED, true>(r, hw, aw, nx, ny, ix, iy, sx, sdk, sak, smu, si, qi, gi, xi, lv);
       const T ni = a.d[i];
 #pragma unroll
-      for (int c = 0; c < GF_KC; ++c) {
+      for (int c = 0; c < KC; ++c) {
         switch (a.op) {
           case BF_OP_W:      yv[c] = fma(ni, xi.v[c], -lv[c]); break;
           case BF_OP_DINV_W: yv[c] = xi.v[c] - lv[c] / ni; break;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
     }
     if (a.dots) {
 #pragma unroll
-      for (int c = 0; c < GF_KC; ++c) {
+      for (int c = 0; c < KC; ++c) {
         if (c0 + c >= a.k) break;                 // the same in every thread
         const T xu = (act && nsym) ? a.X[i * a.ldx + c0 + c] : xi.v[c];
         const T s = warp_sum(act ? xu * yv[c] : T(0));
@@ -240,24 +240,39 @@ __global__ void __launch_bounds__(TW * TH) k_guided_apply(const GfGeom gg, const
   }
 }
 
-template <typename T, int TW, int TH, int RT>
+template <typename T, int KC, int TW, int TH, int RT>
 static int launch_guided(const bf_graph* g, const GfApply<T>& a, cudaStream_t s) {
   const GfGeom gg{g->nx, g->ny, g->rx, g->ry};
   const size_t hp = (size_t)(TW + 4 * gg.r) * (TH + 4 * gg.ry);
   const size_t ap = (size_t)(TW + 2 * gg.r) * (TH + 2 * gg.ry);
-  const size_t sm = ((1 + GF_KC) * hp + (2 + 2 * GF_KC) * ap) * sizeof(T);
+  const size_t sm = ((1 + KC) * hp + (2 + 2 * KC) * ap) * sizeof(T);
   if (sm > 227 * 1024) return bf_fail(BF_EINVAL, "guided apply: window too large for shared memory");
   static bool init = false;
   if (!init) {
-    const cudaError_t e = cudaFuncSetAttribute(k_guided_apply<T, TW, TH, RT>,
+    const cudaError_t e = cudaFuncSetAttribute(k_guided_apply<T, KC, TW, TH, RT>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return bf_cuda_fail(e, "cudaFuncSetAttribute(k_guided_apply)");
     init = true;
   }
   const dim3 grid((unsigned)((g->nx + TW - 1) / TW), (unsigned)((g->ny + TH - 1) / TH), 1);
-  BF_LAUNCH(k_guided_apply<T, TW, TH, RT><<<grid, TW * TH, sm, s>>>(gg, a));
+  BF_LAUNCH(k_guided_apply<T, KC, TW, TH, RT><<<grid, TW * TH, sm, s>>>(gg, a));
   BF_CUDA(cudaGetLastError());
   return BF_OK;
+}
+
+// the radius at compile time for the common windows
+template <typename T, int KC>
+static int launch_guided_r(const bf_graph* g, const GfApply<T>& a, cudaStream_t s) {
+  if (g->ny == 1 && g->ry == 0) {
+    if (g->rx == 2) return launch_guided<T, KC, 256, 1, 2>(g, a, s);
+    return launch_guided<T, KC, 256, 1, 0>(g, a, s);
+  }
+  switch (g->rx) {
+    case 1: return launch_guided<T, KC, 32, 8, 1>(g, a, s);
+    case 2: return launch_guided<T, KC, 32, 8, 2>(g, a, s);
+    case 3: return launch_guided<T, KC, 32, 8, 3>(g, a, s);
+  }
+  return launch_guided<T, KC, 32, 8, 0>(g, a, s);
 }
 
 }  // namespace
@@ -281,16 +296,7 @@ int bf_guided_apply(const bf_graph* g, int op, const T* X, int64_t ldx, int k, T
   a.d = (const T*)g->d;
   a.dis = (const T*)g->dis;
   a.dots = dots;                                  // zeroed by the caller
-  if (g->ny == 1 && g->ry == 0) {
-    if (g->rx == 2) return launch_guided<T, 256, 1, 2>(g, a, s);
-    return launch_guided<T, 256, 1, 0>(g, a, s);
-  }
-  switch (g->rx) {
-    case 1: return launch_guided<T, 32, 8, 1>(g, a, s);
-    case 2: return launch_guided<T, 32, 8, 2>(g, a, s);
-    case 3: return launch_guided<T, 32, 8, 3>(g, a, s);
-  }
-  return launch_guided<T, 32, 8, 0>(g, a, s);
+  return k == 1 ? launch_guided_r<T, 1>(g, a, s) : launch_guided_r<T, GF_KC>(g, a, s);
 }
 template int bf_guided_apply<float>(const bf_graph*, int, const float*, int64_t, int, float*, int64_t,
                                     double*, const float*, cudaStream_t);
