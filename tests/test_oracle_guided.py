@@ -104,3 +104,39 @@ def test_self_guided_small_eps_preserves_a_step_edge():
     x = x.reshape(-1)
     y = guided.guided_filter(x, x, shape, 2, 1e-10)
     np.testing.assert_allclose(y, x, atol=1e-8)
+
+
+def test_cg_on_the_guided_graph_is_krylov_optimal():
+    """Algorithm 2 on the guided filter's L (Section 3 feeds it to the same filters): with
+    T = D^-1 the iterate minimises x^T L x over x0 + K_k(D^-1 L, D^-1 r0), by brute force."""
+    from oracle import solvers
+    shape, r, k = (6, 7), 1, 5
+    rng = np.random.default_rng(6)
+    g = rng.uniform(0, 1, 42)
+    G = guided.GuidedGraph(g, shape, r, 0.02)
+    x0 = g.copy()
+    out = solvers.cg(G, x0, k)
+    Lm = G.L.toarray()
+    M = Lm / G.d[:, None]
+    V = [-(Lm @ x0) / G.d]
+    for _ in range(k - 1):
+        V.append(M @ V[-1])
+    V, _ = np.linalg.qr(np.array(V).T)
+    c = np.linalg.lstsq(V.T @ Lm @ V, -(V.T @ Lm @ x0), rcond=None)[0]
+    np.testing.assert_allclose(out["x"], x0 + V @ c, rtol=1e-9, atol=1e-10)
+
+
+def test_lobpcg_on_the_guided_graph_reaches_the_dense_pencil():
+    """Algorithm 3 for the pencil (L, D) of the guided graph converges to the smallest
+    generalised eigenvalues of the dense pencil."""
+    import scipy.linalg as sla
+
+    from oracle import solvers
+    shape, r = (7, 8), 1
+    rng = np.random.default_rng(8)
+    g = rng.uniform(0, 1, 56)
+    G = guided.GuidedGraph(g, shape, r, 0.05)
+    X0 = rng.standard_normal((56, 3))
+    out = solvers.lobpcg(G, X0, 60, tol=1e-11)
+    lam = sla.eigh(G.L.toarray(), np.diag(G.d), eigvals_only=True)[:3]
+    np.testing.assert_allclose(out["theta"], lam, rtol=1e-8, atol=1e-10)
