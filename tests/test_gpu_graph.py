@@ -182,6 +182,21 @@ def test_reguided_filter(dtype, case, iters):
         assert rel_l2(host(bf().graph_degree(G)), O.d) < (1e-12 if dtype == torch.float64 else 1e-5)
 
 
+@pytest.mark.parametrize("mode", ["stored_f32", "stored_bf16"])
+def test_reguided_filter_stored_weights(mode):
+    """With stored weights every step rebuilds them from the iterate (the graph of the last
+    guide is left behind).  BF16 storage rounds each weight to 2^-9 relative, which moves a
+    weighted average by at most that times the spread of the averaged values: against the
+    exact oracle it is held to the bound the precision study uses for BF16 weights, 2^-6."""
+    _, g = image_case(29, 40, 12)
+    x = dev(g)
+    G = bf().bf_weights(x, 3, 2.0, 0.08, weight_mode=mode)
+    xv = x.reshape(-1)
+    y = bf().reguided_filter(G, xv, 3)
+    ref = solvers.reguided_iteration(host(xv), g.shape, 3, 2.0, 0.08, 3)
+    assert rel_l2(host(y), ref) < (1e-5 if mode == "stored_f32" else 2.0 ** -6)
+
+
 def test_reguided_filter_reports_nonfinite():
     _, g = image_case(16, 16, 3)
     x = dev(g)

@@ -21,6 +21,12 @@ def _case(kind):
     if kind == "1d":
         _, g = signal_case(700, 21)
         return g, 2
+    if kind == "1d_r5":                          # radius at run time (1D)
+        _, g = signal_case(900, 25)
+        return g, 5
+    if kind == "2d_r5":                          # radius at run time (2D)
+        _, g = image_case(41, 70, 26)
+        return g, 5
     if kind == "2d_r1":
         _, g = image_case(20, 33, 22)
         return g, 1
@@ -50,7 +56,7 @@ def _oracle_op(O, op, X):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("kind", ["1d", "2d_r1", "2d", "2d_r3"])
+@pytest.mark.parametrize("kind", ["1d", "1d_r5", "2d_r1", "2d", "2d_r3", "2d_r5"])
 @pytest.mark.parametrize("k", [1, 3, 16])
 def test_guided_apply(dtype, kind, k):
     """Y = op X for every operator of the guided graph; sizes span several tiles with a
