@@ -749,7 +749,7 @@ int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k,
 // One BF step y = D^-1 W x (one column) whose on-the-fly weights take `guide` instead of
 // the graph's own guide (the re-guided iteration: guide = x).
 template <typename T>
-static int apply_step_guided(const bf_graph* g, const T* guide, const T* X, T* Y, cudaStream_t s) {
+static int apply_bf_step_with_guide(const bf_graph* g, const T* guide, const T* X, T* Y, cudaStream_t s) {
   ApplyArgs<T> a;
   a.guide = guide;
   a.scale = nullptr;
@@ -1004,8 +1004,8 @@ extern "C" int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* 
                : bf_guided_apply<double>(g, BF_OP_DINV_W, (const double*)src, 1, 1, (double*)dst, 1, nullptr, nullptr, s);
     else
       rc = (g->esize == 4)
-               ? apply_step_guided<float>(g, (const float*)src, (const float*)src, (float*)dst, s)
-               : apply_step_guided<double>(g, (const double*)src, (const double*)src, (double*)dst, s);
+               ? apply_bf_step_with_guide<float>(g, (const float*)src, (const float*)src, (float*)dst, s)
+               : apply_bf_step_with_guide<double>(g, (const double*)src, (const double*)src, (double*)dst, s);
     if (rc) return rc;
     if (last && otf) {
       rc = launch_weights(g, src, s);              // src is intact: dst differs from it
