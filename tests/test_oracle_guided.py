@@ -140,3 +140,38 @@ def test_lobpcg_on_the_guided_graph_reaches_the_dense_pencil():
     out = solvers.lobpcg(G, X0, 60, tol=1e-11)
     lam = sla.eigh(G.L.toarray(), np.diag(G.d), eigvals_only=True)[:3]
     np.testing.assert_allclose(out["theta"], lam, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("shape,r", [((1, 30), 3), ((9, 11), 2)])
+def test_difference_form_equals_the_laplacian(shape, r):
+    """The identity the operator kernels use: with d_k = sum_j (x_j - x_k) / N_k and
+    a_k = sum_j (g_j - mu_k)(x_j - x_k) / N_k / (sigma_k^2 + eps) over window k,
+    (L x)_i = sum over windows k containing i of (x_i - x_k) - d_k - (g_i - mu_k) a_k."""
+    ny, nx = shape
+    rng = np.random.default_rng(9)
+    g = rng.uniform(0, 1, ny * nx)
+    x = rng.standard_normal(ny * nx)
+    eps = 0.03
+    G = guided.GuidedGraph(g, shape, r, eps)
+    ry = r if ny > 1 else 0
+    Gi, Xi = g.reshape(ny, nx), x.reshape(ny, nx)
+    dk = np.zeros((ny, nx))
+    ak = np.zeros((ny, nx))
+    mu = np.zeros((ny, nx))
+    for ky, kx in itertools.product(range(ny), range(nx)):
+        mem = [(ky + dy, kx + dx) for dy in range(-ry, ry + 1) for dx in range(-r, r + 1)
+               if 0 <= ky + dy < ny and 0 <= kx + dx < nx]
+        gv = np.array([Gi[p] for p in mem])
+        xv = np.array([Xi[p] for p in mem])
+        mu[ky, kx] = gv.mean()
+        var = ((gv - gv.mean()) ** 2).mean()
+        dk[ky, kx] = (xv - Xi[ky, kx]).mean()
+        ak[ky, kx] = ((gv - gv.mean()) * (xv - Xi[ky, kx])).mean() / (var + eps)
+    lx = np.zeros((ny, nx))
+    for iy, ix in itertools.product(range(ny), range(nx)):
+        for dy in range(-ry, ry + 1):
+            for dx in range(-r, r + 1):
+                ky, kx = iy + dy, ix + dx
+                if 0 <= ky < ny and 0 <= kx < nx:
+                    lx[iy, ix] += (Xi[iy, ix] - Xi[ky, kx]) - dk[ky, kx] - (Gi[iy, ix] - mu[ky, kx]) * ak[ky, kx]
+    np.testing.assert_allclose(lx.reshape(-1), G.L @ x, rtol=1e-11, atol=1e-12)
