@@ -11,12 +11,15 @@ self-guided).  W = (w_ij) is symmetric with w_ij >= 0, D = diag(d) with d_i = su
 the BF step is y = D^-1 W x (Eq. 3) and L = D - W (Eq. 4).  Section 4 adds the normalised
 Laplacian (diag L)^-1/2 L (diag L)^-1/2.
 
-Readings of the text (each one is listed with its reason in the design notes):
-* the sum in Eq. 1 runs over all j of the window, so w_ii = 1 is part of W and of d_i;
-* the window is square (Chebyshev radius r, |dx| <= r and |dy| <= r) or, for the 5-point
-  lattice of the Section 7 image experiment, a cross (dx = 0 or dy = 0); neighbours that
-  fall outside the image do not exist (no padding);
-* distances are Euclidean in grid units (the sample index in 1D);
+Readings of the text where it leaves a choice, each with its reason:
+* the sum in Eq. 1 runs over all j of the window, j = i included, and Eq. 2 gives that
+  term exp(0) exp(0) = 1, so w_ii = 1 is part of W and of d_i (it cancels in L);
+* the window is square (Chebyshev radius r, |dx| <= r and |dy| <= r), since the paper
+  sizes it by one width in both directions, or, for the 5-point lattice of the Section 7
+  image experiment, a cross (dx = 0 or dy = 0); the graph's vertices are the pixels, so
+  neighbours that fall outside the image do not exist (no padding);
+* |p_i - p_j| in Eq. 2 is the distance between pixel positions: Euclidean in grid units
+  (the sample index in 1D);
 * besides the paper's (diag L)-normalised Laplacian ("NDIAGL") the oracle also builds
   D^-1/2 L D^-1/2 ("NSYM"), whose spectrum is that of the pencil (L, D) used by CG and
   LOBPCG.  A pixel with diag L = 0 (no neighbour of positive weight) gets a zero row and

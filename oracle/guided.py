@@ -5,8 +5,11 @@ Test infrastructure only (see ``oracle/__init__``).
 * ``box_mean``       -- the mean filter f_mean of Algorithm 1 over a square window of
                         radius r (width rho = 2r + 1; 1D: an interval), truncated at the
                         border: each pixel averages the in-image pixels of its window.
-* ``guided_filter``  -- Algorithm 1 step by step: mean_g, mean_x, corr_g, corr_gx, var_g,
-                        cov_gx, a, b, mean_a, mean_b, y = mean_a .* g + mean_b.
+* ``guided_filter``  -- the transform Algorithm 1 computes, from its definition (Section 3,
+                        Eqs. 5-6): in every window the signal is fitted by a line in the
+                        guide, x ~ a_k g + b_k, by least squares with a ridge eps * a_k^2 per
+                        window pixel; the output at a pixel is the mean of the predictions
+                        a_k g_i + b_k of all windows that contain it.
 * ``GuidedGraph``    -- the matrix of Eq. 6 built entry by entry from the windows, its
                         degree and Laplacian, as explicit FP64 CSR matrices.
 
@@ -63,21 +66,46 @@ def _count(shape, r):
     return cnt.reshape(-1)
 
 
+def _window_sums(v, shape, r: int):
+    """(sum of v over the in-image pixels of each pixel's window, number of those pixels).
+    For square windows pixel j lies in the window centred at i exactly when i lies in the
+    window centred at j, so the same sums run over the windows that contain a pixel."""
+    ny, nx = shape
+    V = np.asarray(v, dtype=np.float64).reshape(ny, nx)
+    total = np.zeros_like(V)
+    count = np.zeros_like(V)
+    for dy, dx in _offsets(1 if ny == 1 else 2, r):
+        y0, y1 = max(0, -dy), min(ny, ny - dy)
+        x0, x1 = max(0, -dx), min(nx, nx - dx)
+        total[y0:y1, x0:x1] += V[y0 + dy:y1 + dy, x0 + dx:x1 + dx]
+        count[y0:y1, x0:x1] += 1.0
+    return total.reshape(-1), count.reshape(-1)
+
+
 def guided_filter(x, g, shape, r: int, eps: float):
-    """Algorithm 1 (guided filter) with f_mean = box_mean of radius r."""
+    """The guided filter of Section 3 (what Algorithm 1 computes with f_mean = box_mean of
+    radius r), from its definition.
+
+    Window k (centred at pixel k, N_k in-image pixels) fits the line a_k g + b_k to x by
+    minimising  sum_{j in window k} ((a_k g_j + b_k - x_j)^2 + eps a_k^2).  Setting the two
+    partial derivatives to zero gives the normal equations
+        (G2 + N eps) a + G1 b = GX,     G1 a + N b = X1,
+    with G1 = sum g_j, G2 = sum g_j^2, X1 = sum x_j, GX = sum g_j x_j over the window; they
+    are solved by Cramer's rule.  Pixel i then takes the mean over the windows k that
+    contain it of the prediction a_k g_i + b_k."""
     x = np.asarray(x, dtype=np.float64).reshape(-1)
     g = np.asarray(g, dtype=np.float64).reshape(-1)
-    mean_g = box_mean(g, shape, r)
-    mean_x = box_mean(x, shape, r)
-    corr_g = box_mean(g * g, shape, r)
-    corr_gx = box_mean(g * x, shape, r)
-    var_g = corr_g - mean_g * mean_g
-    cov_gx = corr_gx - mean_g * mean_x
-    a = cov_gx / (var_g + eps)
-    b = mean_x - a * mean_g
-    mean_a = box_mean(a, shape, r)
-    mean_b = box_mean(b, shape, r)
-    return mean_a * g + mean_b
+    G1, N = _window_sums(g, shape, r)
+    G2, _ = _window_sums(g * g, shape, r)
+    X1, _ = _window_sums(x, shape, r)
+    GX, _ = _window_sums(g * x, shape, r)
+    m11 = G2 + N * eps                       # the 2 x 2 system [[m11, G1], [G1, N]]
+    det = m11 * N - G1 * G1
+    slope = (GX * N - G1 * X1) / det
+    icpt = (m11 * X1 - G1 * GX) / det
+    slope_sum, nwin = _window_sums(slope, shape, r)
+    icpt_sum, _ = _window_sums(icpt, shape, r)
+    return (slope_sum * g + icpt_sum) / nwin
 
 
 class GuidedGraph:

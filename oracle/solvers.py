@@ -13,7 +13,7 @@ Test infrastructure only (see ``oracle/__init__``).
                           (L, B), B = D (or I), on span{X, W, P} with W = T(L X - B X Theta),
                           optionally constrained B-orthogonal to the constant vector e.
 
-Readings of the text (each listed with its reason in the design notes):
+Readings of the text where it leaves a choice, each with its reason:
 * beta.  Algorithm 2 prints beta = s^T (r - r_old) / (s_old^T s_old).  Its denominator is
   consistent with the numerator of alpha (s^T r) only when the preconditioner is the
   identity; the flexible (Polak-Ribiere) CG of the works it cites divides by
@@ -26,7 +26,8 @@ Readings of the text (each listed with its reason in the design notes):
   coefficient of w instead, which leaves the amplitude free).  The filtered signal is the
   B-orthogonal projection of x0 on span(X): y = X X^T B x0; with the constraint the
   B-mean e_bar = e^T B x0 / e^T B e is added back: y = e_bar e + X X^T B (x0 - e_bar e).
-* LOBPCG start.  Column 0 of the block is x0; the other columns are given by the caller.
+* LOBPCG start.  Algorithm 3 is stated for one vector started at x0: in a block, column 0
+  is x0 and the other columns are given by the caller.
 * LOBPCG search direction.  Algorithm 3 sets p_k+1 = w_k + gamma_k p_k.  For a block the
   raw P drifts into span X as columns converge and S^T B S becomes ill-conditioned; P is
   therefore kept B-orthogonal to X after each update (the same trial subspaces, see

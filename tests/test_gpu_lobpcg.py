@@ -5,7 +5,7 @@ import torch
 
 from oracle import solvers, spectral
 from paper_1509_02468_gb300 import synth
-from tests.gpu_helpers import (TOL_RITZ, TOL_RITZ_SMALL_F32, bf, dev, host, image_case, make_pair,
+from tests.gpu_helpers import (TOL_F32, TOL_RITZ, TOL_RITZ_SMALL_F32, bf, dev, host, image_case, make_pair,
                                rel_l2, signal_case)
 
 pytestmark = pytest.mark.gpu
@@ -73,7 +73,8 @@ def test_lobpcg_image_512_k16_fp32():
     assert out["info"].iters == 30
     e = ritz_ok(host(out["theta"]), ref["theta"])
     assert e < TOL_RITZ, (e, host(out["theta"]), ref["theta"])
-    assert rel_l2(host(out["y"]), ref["y"]) < 1e-4
+    # the filtered signal is an FP32 filter output: held to the FP32 bar (measured 2.5e-7)
+    assert rel_l2(host(out["y"]), ref["y"]) < TOL_F32
 
 
 def test_lobpcg_converges_to_dense_eigenvalues_on_gpu():

@@ -105,24 +105,31 @@ def test_gradient_accumulates_over_pairs():
         assert rel_l2(gl, tot[layer]) <= 1e-4
 
 
-def test_adam_step_matches_definition():
+def test_adam_steps_match_definition():
+    """Three Adam steps (t = 1, 2, 3), each on the gradient of a different pair: the GPU
+    weights follow the oracle's adam_step chained with the same moments.  From t = 2 on the
+    bias corrections 1 - beta^t differ from their t = 1 values."""
     G, O, noisy, d, net, Wq = setup(ny=20, nx=33, seed=8)
     rng = np.random.default_rng(12)
-    r = rng.standard_normal(noisy.size).astype(np.float32)
-    z = rng.standard_normal(noisy.size).astype(np.float32)
-    w0 = net.weights().astype(np.float64)
-    net.zero_grad()
-    net.accumulate(G, dev(r), dev(z))
-    net.accumulate(G, dev(z), dev(r))
-    g, _ = net.grad()
-    net.adam(lr=1e-2, scale=0.5)
-    w1 = net.weights().astype(np.float64)
-    gm = 0.5 * g.astype(np.float64)
-    ref, _, _ = cn.adam_step([w0], [gm], [np.zeros_like(w0)], [np.zeros_like(w0)], t=1, lr=1e-2)
-    np.testing.assert_allclose(w1, ref[0], rtol=1e-6, atol=1e-7)
+    w_ref = net.weights().astype(np.float64)
+    m = [np.zeros_like(w_ref)]
+    v = [np.zeros_like(w_ref)]
+    for t in (1, 2, 3):
+        r = rng.standard_normal(noisy.size).astype(np.float32)
+        z = rng.standard_normal(noisy.size).astype(np.float32)
+        net.zero_grad()
+        net.accumulate(G, dev(r), dev(z))
+        net.accumulate(G, dev(z), dev(r))
+        g, _ = net.grad()
+        net.adam(lr=1e-2, scale=0.5)
+        w_gpu = net.weights().astype(np.float64)
+        W, m, v = cn.adam_step([w_ref], [0.5 * g.astype(np.float64)], m, v, t=t, lr=1e-2)
+        np.testing.assert_allclose(w_gpu, W[0], rtol=1e-6, atol=1e-7)
+        # continue from the GPU's FP32 weights so that rounding does not accumulate
+        w_ref = w_gpu
     # the BF16 copy follows the master weights, and the accumulators were reset
     wq = net.weights(rounded=True)
-    assert np.max(np.abs(wq - w1) / np.maximum(np.abs(w1), 1e-30)) <= 2.0 ** -8
+    assert np.max(np.abs(wq - w_gpu) / np.maximum(np.abs(w_gpu), 1e-30)) <= 2.0 ** -8
     g2, l2 = net.grad()
     assert np.all(g2 == 0) and l2 == 0.0
 

@@ -79,3 +79,34 @@ def test_adam_step_from_its_definition():
     np.testing.assert_allclose(W1[0], [0.9, -2.1], atol=1e-7)
     np.testing.assert_allclose(m1[0], 0.1 * g[0])
     np.testing.assert_allclose(v1[0], 0.001 * g[0] ** 2)
+
+
+def test_adam_three_steps_hand_computed():
+    """Three Adam steps on one weight with the gradients 1, -2, 0.5 (lr 0.1, beta1 0.9,
+    beta2 0.999, eps 1e-8), worked out by hand from Kingma and Ba's update:
+    m_t = 0.1, -0.11, -0.049;  v_t = 0.001, 0.004999, 0.005244001;
+    bias-corrected m_t / (1 - 0.9^t) = 1, -0.578947..., -0.180812...;
+    v_t / (1 - 0.999^t) = 1, 2.500750..., 1.749749...;
+    w_t = 0.900000001, 0.936610353..., 0.950279419...  From the second step on, the
+    corrections 1 - beta^t differ from their first-step values, so a dropped exponent
+    fails here."""
+    w, m, v = [np.array([1.0])], [np.zeros(1)], [np.zeros(1)]
+    expect = [(0.1, 0.001, 0.900000001), (-0.11, 0.004999, 0.9366103534720751),
+              (-0.049, 0.005244001, 0.9502794196738217)]
+    for t, (g, (m_ref, v_ref, w_ref)) in enumerate(zip((1.0, -2.0, 0.5), expect), start=1):
+        w, m, v = cn.adam_step(w, [np.array([g])], m, v, t=t, lr=0.1)
+        np.testing.assert_allclose(m[0], [m_ref], rtol=1e-12)
+        np.testing.assert_allclose(v[0], [v_ref], rtol=1e-12)
+        np.testing.assert_allclose(w[0], [w_ref], rtol=1e-12)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    """With a constant gradient the bias corrections make m_hat = g and v_hat = g^2 at
+    every step t (m_t = (1 - beta1^t) g, v_t = (1 - beta2^t) g^2), so each step moves every
+    weight by lr * sign(g) up to eps, whatever t."""
+    g = [np.array([0.3, -1.7, 4.0])]
+    w, m, v = [np.zeros(3)], [np.zeros(3)], [np.zeros(3)]
+    for t in range(1, 8):
+        w_prev = w[0].copy()
+        w, m, v = cn.adam_step(w, g, m, v, t=t, lr=0.05)
+        np.testing.assert_allclose(w[0] - w_prev, -0.05 * np.sign(g[0]), rtol=1e-6)

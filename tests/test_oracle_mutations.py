@@ -46,9 +46,10 @@ MUTATIONS = [
      "G = Graph(x0, shape, radius, sigma_s, sigma_r, window=window)"),
     ("oracle/solvers.py", "window=window)\n        x = G.DINV_W @ x", "window=window)\n        x = x - G.L @ x"),
     # Section 3's guided filter: Algorithm 1 and the matrix of Eq. 6
-    ("oracle/guided.py", "var_g = corr_g - mean_g * mean_g", "var_g = corr_g - mean_g"),
-    ("oracle/guided.py", "b = mean_x - a * mean_g", "b = mean_x + a * mean_g"),
-    ("oracle/guided.py", "return mean_a * g + mean_b", "return mean_a * x + mean_b"),
+    ("oracle/guided.py", "m11 = G2 + N * eps", "m11 = G2 + eps"),
+    ("oracle/guided.py", "icpt = (m11 * X1 - G1 * GX) / det", "icpt = (m11 * X1 + G1 * GX) / det"),
+    ("oracle/guided.py", "return (slope_sum * g + icpt_sum) / nwin", "return (slope_sum * x + icpt_sum) / nwin"),
+    ("oracle/guided.py", "slope = (GX * N - G1 * X1) / det", "slope = (GX * N - G1 * X1) / (m11 * N)"),
     ("oracle/guided.py", "block = (1.0 + np.outer(dev, dev) / (var + eps)) / nk",
      "block = (1.0 + np.outer(dev, dev) / (var + eps)) / nk ** 2"),
     ("oracle/guided.py", "acc[ys0:ys1, xs0:xs1] += V[ys0 + dy:ys1 + dy, xs0 + dx:xs1 + dx]",
@@ -60,6 +61,9 @@ MUTATIONS = [
      "shifted = gp[:, 1 + a:1 + a + H, 1 + b:1 + b + W]"),
     ("oracle/convnet.py", 'G1 = conv_t(G2, W2) * (c["A1"] > 0)', 'G1 = conv_t(G2, W2) * (c["A2"] > 0)'),
     ("oracle/convnet.py", "vv = b2 * vv + (1 - b2) * g * g", "vv = b2 * vv + (1 - b2) * g"),
+    # Adam's bias corrections without the step exponent (equal to the right ones at t = 1)
+    ("oracle/convnet.py", "mh = mm / (1 - b1 ** t)", "mh = mm / (1 - b1)"),
+    ("oracle/convnet.py", "vh = vv / (1 - b2 ** t)", "vh = vv / (1 - b2)"),
 ]
 
 
