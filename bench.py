@@ -113,8 +113,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_step(noisy, w):
-    """One step of the pipeline on the FP64 CPU oracle; returns seconds."""
+def _oracle_step(noisy, w, outputs=None):
+    """One step of the pipeline on the FP64 CPU oracle, on the inputs the GPU step gets
+    (the FP32 image and the FP32 block start, widened); returns seconds.  If `outputs` is a
+    dict it receives the step's results (CG x, LOBPCG y and theta)."""
     import numpy as np
 
     from oracle import solvers
@@ -123,33 +125,58 @@ def _oracle_step(noisy, w):
     t0 = time.perf_counter()
     G = Graph(noisy.astype(np.float64), noisy.shape, w["radius"], w["sigma_s"], w["sigma_r"])
     x0 = noisy.reshape(-1).astype(np.float64)
-    solvers.cg(G, x0, w["cg_iters"])
-    X0 = synth.block_start(x0, w["lob_k"], seed=w["seed"], dtype=np.float64)
-    solvers.lobpcg(G, X0, w["lob_iters"])
-    return time.perf_counter() - t0
+    cg = solvers.cg(G, x0, w["cg_iters"])
+    X0 = synth.block_start(noisy.reshape(-1), w["lob_k"], seed=w["seed"], dtype=np.float32)
+    lob = solvers.lobpcg(G, X0.astype(np.float64), w["lob_iters"])
+    t = time.perf_counter() - t0
+    if outputs is not None:
+        outputs.update(x_cg=cg["x"], y=lob["y"], theta=lob["theta"])
+    return t
 
 
-def _cpu_child(side, steps, warmup):
-    """Runs in a subprocess with one BLAS thread: times the oracle pipeline."""
+def _cpu_child(side, steps, warmup, out_path=None):
+    """Runs in a subprocess with one BLAS thread: times the oracle pipeline; with out_path
+    it also saves the last step's results there (.npz)."""
+    import numpy as np
+
     from paper_1509_02468_gb300 import synth
     w = dict(WORKLOAD)
     _, noisy = synth.polygon_image(side, side, w["seed"], noise=w["noise"])
     for _ in range(warmup):
         _oracle_step(noisy, w)
-    ts = [_oracle_step(noisy, w) for _ in range(steps)]
+    outs = {}
+    ts = [_oracle_step(noisy, w, outs) for _ in range(steps)]
+    if out_path:
+        np.savez(out_path, **outs)
     print(json.dumps({"times": ts, "npix": side * side}))
 
 
-def run_cpu(side, steps, warmup):
+def run_cpu(side, steps, warmup, out_path=None):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", str(side),
-                        str(steps), str(warmup)], capture_output=True, text=True, env=env)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", str(side), str(steps), str(warmup)]
+    if out_path:
+        cmd.append(out_path)
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle timing failed:\n" + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def step_errors(ref, x_cg, y, theta):
+    """Relative errors of the timed step's outputs against the oracle's step on the same
+    input: relative L2 for the CG output and the LOBPCG filtered signal, and for the Ritz
+    values max |theta - theta_ref| / max(|theta_ref|, 1e-3 max |theta_ref|)."""
+    import numpy as np
+    rl2 = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+    th_ref = ref["theta"]
+    scale = np.maximum(np.abs(th_ref), 1e-3 * np.abs(th_ref).max())
+    return {"cg_x": rl2(x_cg, ref["x_cg"]), "lobpcg_y": rl2(y, ref["y"]),
+            "theta": float(np.max(np.abs(np.asarray(theta, np.float64) - th_ref) / scale)),
+            "bar": {"outputs": 1e-5, "theta": 1e-6},
+            "against": "FP64 CPU oracle, one step on the same inputs"}
 
 
 def job_rate(ms_local, units_local, world, dist=None, device="cpu"):
@@ -259,6 +286,9 @@ def run_gpu(args):
             times.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
     launches = (bf.launch_count() - launches0) / args.steps
+    last = keep[-1][1]
+    step_out = {"x_cg": x_cg.double().cpu().numpy(), "y": last["y"].double().cpu().numpy(),
+                "theta": last["theta"].cpu().numpy()}
     keep.clear()
     ms, value = job_rate(sum(times) / len(times), npix, world, dist, "cuda")
 
@@ -330,8 +360,14 @@ def run_gpu(args):
 
     # ---- CPU baseline: the oracle on one full step (rank 0, N = 1 only)
     cpu = None
+    err = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        res = run_cpu(w["nx"], 1, 0)
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            ref_path = os.path.join(td, "oracle_step.npz")
+            res = run_cpu(w["nx"], 1, 0, ref_path)
+            ref = dict(np.load(ref_path))
+        err = step_errors(ref, step_out["x_cg"], step_out["y"], step_out["theta"])
         cpu = {"value": res["npix"] / res["times"][0] / 1e6, "unit": "Mpix/s", "cores": 1,
                "kind": "oracle",
                "sample": "one full step (512x512: graph + CG 50 + LOBPCG k=16 x 30), FP64 "
@@ -349,7 +385,7 @@ def run_gpu(args):
                            "l2": "flushed between steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_2048": roofline_2048,
-                "roofline_dominant": roofline_rr, "cpu_baseline": cpu,
+                "roofline_dominant": roofline_rr, "cpu_baseline": cpu, "err": err,
                 "batched": batched, "reguided": reguided, "guided": guided,
                 "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -685,9 +721,22 @@ def run_case(args):
     return 0
 
 
+def _relaunch(n):
+    """`--gpus N` without a launcher: start N ranks of this script (one per GPU) with
+    torch.distributed.run on this node and return its exit status."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.run(cmd).returncode
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--cpu-child":
-        _cpu_child(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
+        _cpu_child(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]),
+                   sys.argv[5] if len(sys.argv) > 5 else None)
         return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -702,6 +751,8 @@ def main():
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return _relaunch(args.gpus)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -220,8 +220,11 @@ int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* x_out, void
  * flexible beta, shift 0, tol 0).  If info is not NULL the stream is synchronised and
  * info filled; a breakdown then returns BF_EBREAKDOWN.  With tol > 0 the call also reads
  * the solver status every 64 iterations (a stream synchronisation) and stops enqueueing
- * once the run has stopped; with tol = 0 it never reads back before the end (so it can be
- * captured in a CUDA graph).  BF_PRECOND_NET takes T from opts->net. */
+ * once the run has stopped.  With tol = 0 and info = NULL it only enqueues kernels (the
+ * scalar state is initialised by a kernel, not copied from the host), so it can be
+ * captured in a CUDA graph once an uncaptured call on the same graph has sized the
+ * workspace (the first call, or one with a larger problem, may allocate it).
+ * BF_PRECOND_NET takes T from opts->net. */
 int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
               void* x_out, bf_info* info, void* stream);
 
@@ -243,15 +246,19 @@ int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, int k, int km
  * with cudaMalloc -- and cudaFree, which synchronises the whole device -- when a larger
  * problem arrives.  Callers that must not allocate device memory once they are running
  * (a fixed memory budget owned by another allocator, a loop that cannot take the implicit
- * device synchronisation) call this instead: same arguments, same kernels and results,
- * but the scratch lives in a static device array of the library, about 12.6 MB, which
- * every GPU that loads the library holds until the process exits.  Limits: n <= 262144
- * samples and at most 65536 operator tiles; larger problems return BF_EINVAL.  The
+ * device synchronisation) call this instead.  Same arguments and the same algorithm as
+ * cg_filter, run by the same code (the same kernels for the graph's window, the same
+ * early stop with tol > 0), so the results equal cg_filter's; the scratch lives in a
+ * static device array of the library, about 12.6 MB, which every GPU that loads the
+ * library holds until the process exits.  Bilateral graphs (bf_weights) only, FP32 or
+ * FP64, any weight mode; T = Jacobi or identity (BF_EINVAL otherwise).  Limits: n <=
+ * 262144 samples and at most 65536 operator tiles; larger problems return BF_EINVAL.  The
  * caller still provides the graph (built beforehand with bf_weights), x0 and x_out.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture.  Every call
- * shares the one array, so calls whose GPU work overlaps (other streams, other host
- * threads) race and must be serialised by the caller. */
+ * shares the one array and starts by rewriting its scalar state, so calls whose GPU work
+ * overlaps (other streams, other host threads) race and must be serialised by the
+ * caller. */
 int cg_filter_noalloc(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
                       void* x_out, bf_info* info, void* stream);
 

@@ -88,6 +88,23 @@ struct CgArgs {
   double* hist;        // [2 kmax] or NULL
 };
 
+// The scalar state of a run, written on the device (so that a fixed-count run enqueues
+// no host-to-device copy and can be captured in a CUDA graph).  The block counter of the
+// grid reductions must start at zero.
+__global__ void k_cg_state_init(CgState* st, double tol2, int beta_mode) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  CgState z;
+  z.sr = z.ss = z.rr = z.pq = z.alpha = z.beta = z.ref2 = 0.0;
+  z.tol2 = tol2;
+  z.status = CG_RUN;
+  z.iter = 0;
+  z.beta_mode = beta_mode;
+  z.pad = 0;
+  z.counter = 0u;
+  z.pad2 = 0u;
+  *st = z;
+}
+
 // Stage one scalar field (with halo) into shared memory; `f(gp)` gives the value at an
 // in-image pixel, 0 is stored outside.
 template <typename T, class F>
@@ -520,27 +537,32 @@ static void cg_launch_window(bool init, dim3 tg, size_t sm, cudaStream_t s, cons
   else BF_LAUNCH(k_cg_dir<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
 }
 
+// Device buffers of one CG run: residual r, preconditioned residual s, q = A p, the two
+// direction buffers, the block partial sums of the grid reductions and the scalar state.
 template <typename T>
-int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_out,
-           bf_info* info, cudaStream_t s) {
-  bf_graph* gm = const_cast<bf_graph*>(g);
+struct CgBufs {
+  T* r;
+  T* s;
+  T* q;
+  T* p[2];
+  double* partials;
+  CgState* st;
+};
+
+// Algorithm 2 on the buffers `b` (cg_filter: the graph's workspace; cg_filter_noalloc: the
+// library's static array).  `who` names the entry point in error messages.
+template <typename T>
+int cg_exec(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_out,
+            bf_info* info, cudaStream_t s, const CgBufs<T>& b, const char* who) {
   const int64_t n = g->n;
-  const size_t vb = ((size_t)n * sizeof(T) + 255) & ~(size_t)255;
   const dim3 tg = tile_grid(g);
-  const unsigned nb_tile = tg.x * tg.y;
   const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms());
-  const unsigned nbmax = std::max(nb_tile, nb_elem);
-  const size_t pb = ((size_t)nbmax * 4 * sizeof(double) + 255) & ~(size_t)255;
-  int rc = bf_ws_reserve(gm, BF_WS_CG, 5 * vb + pb + 256);
-  if (rc) return rc;
-  char* w = (char*)gm->ws[BF_WS_CG];
   CgArgs<T> a;
-  a.r = (T*)(w);
-  a.s = (T*)(w + vb);
-  a.q = (T*)(w + 2 * vb);
-  T* pbuf[2] = {(T*)(w + 3 * vb), (T*)(w + 4 * vb)};
-  a.partials = (double*)(w + 5 * vb);
-  a.st = (CgState*)(w + 5 * vb + pb);
+  a.r = b.r;
+  a.s = b.s;
+  a.q = b.q;
+  a.partials = b.partials;
+  a.st = b.st;
   a.x0 = x0;
   a.x = x_out;
   a.guide = (const T*)g->guide;
@@ -551,19 +573,15 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   a.shift = (T)o.shift;
   a.hist = o.hist;
   a.first = 1;
-  a.p_old = pbuf[0];
-  a.p_new = pbuf[1];
-
-  CgState init;
-  memset(&init, 0, sizeof(init));
-  init.tol2 = o.tol > 0 ? o.tol * o.tol : 0.0;
-  init.beta_mode = o.beta;
-  BF_CUDA(cudaMemcpyAsync(a.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  a.p_old = b.p[0];
+  a.p_new = b.p[1];
+  BF_LAUNCH(k_cg_state_init<<<1, 32, 0, s>>>(a.st, o.tol > 0 ? o.tol * o.tol : 0.0, o.beta));
   const bool one_d = (g->ny == 1 && g->ry == 0);
   const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
   const size_t sm = hp * 2 * sizeof(T);
   const bool net = (o.precond == BF_PRECOND_NET);
   const bool guided = (g->kind == BF_KIND_GUIDED);
+  int rc = BF_OK;
   if (guided) {
     if ((rc = bf_guided_apply<T>(g, BF_OP_L, x0, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
     BF_LAUNCH(k_cg_init_lx<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
@@ -577,8 +595,8 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
   }
   for (int it = 0; it < kmax; ++it) {
     a.first = (it == 0);
-    a.p_old = pbuf[it & 1];
-    a.p_new = pbuf[(it + 1) & 1];
+    a.p_old = b.p[it & 1];
+    a.p_new = b.p[(it + 1) & 1];
     if (guided) {
       BF_LAUNCH(k_cg_pdir<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
       if ((rc = bf_guided_apply<T>(g, BF_OP_L, a.p_new, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
@@ -613,10 +631,38 @@ int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_o
     info->reserved = 0;
     info->rnorm = sqrt(h.rr);
     info->ref = sqrt(h.ref2);
-    if (h.status == CG_BREAK) return bf_fail(BF_EBREAKDOWN, "cg_filter: p^T q <= 0 (breakdown)");
-    if (h.status == CG_NONFINITE) return bf_fail(BF_ENONFINITE, "cg_filter: non-finite scalar");
+    if (h.status == CG_BREAK) return bf_fail(BF_EBREAKDOWN, std::string(who) + ": p^T q <= 0 (breakdown)");
+    if (h.status == CG_NONFINITE) return bf_fail(BF_ENONFINITE, std::string(who) + ": non-finite scalar");
   }
   return BF_OK;
+}
+
+// Partial-sum slots a run needs: one per block of the widest launch.
+inline unsigned cg_partial_slots(const bf_graph* g) {
+  const dim3 tg = tile_grid(g);
+  const unsigned nb_tile = tg.x * tg.y;
+  const unsigned nb_elem = (unsigned)std::min<int64_t>((g->n + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms());
+  return std::max(nb_tile, nb_elem);
+}
+
+template <typename T>
+int cg_run(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_out,
+           bf_info* info, cudaStream_t s) {
+  bf_graph* gm = const_cast<bf_graph*>(g);
+  const size_t vb = ((size_t)g->n * sizeof(T) + 255) & ~(size_t)255;
+  const size_t pb = ((size_t)cg_partial_slots(g) * 4 * sizeof(double) + 255) & ~(size_t)255;
+  int rc = bf_ws_reserve(gm, BF_WS_CG, 5 * vb + pb + 256);
+  if (rc) return rc;
+  char* w = (char*)gm->ws[BF_WS_CG];
+  CgBufs<T> b;
+  b.r = (T*)(w);
+  b.s = (T*)(w + vb);
+  b.q = (T*)(w + 2 * vb);
+  b.p[0] = (T*)(w + 3 * vb);
+  b.p[1] = (T*)(w + 4 * vb);
+  b.partials = (double*)(w + 5 * vb);
+  b.st = (CgState*)(w + 5 * vb + pb);
+  return cg_exec<T>(g, x0, kmax, o, x_out, info, s, b, "cg_filter");
 }
 
 }  // namespace
@@ -648,8 +694,9 @@ extern "C" int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_c
 // along.  Some callers cannot allow that: code that must not allocate device memory at
 // all once it is running (a fixed memory budget owned by another allocator, a loop that
 // cannot afford the implicit device synchronisation).  cg_filter_noalloc runs the same
-// kernels with their scratch in the file-scope array below instead: five n-vectors, the
-// per-block partial sums and the scalar state.  The array is a fixed part of the library
+// body (cg_exec: the same kernels, launches and early-stop polling) with its scratch in
+// the file-scope array below instead: five n-vectors, the per-block partial sums and the
+// scalar state.  The array is a fixed part of the library
 // image, so every GPU that loads the library holds it until the process exits.
 #define BF_NOALLOC_MAX_N (1 << 18)              // samples (a 512 x 512 image)
 #define BF_NOALLOC_MAX_BLOCKS (1 << 16)         // operator tiles (partial-sum slots)
@@ -682,70 +729,25 @@ int noalloc_scratch(unsigned char** out) {
 template <typename T>
 int cg_run_noalloc(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_out,
                    bf_info* info, cudaStream_t s) {
-  const int64_t n = g->n;
-  const dim3 tg = tile_grid(g);
-  const unsigned nb_tile = tg.x * tg.y;
-  const unsigned nb_elem = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms());
-  if (n > BF_NOALLOC_MAX_N)
+  if (g->n > BF_NOALLOC_MAX_N)
     return bf_fail(BF_EINVAL, "cg_filter_noalloc: n exceeds the static scratch limit of 262144 samples");
-  if (std::max(nb_tile, nb_elem) > BF_NOALLOC_MAX_BLOCKS)
+  if (cg_partial_slots(g) > BF_NOALLOC_MAX_BLOCKS)
     return bf_fail(BF_EINVAL, "cg_filter_noalloc: image shape needs more than 65536 operator tiles");
   unsigned char* w = nullptr;
   int rc = noalloc_scratch(&w);
   if (rc) return rc;
-  CgArgs<T> a;
-  a.r = (T*)(w);
-  a.s = (T*)(w + BF_NOALLOC_VEC_BYTES);
-  a.q = (T*)(w + 2 * BF_NOALLOC_VEC_BYTES);
-  T* pbuf[2] = {(T*)(w + 3 * BF_NOALLOC_VEC_BYTES), (T*)(w + 4 * BF_NOALLOC_VEC_BYTES)};
-  a.partials = (double*)(w + 5 * BF_NOALLOC_VEC_BYTES);
-  a.st = (CgState*)(w + 5 * BF_NOALLOC_VEC_BYTES + (size_t)BF_NOALLOC_MAX_BLOCKS * 4 * sizeof(double));
-  a.x0 = x0;
-  a.x = x_out;
-  a.guide = (const T*)g->guide;
-  a.dinv = o.precond == BF_PRECOND_JACOBI ? (const T*)g->dinv : nullptr;
-  a.wf = g->wf;
-  a.wmode = g->p.weight_mode;
-  a.n = n;
-  a.shift = (T)o.shift;
-  a.hist = o.hist;
-  a.first = 1;
-  a.p_old = pbuf[0];
-  a.p_new = pbuf[1];
-  // The array keeps whatever the previous call left: the state (including the block
-  // counter of the grid reductions, which must start at 0) is written in full here.
-  CgState init;
-  memset(&init, 0, sizeof(init));
-  init.tol2 = o.tol > 0 ? o.tol * o.tol : 0.0;
-  init.beta_mode = o.beta;
-  BF_CUDA(cudaMemcpyAsync(a.st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  const bool one_d = (g->ny == 1 && g->ry == 0);
-  const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
-  const size_t sm = hp * 2 * sizeof(T);
-  BF_LAUNCH(k_cg_init<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
-  BF_CUDA(cudaGetLastError());
-  for (int it = 0; it < kmax; ++it) {
-    a.first = (it == 0);
-    a.p_old = pbuf[it & 1];
-    a.p_new = pbuf[(it + 1) & 1];
-    BF_LAUNCH(k_cg_dir<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
-    BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
-  }
-  BF_CUDA(cudaGetLastError());
-  if (info) {
-    CgState h;
-    BF_CUDA(cudaMemcpyAsync(&h, a.st, sizeof(h), cudaMemcpyDeviceToHost, s));
-    BF_CUDA(cudaStreamSynchronize(s));
-    info->iters = h.iter;
-    info->status = h.status == CG_CONV ? BF_CG_CONVERGED : (h.status == CG_BREAK ? BF_CG_BREAKDOWN : 0);
-    info->restarts = 0;
-    info->reserved = 0;
-    info->rnorm = sqrt(h.rr);
-    info->ref = sqrt(h.ref2);
-    if (h.status == CG_BREAK) return bf_fail(BF_EBREAKDOWN, "cg_filter_noalloc: p^T q <= 0 (breakdown)");
-    if (h.status == CG_NONFINITE) return bf_fail(BF_ENONFINITE, "cg_filter_noalloc: non-finite scalar");
-  }
-  return BF_OK;
+  // The array keeps whatever the previous call left: cg_exec rewrites the scalar state
+  // (including the block counter of the grid reductions, which must start at 0) with a
+  // kernel before anything reads it, and every vector is written before it is read.
+  CgBufs<T> b;
+  b.r = (T*)(w);
+  b.s = (T*)(w + BF_NOALLOC_VEC_BYTES);
+  b.q = (T*)(w + 2 * BF_NOALLOC_VEC_BYTES);
+  b.p[0] = (T*)(w + 3 * BF_NOALLOC_VEC_BYTES);
+  b.p[1] = (T*)(w + 4 * BF_NOALLOC_VEC_BYTES);
+  b.partials = (double*)(w + 5 * BF_NOALLOC_VEC_BYTES);
+  b.st = (CgState*)(w + 5 * BF_NOALLOC_VEC_BYTES + (size_t)BF_NOALLOC_MAX_BLOCKS * 4 * sizeof(double));
+  return cg_exec<T>(g, x0, kmax, o, x_out, info, s, b, "cg_filter_noalloc");
 }
 
 }  // namespace

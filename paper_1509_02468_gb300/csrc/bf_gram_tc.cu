@@ -365,12 +365,10 @@ int bf_gram_tc(const float* const* S, const float* const* AS, const float* b, in
   const size_t sm = 2 * (split ? 2 : 1) * half;
   const int64_t nch = (n + TC_KT - 1) / TC_KT;
   grid = (int)std::min<int64_t>(grid, nch);
-  static bool init[2] = {false, false};
-  if (!init[split]) {
-    cudaError_t e = split ? cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
-                          : cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return bf_cuda_fail(e, "cudaFuncSetAttribute(k_gram_tc)");
-    init[split] = true;
+  {
+    const int rc_ = split ? bf_smem_attr((const void*)k_gram_tc<true>, 200 * 1024, "cudaFuncSetAttribute(k_gram_tc)")
+                          : bf_smem_attr((const void*)k_gram_tc<false>, 200 * 1024, "cudaFuncSetAttribute(k_gram_tc)");
+    if (rc_) return rc_;
   }
   if (split) BF_LAUNCH((k_gram_tc<true><<<grid, TC_THREADS, sm, s>>>(a)));
   else BF_LAUNCH((k_gram_tc<false><<<grid, TC_THREADS, sm, s>>>(a)));

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "bf_internal.cuh"
@@ -32,6 +33,19 @@ extern "C" const char* bf_last_error(void) { return g_last_error.c_str(); }
 static std::atomic<unsigned long long> g_launches{0};
 void bf_count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 extern "C" uint64_t bf_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+int bf_smem_attr(const void* fn, int bytes, const char* what) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  BF_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, fn})) return BF_OK;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return bf_cuda_fail(e, what);
+  done.insert({dev, fn});
+  return BF_OK;
+}
 
 int bf_ws_reserve(bf_graph* g, int slot, size_t bytes) {
   if (bytes <= g->ws_bytes[slot]) return BF_OK;
@@ -565,12 +579,10 @@ template <int K>
 static int launch_apply_pipe(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
   typedef PipeTile<K> TT;
   static_assert(TT::smem <= 227 * 1024, "pipelined apply tile does not fit in shared memory");
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(k_apply_pipe<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::smem);
-  });
-  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply_pipe)");
+  {
+    const int rc_ = bf_smem_attr((const void*)k_apply_pipe<K>, (int)TT::smem, "cudaFuncSetAttribute(k_apply_pipe)");
+    if (rc_) return rc_;
+  }
   const int64_t ntiles = ((g->nx + TT::tw - 1) / TT::tw) * (int64_t)((g->ny + TT::th - 1) / TT::th);
   const int grid = (int)std::min<int64_t>(ntiles, num_sms());
   BF_LAUNCH(k_apply_pipe<K><<<grid, TT::threads, TT::smem, s>>>(g->gf, a));
@@ -582,13 +594,10 @@ template <int K, bool STORED>
 static int launch_apply_rb(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
   typedef RBTile<K> TT;
   const size_t sm = (size_t)TT::hp * (K / 4) * sizeof(float4) + 2 * TT::hp * sizeof(float);
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(k_apply_rb<K, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    227 * 1024);
-  });
-  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply_rb)");
+  {
+    const int rc_ = bf_smem_attr((const void*)k_apply_rb<K, STORED>, 227 * 1024, "cudaFuncSetAttribute(k_apply_rb)");
+    if (rc_) return rc_;
+  }
   const dim3 grid((unsigned)((g->nx + TT::tw - 1) / TT::tw), (unsigned)((g->ny + TT::th - 1) / TT::th), 1);
   BF_LAUNCH(k_apply_rb<K, STORED><<<grid, BF_THREADS, sm, s>>>(g->gf, a));
   BF_CUDA(cudaGetLastError());
@@ -608,13 +617,10 @@ template <class SH, int K, bool STORED>
 static int launch_apply_fast(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
   constexpr int V = VecW<float, K>::value;
   const size_t sm = (size_t)SH::hp * (K / V) * sizeof(Vec<float, V>) + 2 * SH::hp * sizeof(float);
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(k_apply_fast<SH, K, STORED>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  });
-  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply_fast)");
+  {
+    const int rc_ = bf_smem_attr((const void*)k_apply_fast<SH, K, STORED>, 227 * 1024, "cudaFuncSetAttribute(k_apply_fast)");
+    if (rc_) return rc_;
+  }
   BF_LAUNCH(k_apply_fast<SH, K, STORED><<<tile_grid(g), BF_THREADS, sm, s>>>(g->gf, a));
   BF_CUDA(cudaGetLastError());
   return BF_OK;
@@ -668,13 +674,10 @@ static size_t apply_smem(const bf_graph* g) {
 template <typename T, int K>
 static int launch_apply(const bf_graph* g, const ApplyArgs<T>& a, cudaStream_t s) {
   const size_t sm = apply_smem<T, K>(g);
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(k_apply<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    227 * 1024);
-  });
-  if (attr_err != cudaSuccess) return bf_cuda_fail(attr_err, "cudaFuncSetAttribute(k_apply)");
+  {
+    const int rc_ = bf_smem_attr((const void*)k_apply<T, K>, 227 * 1024, "cudaFuncSetAttribute(k_apply)");
+    if (rc_) return rc_;
+  }
   if (sm > 227 * 1024) return bf_fail(BF_EINVAL, "bf_apply: tile does not fit in shared memory");
   BF_LAUNCH(k_apply<T, K><<<tile_grid(g), BF_THREADS, sm, s>>>(geom_of<T>(g), a));
   BF_CUDA(cudaGetLastError());

@@ -247,12 +247,10 @@ static int launch_guided(const bf_graph* g, const GfApply<T>& a, cudaStream_t s)
   const size_t ap = (size_t)(TW + 2 * gg.r) * (TH + 2 * gg.ry);
   const size_t sm = ((1 + KC) * hp + (2 + 2 * KC) * ap) * sizeof(T);
   if (sm > 227 * 1024) return bf_fail(BF_EINVAL, "guided apply: window too large for shared memory");
-  static bool init = false;
-  if (!init) {
-    const cudaError_t e = cudaFuncSetAttribute(k_guided_apply<T, KC, TW, TH, RT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return bf_cuda_fail(e, "cudaFuncSetAttribute(k_guided_apply)");
-    init = true;
+  {
+    const int rc_ = bf_smem_attr((const void*)k_guided_apply<T, KC, TW, TH, RT>, 227 * 1024,
+                                 "cudaFuncSetAttribute(k_guided_apply)");
+    if (rc_) return rc_;
   }
   const dim3 grid((unsigned)((g->nx + TW - 1) / TW), (unsigned)((g->ny + TH - 1) / TH), 1);
   BF_LAUNCH(k_guided_apply<T, KC, TW, TH, RT><<<grid, TW * TH, sm, s>>>(gg, a));

@@ -25,6 +25,10 @@ void bf_set_error(const std::string& msg);
 int bf_fail(int code, const std::string& msg);
 int bf_cuda_fail(cudaError_t e, const char* what);
 
+// Allow kernel `fn` `bytes` of dynamic shared memory on the current device.  The attribute
+// belongs to the device's context, so it is set once per (device, kernel), under a lock.
+int bf_smem_attr(const void* fn, int bytes, const char* what);
+
 // Every kernel launch of the library goes through BF_LAUNCH, which counts it (the count
 // is exported by bf_launch_count for diagnostics and benchmarks).
 void bf_count_launches(int n);

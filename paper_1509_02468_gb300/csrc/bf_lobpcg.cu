@@ -862,10 +862,9 @@ static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
   const int ng = GRAM_T / nt;
   size_t sm = (size_t)(4 * GramChunk<T>::buf + 2 * GramChunk<T>::pxc) * sizeof(T);
   sm = std::max(sm, (size_t)(ng / 2 + 1) * nt * 64 * sizeof(T));
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    init = true;
+  {
+    const int rc_ = bf_smem_attr((const void*)k_gram<T>, 200 * 1024, "cudaFuncSetAttribute(k_gram)");
+    if (rc_) return rc_;
   }
   BF_LAUNCH(k_gram<T><<<grid, GRAM_T, sm, s>>>(ga));
   BF_CUDA(cudaGetLastError());
@@ -883,20 +882,17 @@ static void launch_update_cw(const UpdArgs<T>& ua, int grid, cudaStream_t s) {
   const size_t sm = (size_t)(2 * ua.m * ua.k) * sizeof(T);
   const int64_t work = ua.n * (ua.k / CW);
   grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)grid);
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(k_update<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    init = true;
-  }
+  // a failure here shows as a failed launch, which the caller's cudaGetLastError reports
+  (void)bf_smem_attr((const void*)k_update<T, CW>, 200 * 1024, "cudaFuncSetAttribute(k_update)");
   BF_LAUNCH(k_update<T, CW><<<grid, 256, sm, s>>>(ua));
 }
 
 template <int KT>
 static void launch_update_f32(const UpdArgs<float>& ua, cudaStream_t s) {
   const size_t sm = (size_t)(2 * ua.m * KT) * sizeof(float);
+  (void)bf_smem_attr((const void*)k_update_f32<KT>, 200 * 1024, "cudaFuncSetAttribute(k_update_f32)");
   static int per_sm = 0;
   if (per_sm == 0) {
-    cudaFuncSetAttribute(k_update_f32<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_f32<KT>, 256, 2 * 3 * KT * KT * sizeof(float)) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;

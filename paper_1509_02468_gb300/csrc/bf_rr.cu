@@ -1059,15 +1059,11 @@ size_t rr_smem_bytes() {
 }  // namespace
 
 int bf_rr_launch(const RRParams& a, cudaStream_t s) {
-  static bool init = false;
   const size_t sm = rr_smem_bytes();
   if (!a.scr) return bf_fail(BF_EINVAL, "Rayleigh-Ritz: no scratch area");
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(k_rr_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return bf_cuda_fail(e, "cudaFuncSetAttribute(k_rr)");
-    init = true;
-  }
+  int rc = bf_smem_attr((const void*)k_rr_reduce, (int)sm, "cudaFuncSetAttribute(k_rr_reduce)");
+  if (!rc) rc = bf_smem_attr((const void*)k_rr, (int)sm, "cudaFuncSetAttribute(k_rr)");
+  if (rc) return rc;
   BF_LAUNCH(k_rr_reduce<<<1, RR_T, sm, s>>>(a));
   BF_LAUNCH(k_rr_vectors<<<a.m, 32, 0, s>>>(a));
   BF_LAUNCH(k_rr<<<1, RR_T, sm, s>>>(a));

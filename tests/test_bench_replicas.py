@@ -64,3 +64,21 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(bench, "run_cpu", lambda *a, **k: called.append(a))
     assert bench.run_reference(Args()) == 0
     assert not called and capsys.readouterr().out == ""
+
+
+def test_gpus_flag_starts_its_own_ranks():
+    """`bench.py --gpus 2` without a launcher starts two ranks itself (torch.distributed.run
+    on 127.0.0.1); the reference arm needs no GPU, runs on rank 0 and prints one line."""
+    import json
+    import subprocess
+    env = dict(os.environ)
+    for v in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(v, None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0

@@ -103,3 +103,25 @@ def test_cg_in_place_and_1d_ragged():
     bf().cg_filter(G, x, 20, out=x)
     ref = solvers.cg(O, g.astype(np.float64), 20)
     assert rel_l2(host(x), ref["x"]) < 1e-5
+
+
+def test_cg_fixed_count_captured_in_a_cuda_graph():
+    """A fixed-count cg_filter (tol = 0, no info) only enqueues kernels -- its scalar state
+    is set by a kernel -- so it can be captured once and replayed: every replay gives the
+    uncaptured result exactly."""
+    _, g = image_case(120, 136, 31)
+    G, O = make_pair(g, 3, 2.0, 0.08)
+    x0 = dev(g.reshape(-1))
+    ref, _, _ = bf().cg_filter(G, x0, 20)            # uncaptured; sizes the workspace
+    out = torch.empty_like(x0)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        bf().cg_filter(G, x0, 20, out=out, sync=False)
+    for _ in range(2):
+        out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    assert rel_l2(host(out), solvers.cg(O, g.reshape(-1).astype(np.float64), 20)["x"]) < 1e-5

@@ -1,0 +1,75 @@
+"""Parity at the sizes of the batched and the shifted-system workloads.
+
+* The 256-instance batch (192 images with sides log-uniform in [64, 1024], 64 signals with
+  lengths log-uniform in [1e3, 1e6], 36.7 M samples): one bf_batch_cg run of 50 Jacobi CG
+  iterations (Algorithm 2), every instance compared in full with the FP64 oracle's CG
+  (the oracle runs in a pool of spawned worker processes).
+* The 1024 x 1024 image of the shifted-system workload: cg_filter on (L + sigma I) x =
+  sigma x0 with sigma = 1e-2, at a fixed iteration count and with the tolerance the
+  refinement's inner solves use, against the oracle.
+"""
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1509_02468_gb300 import synth
+from tests.gpu_helpers import TOL_F32, bf, dev, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+from tests.oracle_jobs import BATCH_SEED, CG_ITERS, batch_cg_error, batch_instance
+
+
+def test_batch_256_instances_every_instance_against_oracle():
+    sizes = synth.batch_sizes(BATCH_SEED)
+    assert len(sizes) == 256
+    graphs, x0s = [], []
+    for i, (nd, ny, nx) in enumerate(sizes):
+        noisy, (r, ss, sr) = batch_instance(i, nd, ny, nx)
+        t = dev(noisy)
+        graphs.append(bf().bf_weights(t, r, ss, sr))
+        x0s.append(t.reshape(-1))
+    B = bf().Batch(graphs)
+    outs, infos = B.cg(x0s, CG_ITERS)
+    jobs = [(i, nd, ny, nx, host(x)) for i, ((nd, ny, nx), x) in enumerate(zip(sizes, outs))]
+    for G in graphs:
+        G.free()
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        # largest instances first, so the pool finishes evenly
+        order = sorted(jobs, key=lambda j: -j[2] * j[3])
+        results = list(ex.map(batch_cg_error, order, chunksize=1))
+    worst = max(results, key=lambda t: t[2])
+    for i, iters, err in results:
+        assert infos[i].iters == iters == CG_ITERS
+        assert err <= TOL_F32, (i, sizes[i], err)
+    assert worst[2] <= TOL_F32
+
+
+def test_shifted_cg_1024_fixed_count_and_inner_tolerance():
+    from oracle import solvers
+    from oracle.graph import Graph
+    _, noisy = synth.polygon_image(1024, 1024, 5)
+    t = dev(noisy)
+    G = bf().bf_weights(t, 3, 2.0, 0.08)
+    O = Graph(noisy.astype(np.float64), noisy.shape, 3, 2.0, 0.08)
+    x0 = noisy.reshape(-1).astype(np.float64)
+    sigma = 1e-2
+    # a fixed count
+    x, info, _ = bf().cg_filter(G, t.reshape(-1), 100, shift=sigma)
+    ref = solvers.cg(O, x0, 100, shift=sigma)
+    assert info.iters == ref["iters"] == 100
+    assert rel_l2(host(x), ref["x"]) <= TOL_F32
+    # with the inner tolerance of the mixed-precision refinement: the GPU's FP32 recursive
+    # residual and the oracle's FP64 one cross 1e-3 at the same iteration (+-1); the GPU
+    # iterate equals the oracle's after as many iterations
+    x, info, _ = bf().cg_filter(G, t.reshape(-1), 1000, shift=sigma, tol=1e-3)
+    ref = solvers.cg(O, x0, 1000, shift=sigma, tol=1e-3)
+    assert info.status == ref["status"] == "converged"
+    assert abs(info.iters - ref["iters"]) <= 1
+    same = solvers.cg(O, x0, info.iters, shift=sigma)
+    assert rel_l2(host(x), same["x"]) <= TOL_F32

@@ -155,8 +155,10 @@ def test_flexible_cg_with_net_matches_oracle():
     ref = solvers.cg(O, noisy.ravel().astype(np.float64), 8, precond=T, shift=shift)
     x, info, h = bf().cg_filter(G, dev(noisy.ravel()), 8, precond="net", net=net, shift=shift, hist=True)
     assert info.iters == ref["iters"] == 8
-    assert rel_l2(host(x), ref["x"]) <= 1e-4
-    np.testing.assert_allclose(host(h).reshape(-1, 2)[:, 0], ref["alpha"], rtol=1e-3)
+    # measured: x within 7e-8 and alpha within 9e-8 of the oracle (the net's ReLUs do not
+    # flip between the FP32 and the FP64 run on this input), so the FP32 bar holds
+    assert rel_l2(host(x), ref["x"]) <= TOL_F32
+    np.testing.assert_allclose(host(h).reshape(-1, 2)[:, 0], ref["alpha"], rtol=1e-5)
 
 
 def test_net_rejected_where_unsupported():
