@@ -18,6 +18,7 @@
 
 #include "bf_internal.cuh"
 #include "bf_window_fast.cuh"
+#include "bf_strip.cuh"
 
 int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, float* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
@@ -78,6 +79,7 @@ struct CgArgs {
   T* p_new;
   const T* guide;
   const T* dinv;       // Jacobi preconditioner (NULL: identity)
+  const T* d;          // degree (the strip path divides by it)
   const void* wf;
   int wmode;
   int64_t n;
@@ -507,6 +509,165 @@ __global__ void __launch_bounds__(BF_THREADS) k_cg_dir_fast(const Geom<float> g,
   }
 }
 
+// ---- strip path: FP32 graphs with the 7 x 7 window, T = Jacobi or identity -----------
+static_assert(STRIP_THREADS == BF_THREADS, "the block reductions assume BF_THREADS threads");
+// The vectors are x, s = T r (r itself is not stored: r = d s for Jacobi, r = s for the
+// identity), p (two buffers) and q.  Per iteration:
+//   k_cgs_dir:    p = s + beta p_old on the tile and its halo (staged by cp.async, the next
+//                 tile's copies in flight), q = (L + sigma I) p by strip window sums, p^T q,
+//                 and in the last block alpha;
+//   k_cgs_update: x += alpha p, s -= alpha T q, the sums s^T r, s^T q, s^T s, r^T r and
+//                 beta (four-pixel vectors).
+// Reads and writes per pixel and iteration: 20 B (direction) + 28 B (update).
+
+// r = -L x0, x = x0, s = T r; sums s^T r, s^T s, r^T r, x0^T x0.
+template <int WM>
+__global__ void __launch_bounds__(STRIP_THREADS, 2) k_cgs_init(const Geom<float> g, const CgArgs<float> a) {
+  __shared__ double red[4 * (STRIP_THREADS / 32)];
+  __shared__ int last;
+  const int nx = g.nx, ny = g.ny;
+  float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float* src[2] = {a.x0, WM == BF_W_ONTHEFLY ? a.guide : nullptr};
+  const int64_t ld[2] = {1, 1};
+  auto epi = [&](int bx, int by, int lx, int ly0, const float (&xi)[STRIP_P], const float (&acc)[STRIP_P]) {
+    const int x = bx + lx;
+#pragma unroll
+    for (int j = 0; j < STRIP_P; ++j) {
+      const int y = by + ly0 + j;
+      if (x < nx && y < ny) {
+        const int64_t i = (int64_t)y * nx + x;
+        const float r = -acc[j];
+        const float sj = a.dinv ? __fdiv_rn(r, a.d[i]) : r;
+        a.x[i] = xi[j];
+        a.s[i] = sj;
+        v[0] = fmaf(sj, r, v[0]);
+        v[1] = fmaf(sj, sj, v[1]);
+        v[2] = fmaf(r, r, v[2]);
+        v[3] = fmaf(xi[j], xi[j], v[3]);
+      }
+    }
+  };
+  strip_run<WM, 2, false>(g, a.wf, a.n, src, ld, 1, [](float*) {}, epi);
+  double blk[4], tot[4];
+  block_sum<4, float>(v, red, blk);
+  if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->sr = tot[0];
+    st->ss = tot[1];
+    st->rr = tot[2];
+    const double b2 = (double)a.shift * (double)a.shift * tot[3];
+    st->ref2 = b2 > 0.0 ? b2 : tot[2];
+    st->beta = 0.0;
+    st->alpha = 0.0;
+    st->iter = 0;
+    st->status = (isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2])) ? CG_RUN : CG_NONFINITE;
+  }
+}
+
+// p = s + beta p_old (first: p = s), q = (L + shift I) p, p^T q, alpha.
+template <int WM>
+__global__ void __launch_bounds__(STRIP_THREADS, 2) k_cgs_dir(const Geom<float> g, const CgArgs<float> a) {
+  if (a.st->status != CG_RUN) return;
+  __shared__ double red[STRIP_THREADS / 32];
+  __shared__ int last;
+  const float beta = (float)a.st->beta;
+  const int nx = g.nx, ny = g.ny;
+  float v[1] = {0.0f};
+  const bool first = a.first != 0;
+  const float* src[3] = {a.s, first ? nullptr : a.p_old, WM == BF_W_ONTHEFLY ? a.guide : nullptr};
+  const int64_t ld[3] = {1, 1, 1};
+  auto combine = [&](float* st) {
+    if (first) return;
+    for (int hp = threadIdx.x; hp < STRIP_HP; hp += STRIP_THREADS) st[hp] = fmaf(beta, st[STRIP_HP + hp], st[hp]);
+  };
+  auto epi = [&](int bx, int by, int lx, int ly0, const float (&pi)[STRIP_P], const float (&acc)[STRIP_P]) {
+    const int x = bx + lx;
+#pragma unroll
+    for (int j = 0; j < STRIP_P; ++j) {
+      const int y = by + ly0 + j;
+      if (x < nx && y < ny) {
+        const int64_t i = (int64_t)y * nx + x;
+        const float q = fmaf(a.shift, pi[j], acc[j]);
+        a.p_new[i] = pi[j];
+        a.q[i] = q;
+        v[0] = fmaf(pi[j], q, v[0]);
+      }
+    }
+  };
+  strip_run<WM, 3, true>(g, a.wf, a.n, src, ld, 2, combine, epi);
+  double blk[1], tot[1];
+  block_sum<1, float>(v, red, blk);
+  if (grid_sum_last<1>(blk, a.partials, &a.st->counter, tot, &last)) {
+    CgState* st = a.st;
+    st->pq = tot[0];
+    if (st->sr == 0.0) {
+      st->status = CG_CONV;
+    } else if (!isfinite(tot[0])) {
+      st->status = CG_NONFINITE;
+    } else if (!(tot[0] > 0.0)) {
+      st->status = CG_BREAK;
+    } else {
+      st->alpha = st->sr / tot[0];
+    }
+  }
+}
+
+// One pixel of the update: x += alpha p, s -= alpha T q, and the four sums.
+__device__ __forceinline__ void cgs_upd1(float alpha, bool jac, float q, float d, float p, float& x, float& s,
+                                         float (&v)[4]) {
+  x = fmaf(alpha, p, x);
+  float r;
+  if (jac) {
+    s = fmaf(-alpha, __fdiv_rn(q, d), s);
+    r = d * s;
+  } else {
+    s = fmaf(-alpha, q, s);
+    r = s;
+  }
+  v[0] = fmaf(s, r, v[0]);
+  v[1] = fmaf(s, q, v[1]);
+  v[2] = fmaf(s, s, v[2]);
+  v[3] = fmaf(r, r, v[3]);
+}
+
+// x += alpha p, s -= alpha T q (T = D^-1: s -= alpha q / d; r = d s), sums, beta.  Four
+// pixels per vector access (all arrays 16-byte aligned), the n % 4 tail by the last block.
+__global__ void __launch_bounds__(BF_THREADS) k_cgs_update(const CgArgs<float> a) {
+  if (a.st->status != CG_RUN) return;
+  __shared__ double red[4 * (BF_THREADS / 32)];
+  __shared__ int last;
+  const float alpha = (float)a.st->alpha;
+  const bool jac = a.dinv != nullptr;
+  float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const int64_t n4 = a.n >> 2;
+  const float4* q4 = reinterpret_cast<const float4*>(a.q);
+  const float4* d4 = reinterpret_cast<const float4*>(a.d);
+  const float4* p4 = reinterpret_cast<const float4*>(a.p_new);
+  float4* x4 = reinterpret_cast<float4*>(a.x);
+  float4* s4 = reinterpret_cast<float4*>(a.s);
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < n4; i += (int64_t)gridDim.x * BF_THREADS) {
+    const float4 q = q4[i], p = p4[i];
+    const float4 d = jac ? d4[i] : make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+    float4 x = x4[i], sv = s4[i];
+    cgs_upd1(alpha, jac, q.x, d.x, p.x, x.x, sv.x, v);
+    cgs_upd1(alpha, jac, q.y, d.y, p.y, x.y, sv.y, v);
+    cgs_upd1(alpha, jac, q.z, d.z, p.z, x.z, sv.z, v);
+    cgs_upd1(alpha, jac, q.w, d.w, p.w, x.w, sv.w, v);
+    x4[i] = x;
+    s4[i] = sv;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x < (a.n & 3)) {
+    const int64_t i = 4 * n4 + threadIdx.x;
+    float x = a.x[i], sv = a.s[i];
+    cgs_upd1(alpha, jac, a.q[i], jac ? a.d[i] : 1.0f, a.p_new[i], x, sv, v);
+    a.x[i] = x;
+    a.s[i] = sv;
+  }
+  double blk[4], tot[4];
+  block_sum<4, float>(v, red, blk);
+  if (grid_sum_last<4>(blk, a.partials, &a.st->counter, tot, &last)) cg_step_tail(a, tot);
+}
+
 // Launch the init / direction kernels: specialised window when the graph has one.
 template <class SH, bool STORED>
 static void cg_launch_fast(bool init, dim3 tg, cudaStream_t s, const bf_graph* g, const CgArgs<float>& a) {
@@ -535,6 +696,101 @@ static void cg_launch_window(bool init, dim3 tg, size_t sm, cudaStream_t s, cons
   }
   if (init) BF_LAUNCH(k_cg_init<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
   else BF_LAUNCH(k_cg_dir<T><<<tg, BF_THREADS, sm, s>>>(geom_of<T>(g), a));
+}
+
+// The kernels of the generic path (any window, FP32/FP64, guided graphs, the net T).
+template <typename T>
+int cg_generic_loop(const bf_graph* g, CgArgs<T>& a, int kmax, const bf_cg_opts& o, cudaStream_t s,
+                    T* const* pbuf, dim3 tg, size_t sm, unsigned nb_elem) {
+  const bool net = (o.precond == BF_PRECOND_NET);
+  const bool guided = (g->kind == BF_KIND_GUIDED);
+  int rc = BF_OK;
+  if (guided) {
+    if ((rc = bf_guided_apply<T>(g, BF_OP_L, a.x0, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
+    BF_LAUNCH(k_cg_init_lx<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+  } else {
+    cg_launch_window<T>(true, tg, sm, s, g, a);
+  }
+  BF_CUDA(cudaGetLastError());
+  if (net) {
+    if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
+    BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 1));
+  }
+  for (int it = 0; it < kmax; ++it) {
+    a.first = (it == 0);
+    a.p_old = pbuf[it & 1];
+    a.p_new = pbuf[(it + 1) & 1];
+    if (guided) {
+      BF_LAUNCH(k_cg_pdir<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+      if ((rc = bf_guided_apply<T>(g, BF_OP_L, a.p_new, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
+      BF_LAUNCH(k_cg_pq<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+    } else {
+      cg_launch_window<T>(false, tg, sm, s, g, a);
+    }
+    if (net) {
+      BF_LAUNCH(k_cg_xr<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+      if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
+      BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 0));
+    } else {
+      BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+    }
+    // with a tolerance, look at the status every CG_POLL iterations so that a converged
+    // run stops enqueueing (a fixed-count run never reads back and can be captured)
+    if (o.tol > 0.0 && (it + 1) % CG_POLL == 0 && it + 1 < kmax) {
+      int stv = 0;
+      BF_CUDA(cudaMemcpyAsync(&stv, &a.st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      BF_CUDA(cudaStreamSynchronize(s));
+      if (stv != CG_RUN) break;
+    }
+  }
+  return BF_OK;
+}
+
+template <int WM>
+int strip_grid(const bf_graph* g, const void* fn) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, STRIP_THREADS, STRIP_SMEM_BYTES) != cudaSuccess || v < 1)
+      v = 1;
+    per_sm = v;
+  }
+  const int64_t ntiles = (int64_t)strip_tiles_x(g->nx) * strip_tiles_y(g->ny);
+  return (int)std::min<int64_t>(ntiles, (int64_t)per_sm * cg_num_sms());
+}
+
+template <int WM>
+int cg_strip_loop_w(const bf_graph* g, CgArgs<float>& a, int kmax, double tol, cudaStream_t s,
+                    float* const* pbuf) {
+  const unsigned nb_vec =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.n / 4 + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms()));
+  a.d = (const float*)g->d;
+  const int gi = strip_grid<WM>(g, (const void*)k_cgs_init<WM>);
+  const int gd = strip_grid<WM>(g, (const void*)k_cgs_dir<WM>);
+  BF_LAUNCH(k_cgs_init<WM><<<gi, STRIP_THREADS, STRIP_SMEM_BYTES, s>>>(g->gf, a));
+  for (int it = 0; it < kmax; ++it) {
+    a.first = (it == 0);
+    a.p_old = pbuf[it & 1];
+    a.p_new = pbuf[(it + 1) & 1];
+    BF_LAUNCH(k_cgs_dir<WM><<<gd, STRIP_THREADS, STRIP_SMEM_BYTES, s>>>(g->gf, a));
+    BF_LAUNCH(k_cgs_update<<<nb_vec, BF_THREADS, 0, s>>>(a));
+    if (tol > 0.0 && (it + 1) % CG_POLL == 0 && it + 1 < kmax) {
+      int stv = 0;
+      BF_CUDA(cudaMemcpyAsync(&stv, &a.st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      BF_CUDA(cudaStreamSynchronize(s));
+      if (stv != CG_RUN) break;
+    }
+  }
+  return BF_OK;
+}
+
+int cg_strip_loop(const bf_graph* g, CgArgs<float>& a, int kmax, double tol, cudaStream_t s,
+                  float* const* pbuf) {
+  switch (g->p.weight_mode) {
+    case BF_W_STORED_F32: return cg_strip_loop_w<BF_W_STORED_F32>(g, a, kmax, tol, s, pbuf);
+    case BF_W_STORED_BF16: return cg_strip_loop_w<BF_W_STORED_BF16>(g, a, kmax, tol, s, pbuf);
+  }
+  return cg_strip_loop_w<BF_W_ONTHEFLY>(g, a, kmax, tol, s, pbuf);
 }
 
 // Device buffers of one CG run: residual r, preconditioned residual s, q = A p, the two
@@ -567,6 +823,7 @@ int cg_exec(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_
   a.x = x_out;
   a.guide = (const T*)g->guide;
   a.dinv = o.precond == BF_PRECOND_JACOBI ? (const T*)g->dinv : nullptr;
+  a.d = (const T*)g->d;
   a.wf = g->wf;
   a.wmode = g->p.weight_mode;
   a.n = n;
@@ -582,43 +839,13 @@ int cg_exec(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_
   const bool net = (o.precond == BF_PRECOND_NET);
   const bool guided = (g->kind == BF_KIND_GUIDED);
   int rc = BF_OK;
-  if (guided) {
-    if ((rc = bf_guided_apply<T>(g, BF_OP_L, x0, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
-    BF_LAUNCH(k_cg_init_lx<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
+  if (!guided && !net && sizeof(T) == 4 && fast_shape(g) == FAST_R3_2D && ((uintptr_t)x_out & 15) == 0) {
+    rc = cg_strip_loop(g, reinterpret_cast<CgArgs<float>&>(a), kmax, o.tol, s,
+                       reinterpret_cast<float* const*>(b.p));
+    if (rc) return rc;
   } else {
-    cg_launch_window<T>(true, tg, sm, s, g, a);
-  }
-  BF_CUDA(cudaGetLastError());
-  if (net) {
-    if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
-    BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 1));
-  }
-  for (int it = 0; it < kmax; ++it) {
-    a.first = (it == 0);
-    a.p_old = b.p[it & 1];
-    a.p_new = b.p[(it + 1) & 1];
-    if (guided) {
-      BF_LAUNCH(k_cg_pdir<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
-      if ((rc = bf_guided_apply<T>(g, BF_OP_L, a.p_new, 1, 1, a.q, 1, nullptr, nullptr, s))) return rc;
-      BF_LAUNCH(k_cg_pq<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
-    } else {
-      cg_launch_window<T>(false, tg, sm, s, g, a);
-    }
-    if (net) {
-      BF_LAUNCH(k_cg_xr<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
-      if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
-      BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 0));
-    } else {
-      BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
-    }
-    // with a tolerance, look at the status every CG_POLL iterations so that a converged
-    // run stops enqueueing (a fixed-count run never reads back and can be captured)
-    if (o.tol > 0.0 && (it + 1) % CG_POLL == 0 && it + 1 < kmax) {
-      int stv = 0;
-      BF_CUDA(cudaMemcpyAsync(&stv, &a.st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-      BF_CUDA(cudaStreamSynchronize(s));
-      if (stv != CG_RUN) break;
-    }
+    rc = cg_generic_loop<T>(g, a, kmax, o, s, b.p, tg, sm, nb_elem);
+    if (rc) return rc;
   }
   BF_CUDA(cudaGetLastError());
   if (info) {

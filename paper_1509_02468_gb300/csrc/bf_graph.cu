@@ -14,6 +14,7 @@
 
 #include "bf_internal.cuh"
 #include "bf_window_fast.cuh"
+#include "bf_strip.cuh"
 
 // ================================================================== errors
 static thread_local std::string g_last_error;
@@ -304,6 +305,40 @@ __global__ void __launch_bounds__(BF_THREADS) k_apply_fast(const Geom<float> g, 
       const float s = warp_sum(active ? xi[c] * yv[c] : 0.0f);
       if ((threadIdx.x & 31) == 0) atomicAdd(&a.dots[c], (double)s);
     }
+  }
+}
+
+// One column (k = 1) through the 7 x 7 window, L-type operators (L, D^-1/2 L D^-1/2,
+// (diag L)^-1/2 L (diag L)^-1/2): strip-blocked window sums (bf_strip.cuh), persistent over
+// 32 x 32 tiles, optional fused dot x^T y.
+template <int WM>
+__global__ void __launch_bounds__(STRIP_THREADS, 2) k_apply1_strip(const Geom<float> g, const ApplyArgs<float> a) {
+  const int nx = g.nx, ny = g.ny;
+  float dsum = 0.0f;
+  const float* src[3] = {a.X, a.scale, WM == BF_W_ONTHEFLY ? a.guide : nullptr};
+  const int64_t ld[3] = {a.ldx, 1, 1};
+  const bool scaled = a.scale != nullptr;
+  auto combine = [&](float* st) {           // operand of the scaled operators: x * scale
+    if (!scaled) return;
+    for (int hp = threadIdx.x; hp < STRIP_HP; hp += STRIP_THREADS) st[hp] *= st[STRIP_HP + hp];
+  };
+  auto epi = [&](int bx, int by, int lx, int ly0, const float (&vi)[STRIP_P], const float (&acc)[STRIP_P]) {
+    const int x = bx + lx;
+#pragma unroll
+    for (int j = 0; j < STRIP_P; ++j) {
+      const int y = by + ly0 + j;
+      if (x < nx && y < ny) {
+        const int64_t i = (int64_t)y * nx + x;
+        const float yv = scaled ? a.scale[i] * acc[j] : acc[j];
+        a.Y[i * a.ldy] = yv;
+        if (a.dots) dsum = fmaf(scaled ? a.X[i * a.ldx] : vi[j], yv, dsum);
+      }
+    }
+  };
+  strip_run<WM, 3, true>(g, a.wf, a.n, src, ld, 2, combine, epi);
+  if (a.dots) {
+    const float w = warp_sum(dsum);
+    if ((threadIdx.x & 31) == 0) atomicAdd(a.dots, (double)w);
   }
 }
 
@@ -632,6 +667,33 @@ static int launch_apply_fast_w(const bf_graph* g, const ApplyArgs<float>& a, cud
   return launch_apply_fast<SH, K, true>(g, a, s);
 }
 
+static int strip_occupancy(const void* fn) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, STRIP_THREADS, STRIP_SMEM_BYTES) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  return per;
+}
+
+template <int WM>
+static int launch_apply1_strip(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  static int per_sm = 0;
+  if (per_sm == 0) per_sm = strip_occupancy((const void*)k_apply1_strip<WM>);
+  const int64_t ntiles = (int64_t)strip_tiles_x(g->nx) * strip_tiles_y(g->ny);
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms());
+  BF_LAUNCH(k_apply1_strip<WM><<<grid, STRIP_THREADS, STRIP_SMEM_BYTES, s>>>(g->gf, a));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
+static int launch_apply1_strip_w(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  switch (g->p.weight_mode) {
+    case BF_W_STORED_F32: return launch_apply1_strip<BF_W_STORED_F32>(g, a, s);
+    case BF_W_STORED_BF16: return launch_apply1_strip<BF_W_STORED_BF16>(g, a, s);
+  }
+  return launch_apply1_strip<BF_W_ONTHEFLY>(g, a, s);
+}
+
 // Returns 1 when it launched the specialised kernel for this chunk width.
 template <class SH>
 static int apply_fast_shape(const bf_graph* g, int K, const ApplyArgs<float>& a, cudaStream_t s, int* rc) {
@@ -647,6 +709,10 @@ static int apply_fast_shape(const bf_graph* g, int K, const ApplyArgs<float>& a,
 
 static int try_apply_fast(const bf_graph* g, int K, const ApplyArgs<float>& a, cudaStream_t s, int* rc) {
   if (!(a.op == BF_OP_L || a.op == BF_OP_NSYM || a.op == BF_OP_NDIAGL || a.op == BF_OP_DINV_W)) return 0;
+  if (fast_shape(g) == FAST_R3_2D && K == 1 && a.op != BF_OP_DINV_W) {
+    *rc = launch_apply1_strip_w(g, a, s);
+    return 1;
+  }
   if (fast_shape(g) == FAST_R3_2D && !a.dots && a.op != BF_OP_DINV_W) {
     switch (K) {
       case 4: *rc = launch_apply_rb_w<4>(g, a, s); return 1;

@@ -6,7 +6,7 @@ import torch
 
 from oracle import solvers
 from oracle.graph import Graph
-from tests.gpu_helpers import (bf, dev, host, image_case, make_pair, rel_l2, signal_case,
+from tests.gpu_helpers import (TOL_F32, bf, dev, host, image_case, make_pair, rel_l2, signal_case,
                                tol_for)
 
 pytestmark = pytest.mark.gpu
@@ -338,3 +338,18 @@ def test_graph_update_rejects_and_reports():
     bf().graph_update(G, dev(g))                                     # a valid guide recovers it
     H = bf().bf_weights(dev(g), 3, 2.0, 0.08)
     assert torch.equal(bf().graph_degree(G), bf().graph_degree(H))
+
+
+@pytest.mark.parametrize("mode", ["onthefly", "stored_f32", "stored_bf16"])
+@pytest.mark.parametrize("op", ["L", "NSYM", "NDIAGL"])
+def test_apply_k1_interior_and_border_tiles(mode, op):
+    """One column on an image large enough for unmasked interior tiles (32 x 32 tiles with
+    a radius-3 halo) next to ragged border tiles, with the fused dot x^T y."""
+    _, g = image_case(150, 163, 41)
+    G, O = make_pair(g, 3, 2.0, 0.08, mode=mode)
+    x = np.random.default_rng(3).standard_normal(g.size)
+    xd = dev(x)
+    Y, d = bf().bf_apply(G, op, xd, dots=True)
+    ref = O.apply(op, host(xd))
+    assert rel_l2(host(Y), ref) < TOL_F32
+    assert abs(host(d)[0] - host(xd) @ ref) <= 1e-5 * np.abs(host(xd) * ref).sum()
