@@ -685,9 +685,10 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
 
 def run_case(args):
     """Launch one kernel family of the timed step a few times on the benchmark workload, for
-    an ncu capture (no timing, no JSON line): `apply` (k = 16 operator), `cg` (the CG
-    filter), `lobpcg` (one LOBPCG run), `guided` (the guided filter's L at k = 16, window
-    5 x 5, eps 0.01)."""
+    an ncu capture (no timing, no JSON line): `apply` (k = 16 operator), `apply1` (k = 1
+    operator in the --case-weights mode), `cg` (the CG filter, --case-weights mode),
+    `lobpcg` (one LOBPCG run), `guided` (the guided filter's L at k = 16, window 5 x 5,
+    eps 0.01)."""
     import numpy as np
     import torch
 
@@ -702,9 +703,16 @@ def run_case(args):
         Y = torch.empty_like(X)
         for _ in range(args.steps):
             bf.bf_apply(G, "L", X, Y=Y)
-    elif args.case == "cg":
+    elif args.case == "apply1":
+        Gw = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"], weight_mode=args.case_weights)
+        x = torch.randn(noisy.size, device="cuda")
+        y = torch.empty_like(x)
         for _ in range(args.steps):
-            bf.cg_filter(G, guide.view(-1), w["cg_iters"], sync=False)
+            bf.bf_apply(Gw, "L", x, Y=y)
+    elif args.case == "cg":
+        Gw = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"], weight_mode=args.case_weights)
+        for _ in range(args.steps):
+            bf.cg_filter(Gw, guide.view(-1), w["cg_iters"], sync=False)
     elif args.case == "guided":
         Gg = bf.guided_graph(guide, 2, 1e-2)
         X = torch.randn(noisy.size, 16, device="cuda")
@@ -745,8 +753,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-CG, re-guided and guided-filter measurements")
-    ap.add_argument("--case", choices=["apply", "cg", "lobpcg", "guided"], default=None,
+    ap.add_argument("--case", choices=["apply", "apply1", "cg", "lobpcg", "guided"], default=None,
                     help="only launch one kernel family (for profiler captures)")
+    ap.add_argument("--case-weights", default="onthefly", choices=["onthefly", "stored_f32", "stored_bf16"],
+                    help="weight mode of the graph for --case apply1 / cg")
     ap.add_argument("--case-side", type=int, default=0, help="image side for --case")
     args = ap.parse_args()
     if args.case:

@@ -15,6 +15,7 @@
 #include "bf_internal.cuh"
 #include "bf_window_fast.cuh"
 #include "bf_strip.cuh"
+#include "bf_hrun.cuh"
 
 // ================================================================== errors
 static thread_local std::string g_last_error;
@@ -336,6 +337,40 @@ __global__ void __launch_bounds__(STRIP_THREADS, 2) k_apply1_strip(const Geom<fl
     }
   };
   strip_run<WM, 3, true>(g, a.wf, a.n, src, ld, 2, combine, epi);
+  if (a.dots) {
+    const float w = warp_sum(dsum);
+    if ((threadIdx.x & 31) == 0) atomicAdd(a.dots, (double)w);
+  }
+}
+
+// One column (k = 1) with stored weights through the 7 x 7 window by horizontal runs
+// (bf_hrun.cuh): L-type operators, optional fused dot x^T y.  Needs nx % 4 == 0 and a
+// contiguous operand.
+template <int WM>
+__global__ void __launch_bounds__(HRUN_THREADS, 3) k_apply1_hrun(const Geom<float> g, const ApplyArgs<float> a) {
+  const int nx = g.nx, ny = g.ny;
+  float dsum = 0.0f;
+  const bool scaled = a.scale != nullptr;
+  const float* src[2] = {a.X, a.scale};
+  auto combine = [&](float* st) {           // operand of the scaled operators: x * scale
+    if (!scaled) return;
+    for (int e = threadIdx.x; e < HRUN_HP; e += HRUN_THREADS) st[e] *= st[HRUN_HP + e];
+  };
+  auto epi = [&](int bx, int by, int cx, int ry, const float (&vi)[HRUN_P], const float (&acc)[HRUN_P]) {
+    const int y = by + ry;
+    if (y >= ny) return;
+#pragma unroll
+    for (int j = 0; j < HRUN_P; ++j) {
+      const int x = bx + cx + j;
+      if (x < nx) {
+        const int64_t i = (int64_t)y * nx + x;
+        const float yv = scaled ? a.scale[i] * acc[j] : acc[j];
+        a.Y[i * a.ldy] = yv;
+        if (a.dots) dsum = fmaf(scaled ? a.X[i] : vi[j], yv, dsum);
+      }
+    }
+  };
+  hrun_run<WM, 2>(nx, ny, a.wf, a.n, src, combine, epi);
   if (a.dots) {
     const float w = warp_sum(dsum);
     if ((threadIdx.x & 31) == 0) atomicAdd(a.dots, (double)w);
@@ -686,7 +721,28 @@ static int launch_apply1_strip(const bf_graph* g, const ApplyArgs<float>& a, cud
   return BF_OK;
 }
 
+template <int WM>
+static int launch_apply1_hrun(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply1_hrun<WM>, HRUN_THREADS, HRUN_SMEM_BYTES) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const int64_t ntiles = (int64_t)((g->nx + HRUN_TW - 1) / HRUN_TW) * ((g->ny + HRUN_TH - 1) / HRUN_TH);
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms());
+  BF_LAUNCH(k_apply1_hrun<WM><<<grid, HRUN_THREADS, HRUN_SMEM_BYTES, s>>>(g->gf, a));
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
+}
+
 static int launch_apply1_strip_w(const bf_graph* g, const ApplyArgs<float>& a, cudaStream_t s) {
+  // stored weights by horizontal runs when the rows are whole 16-byte vectors of the planes
+  if (g->p.weight_mode != BF_W_ONTHEFLY && g->nx % 4 == 0 && a.ldx == 1 && ((uintptr_t)g->wf & 15) == 0) {
+    if (g->p.weight_mode == BF_W_STORED_BF16) return launch_apply1_hrun<BF_W_STORED_BF16>(g, a, s);
+    return launch_apply1_hrun<BF_W_STORED_F32>(g, a, s);
+  }
   switch (g->p.weight_mode) {
     case BF_W_STORED_F32: return launch_apply1_strip<BF_W_STORED_F32>(g, a, s);
     case BF_W_STORED_BF16: return launch_apply1_strip<BF_W_STORED_BF16>(g, a, s);

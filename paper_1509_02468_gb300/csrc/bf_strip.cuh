@@ -39,7 +39,7 @@ __device__ __forceinline__ float strip_ex2(float a) {
 // Stored weight idx of mode WM (BF_W_STORED_F32 or BF_W_STORED_BF16).
 template <int WM>
 __device__ __forceinline__ float strip_ld_w(const void* wf, int64_t idx) {
-  if (WM == BF_W_STORED_BF16) return __bfloat162float(((const __nv_bfloat16*)wf)[idx]);
+  if (WM == BF_W_STORED_BF16) return __uint_as_float((unsigned)__ldg((const unsigned short*)wf + idx) << 16);
   return __ldg((const float*)wf + idx);
 }
 

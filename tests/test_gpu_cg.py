@@ -125,3 +125,17 @@ def test_cg_fixed_count_captured_in_a_cuda_graph():
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
     assert rel_l2(host(out), solvers.cg(O, g.reshape(-1).astype(np.float64), 20)["x"]) < 1e-5
+
+
+@pytest.mark.parametrize("mode", ["stored_f32", "stored_bf16"])
+@pytest.mark.parametrize("shape", [(131, 160), (96, 123)])
+def test_cg_stored_weights(mode, shape):
+    """Stored weights through the strip kernels, an even and an odd width: the result equals
+    the oracle of the stored operator."""
+    _, g = image_case(*shape, 33)
+    G, O = make_pair(g, 3, 2.0, 0.08, mode=mode)
+    x, info, h = bf().cg_filter(G, dev(g), 25, hist=True)
+    ref = solvers.cg(O, g.reshape(-1).astype(np.float64), 25)
+    assert info.iters == 25
+    assert rel_l2(host(x), ref["x"]) < 1e-5
+    np.testing.assert_allclose(host(h).reshape(-1, 2)[:, 0], ref["alpha"], rtol=1e-5)

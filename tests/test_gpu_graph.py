@@ -340,12 +340,14 @@ def test_graph_update_rejects_and_reports():
     assert torch.equal(bf().graph_degree(G), bf().graph_degree(H))
 
 
+@pytest.mark.parametrize("shape", [(150, 163), (137, 168)])
 @pytest.mark.parametrize("mode", ["onthefly", "stored_f32", "stored_bf16"])
 @pytest.mark.parametrize("op", ["L", "NSYM", "NDIAGL"])
-def test_apply_k1_interior_and_border_tiles(mode, op):
+def test_apply_k1_interior_and_border_tiles(shape, mode, op):
     """One column on an image large enough for unmasked interior tiles (32 x 32 tiles with
-    a radius-3 halo) next to ragged border tiles, with the fused dot x^T y."""
-    _, g = image_case(150, 163, 41)
+    a radius-3 halo) next to ragged border tiles, with the fused dot x^T y; an odd and an
+    even width."""
+    _, g = image_case(*shape, 41)
     G, O = make_pair(g, 3, 2.0, 0.08, mode=mode)
     x = np.random.default_rng(3).standard_normal(g.size)
     xd = dev(x)
