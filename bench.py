@@ -9,9 +9,12 @@ on the host and resident on the device before the timed region; L2 (126 MB) is f
 writing a 256 MB buffer between timed steps, and each step is timed with CUDA events on
 the launching stream.
 
-Extra keys: `roofline` for the bilateral operator kernel (L X on a k = 16 block, timed alone
-with an L2 flush before each launch; bound by the FP32 pipe, with its HBM fraction beside),
-`roofline_2048` (the same on a 2048 x 2048 image, X and Y far larger than L2),
+Extra keys: `roofline` for the operator bf_apply in its HBM-bound form (L x on one column
+with stored FP32 weights on a 2048 x 2048 image, timed alone with an L2 flush before each
+launch), `apply_modes_2048` (the operator per weight mode and k in {1, 4, 16} against
+HBM), `cg_2048` (CG 50 on the 2048 x 2048 image against HBM), `roofline_apply16_512` (L X
+on a k = 16 block of the step's image, bound by the FP32 pipe), `roofline_2048` (the same
+on a 2048 x 2048 image, X and Y far larger than L2),
 `roofline_dominant` (the Rayleigh-Ritz solve, the largest share of the step's GPU time),
 `batched` (CG on 256 uneven instances, one CUDA graph, against plain calls),
 `cpu_baseline` (the FP64 CPU oracle, one thread, on
@@ -298,12 +301,18 @@ def run_gpu(args):
     peak, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = nsm * FP32_LANES_PER_SM * _sm_max_ghz() * 1e9      # FP32 lane-ops per second
-    roofline = _apply_roofline(bf, torch, stream, flush, guide, w, 16, peak, peak_src, alu_peak,
-                               TRAFFIC_APPLY_512)
+    roofline_512 = _apply_roofline(bf, torch, stream, flush, guide, w, 16, peak, peak_src, alu_peak,
+                                   TRAFFIC_APPLY_512)
     _, noisy2k = synth.polygon_image(2048, 2048, w["seed"], noise=w["noise"])
-    roofline_2048 = _apply_roofline(bf, torch, stream, flush, torch.as_tensor(noisy2k).cuda(), w, 16,
+    guide2k = torch.as_tensor(noisy2k).cuda()
+    roofline_2048 = _apply_roofline(bf, torch, stream, flush, guide2k, w, 16,
                                     peak, peak_src, alu_peak, TRAFFIC_APPLY_2048)
-    del noisy2k
+    # the operator per weight mode and block width on the 2048 x 2048 image, and the k = 1
+    # apply with stored FP32 weights (the HBM-bound form) as the line's roofline
+    apply_modes = _apply_modes(bf, torch, stream, flush, guide2k, w, peak, peak_src)
+    roofline = apply_modes.pop("roofline")
+    cg_2048 = _cg_roofline(bf, torch, stream, flush, guide2k, w, peak, peak_src)
+    del noisy2k, guide2k
     rr_ms = _time_rr(bf, torch, stream, flush)
     rr_flops = 2.0 * RR_FP64_FMA
     rr_peak = 2.0 * 2.0 * _sm_max_ghz()      # GFLOP/s: one SM, 2 FP64 FMA per clock
@@ -384,7 +393,8 @@ def run_gpu(args):
                            "lobpcg_iters": w["lob_iters"], "weights": "on-the-fly fp32",
                            "l2": "flushed between steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "roofline_2048": roofline_2048,
+                "roofline": roofline, "apply_modes_2048": apply_modes, "cg_2048": cg_2048,
+                "roofline_apply16_512": roofline_512, "roofline_2048": roofline_2048,
                 "roofline_dominant": roofline_rr, "cpu_baseline": cpu, "err": err,
                 "batched": batched, "reguided": reguided, "guided": guided,
                 "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
@@ -418,6 +428,82 @@ def _sm_max_ghz():
             return float(json.load(f)["sm_max_mhz"]) / 1e3
     except Exception:
         return 2.07
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k = 1 stored-FP32 apply on the
+# 2048 x 2048 image (ncu capture of `bench.py --case apply1 --case-side 2048
+# --case-weights stored_f32`)
+TRAFFIC_APPLY1_F32_2048 = 437919232
+# algorithmic bytes per pixel of L x on one column per weight mode: x in, y out, and the
+# guide (on the fly) or the 24 stored forward weights of the 7 x 7 window
+APPLY_W_BYTES = {"onthefly": 4, "stored_f32": 96, "stored_bf16": 48}
+# algorithmic bytes per pixel of one CG iteration (Jacobi): direction pass s, p_old, guide
+# in and p, q out; update pass q, d, p, x, s in and x, s out
+CG_BYTES_PER_PX = 48
+
+
+def _timed_ms(torch, stream, flush, fn, reps):
+    """Mean CUDA-event time (ms) of fn on `stream`, L2 flushed before every launch."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts)
+
+
+def _apply_modes(bf, torch, stream, flush, guide, w, peak, peak_src, reps=20):
+    """L X on the 2048 x 2048 image for each weight mode and k in {1, 4, 16}: time and
+    algorithmic bytes ((8k + weight bytes) per pixel) against the measured HBM peak.  Also
+    returns, under "roofline", the k = 1 stored-FP32 entry in the line's roofline form."""
+    ny, nx = guide.shape
+    n = ny * nx
+    out = {"image": f"{ny}x{nx}", "window": "7x7", "bytes_per_px": "8k + weights (onthefly 4, "
+           "stored_f32 96, stored_bf16 48)", "peak_gbs": peak, "peak_source": peak_src}
+    for mode in ("onthefly", "stored_f32", "stored_bf16"):
+        G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"], weight_mode=mode)
+        for k in (1, 4, 16):
+            X = torch.randn(n, k, device="cuda") if k > 1 else torch.randn(n, device="cuda")
+            Y = torch.empty_like(X)
+            ms = _timed_ms(torch, stream, flush, lambda: bf.bf_apply(G, "L", X, Y=Y), reps)
+            byts = (8 * k + APPLY_W_BYTES[mode]) * n
+            gbs = byts / (ms * 1e-3) / 1e9
+            out[f"{mode}_k{k}"] = {"us": 1e3 * ms, "gbs": gbs, "frac_hbm": gbs / peak}
+            del X, Y
+        G.free()
+    e = out["stored_f32_k1"]
+    byts = (8 + APPLY_W_BYTES["stored_f32"]) * n
+    out["roofline"] = {"kernel": f"k_apply1_hrun<stored f32> (L x, 7x7, one column, {ny}x{nx})",
+                       "bound": "hbm", "achieved": e["gbs"], "peak": peak, "unit": "GB/s",
+                       "frac": e["frac_hbm"], "traffic": TRAFFIC_APPLY1_F32_2048,
+                       "algorithmic_bytes": byts, "ms_per_launch": e["us"] / 1e3,
+                       "peak_source": peak_src,
+                       "note": "bf_apply with stored FP32 weights, k = 1: the operator's HBM-bound form; "
+                               "weights on the fly move 12 B/px and are faster at every k on GB300"}
+    return out
+
+
+def _cg_roofline(bf, torch, stream, flush, guide, w, peak, peak_src, iters=50, reps=3):
+    """CG (Jacobi, on-the-fly weights) on the 2048 x 2048 image: time per iteration and its
+    algorithmic bytes (CG_BYTES_PER_PX per pixel) against the measured HBM peak."""
+    G = bf.bf_weights(guide, w["radius"], w["sigma_s"], w["sigma_r"])
+    x0 = guide.reshape(-1)
+    xo = torch.empty_like(x0)
+    ms = _timed_ms(torch, stream, flush, lambda: bf.cg_filter(G, x0, iters, out=xo, sync=False), reps)
+    G.free()
+    n = x0.numel()
+    gbs = CG_BYTES_PER_PX * n * iters / (ms * 1e-3) / 1e9
+    return {"image": f"{guide.shape[0]}x{guide.shape[1]}", "iters": iters, "ms": ms,
+            "us_per_iter": 1e3 * ms / iters, "mpix_s": n / (ms * 1e-3) / 1e6,
+            "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "bytes_per_px_iter": CG_BYTES_PER_PX, "peak_source": peak_src}}
 
 
 def _apply_roofline(bf, torch, stream, flush, guide, w, k, peak, peak_src, alu_peak, traffic):
