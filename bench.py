@@ -809,7 +809,7 @@ def run_case(args):
         X0 = torch.as_tensor(synth.block_start(noisy.reshape(-1), w["lob_k"], seed=w["seed"],
                                                dtype=np.float32)).cuda()
         for _ in range(args.steps):
-            bf.lobpcg_filter(G, X0, w["lob_iters"], want_X=False, sync=False)
+            bf.lobpcg_filter(G, X0, w["lob_iters"], want_X=False, sync=False, gram=args.case_gram)
     torch.cuda.synchronize()
     print(f"case {args.case} side {side}: {bf.launch_count()} launches")
     return 0
@@ -841,6 +841,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-CG, re-guided and guided-filter measurements")
     ap.add_argument("--case", choices=["apply", "apply1", "cg", "lobpcg", "guided"], default=None,
                     help="only launch one kernel family (for profiler captures)")
+    ap.add_argument("--case-gram", default="fp32", choices=["fp32", "bf16", "bf16x3", "bf16x6"],
+                    help="Gram precision of the LOBPCG run for --case lobpcg")
     ap.add_argument("--case-weights", default="onthefly", choices=["onthefly", "stored_f32", "stored_bf16"],
                     help="weight mode of the graph for --case apply1 / cg")
     ap.add_argument("--case-side", type=int, default=0, help="image side for --case")

@@ -73,6 +73,10 @@ extern "C" {
 #define BF_GRAM_FP32      0   /* FP32 products in runs of 16 pixels, folded into FP64     */
 #define BF_GRAM_BF16      1   /* tensor cores (tcgen05): BF16 operands, FP32 accumulation */
 #define BF_GRAM_BF16X3    2   /* tensor cores: x = hi + lo in BF16, hi*hi + hi*lo + lo*hi */
+#define BF_GRAM_BF16X6    3   /* tensor cores: x = hi + mid + lo in BF16 (24 bits), six   */
+                              /* products, accumulators folded per 64 pixels into         */
+                              /* double-float sums; bases of m = 3k <= 48 columns (k <= 16), */
+                              /* wider ones use BF_GRAM_FP32                               */
 
 #define BF_CG_CONVERGED   1   /* bf_info.status: stopped by s^T r = 0 or by tol           */
 #define BF_CG_BREAKDOWN   2   /* bf_info.status: stopped by p^T q <= 0                    */

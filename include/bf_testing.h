@@ -31,12 +31,14 @@ int bf_rayleigh_ritz(const double* G, int m, int k, int m_nop, double* C, double
 /* The tensor-core Gram products of the LOBPCG Rayleigh-Ritz step (Algorithm 3): with
  * S = [S0 S1 S2] and AS = [AS0 AS1 AS2] (the first nblk blocks, each n x k pixel-major
  * float) and B = diag(b) (b NULL: I), writes G[0] = S^T AS and G[1] = S^T B S (double,
- * [2][m][m], m = nblk k) computed by tcgen05 MMAs on BF16 operands (split = 0) or on
- * split-BF16 operands hi + lo with hi*hi + hi*lo + lo*hi (split = 1), FP32 accumulation.
- * Needs k % 4 == 0 and m <= 96.  Allocates scratch and synchronises the stream. */
+ * [2][m][m], m = nblk k) computed by tcgen05 MMAs in mode BF_GRAM_BF16 (BF16 operands),
+ * BF_GRAM_BF16X3 (hi + lo, hi*hi + hi*lo + lo*hi) or BF_GRAM_BF16X6 (hi + mid + lo, six
+ * products, per-chunk folding into double-float sums; m <= 48), FP32 accumulation in
+ * tensor memory.  Needs k % 4 == 0 and m <= 96.  Allocates scratch and synchronises the
+ * stream. */
 int bf_gram_tc_test(const float* S0, const float* S1, const float* S2, const float* AS0,
                     const float* AS1, const float* AS2, const float* b, int nblk, int k,
-                    int64_t n, int split, double* G, void* stream);
+                    int64_t n, int mode, double* G, void* stream);
 
 /* The bounded device wait used by the tensor-core Gram (an mbarrier wait that gives up
  * after a number of polls, so that a kernel whose producer never signals returns an error

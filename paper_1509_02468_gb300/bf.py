@@ -23,7 +23,7 @@ OPS = {"W": 0, "L": 1, "DINV_W": 2, "D": 3, "NSYM": 4, "NDIAGL": 5}
 PRECONDS = {"jacobi": 0, "identity": 1, "net": 2}
 BETAS = {"flexible": 0, "printed": 1}
 PENCILS = {"D": 0, "I": 1}
-GRAMS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+GRAMS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
 STATUS = {0: "ran", 1: "converged", 2: "breakdown"}
 
 
@@ -482,14 +482,16 @@ def wait_test(iters: int, arrive: bool, stream=None):
     _check(_lib.bf_wait_test(int(iters), int(bool(arrive)), _stream(stream)))
 
 
-def gram_tc(S_blocks, AS_blocks, b=None, split: bool = False, stream=None):
+def gram_tc(S_blocks, AS_blocks, b=None, split: bool = False, stream=None, mode: str | None = None):
     """Tensor-core Gram (include/bf_testing.h): returns (S^T AS, S^T B S) as float64 tensors
-    for lists of 1..3 pixel-major float32 blocks of shape (n, k)."""
+    for lists of 1..3 pixel-major float32 blocks of shape (n, k).  mode: "bf16", "bf16x3"
+    or "bf16x6" (default: "bf16x3" if split else "bf16")."""
     nblk = len(S_blocks)
     n, k = S_blocks[0].shape
     m = nblk * k
+    mode = mode or ("bf16x3" if split else "bf16")
     G = torch.empty((2, m, m), dtype=torch.float64, device=S_blocks[0].device)
     Sp = [_ptr(x) for x in S_blocks] + [None] * (3 - nblk)
     Ap = [_ptr(x) for x in AS_blocks] + [None] * (3 - nblk)
-    _check(_lib.bf_gram_tc_test(*Sp, *Ap, _ptr(b), nblk, k, n, int(split), _ptr(G), _stream(stream)))
+    _check(_lib.bf_gram_tc_test(*Sp, *Ap, _ptr(b), nblk, k, n, GRAMS[mode], _ptr(G), _stream(stream)))
     return G[0], G[1]

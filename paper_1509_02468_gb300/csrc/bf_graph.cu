@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <map>
 #include <set>
 #include <vector>
 
@@ -38,14 +39,15 @@ extern "C" uint64_t bf_launch_count(void) { return (uint64_t)g_launches.load(); 
 
 int bf_smem_attr(const void* fn, int bytes, const char* what) {
   static std::mutex mu;
-  static std::set<std::pair<int, const void*>> done;
+  static std::map<std::pair<int, const void*>, int> done;   // largest size set so far
   int dev = 0;
   BF_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
-  if (done.count({dev, fn})) return BF_OK;
+  auto it = done.find({dev, fn});
+  if (it != done.end() && it->second >= bytes) return BF_OK;
   const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return bf_cuda_fail(e, what);
-  done.insert({dev, fn});
+  done[{dev, fn}] = bytes;
   return BF_OK;
 }
 

@@ -26,7 +26,8 @@ int bf_fail(int code, const std::string& msg);
 int bf_cuda_fail(cudaError_t e, const char* what);
 
 // Allow kernel `fn` `bytes` of dynamic shared memory on the current device.  The attribute
-// belongs to the device's context, so it is set once per (device, kernel), under a lock.
+// belongs to the device's context: it is set per (device, kernel), under a lock, again
+// whenever a larger size is asked for.
 int bf_smem_attr(const void* fn, int bytes, const char* what);
 
 // Every kernel launch of the library goes through BF_LAUNCH, which counts it (the count

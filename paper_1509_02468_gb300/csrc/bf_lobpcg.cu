@@ -24,7 +24,7 @@ int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, 
 int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
                      int64_t ldz, cudaStream_t s, const int* stop);
 int bf_gram_tc(const float* const* S, const float* const* AS, const float* b, int nblk, int k, int64_t n,
-               bool split, float* partials, int grid, double* G, const int* status, int* err, cudaStream_t s);
+               int mode, double* partials, int grid, double* G, const int* status, int* err, cudaStream_t s);
 int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
                  int64_t ldy, double* dots, cudaStream_t s);
 
@@ -948,14 +948,15 @@ static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T
 }
 
 // The Gram products: FP32 kernel, or (FP32 graphs, k % 4 == 0) the tensor-core kernel in
-// BF16 or split-BF16.
+// BF16, two-way or three-way split BF16 (the latter for m <= 48; wider bases fall back to
+// the FP32 kernel).
 template <typename T>
 static int gram_step(const GramArgs<T>& ga, int gram_mode, int ggrid, double* part, double* G, LobState* st,
                      cudaStream_t s) {
   if (sizeof(T) == 4 && gram_mode != BF_GRAM_FP32) {
     const int rc = bf_gram_tc(reinterpret_cast<const float* const*>(ga.S), reinterpret_cast<const float* const*>(ga.AS),
-                              reinterpret_cast<const float*>(ga.b), ga.nblk, ga.k, ga.n, gram_mode == BF_GRAM_BF16X3,
-                              reinterpret_cast<float*>(part), ggrid, G, &st->status, &st->status, s);
+                              reinterpret_cast<const float*>(ga.b), ga.nblk, ga.k, ga.n, gram_mode, part, ggrid, G,
+                              &st->status, &st->status, s);
     if (rc != BF_EINVAL) return rc;
   }
   const int rc = run_gram<T>(ga, ggrid, s);
@@ -1150,7 +1151,7 @@ extern "C" int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, in
   if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4 || g->kind != BF_KIND_BILATERAL))
     return bf_fail(BF_EINVAL, "lobpcg_filter: BF_PRECOND_NET needs a net and an FP32 bilateral graph");
   if (!(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "lobpcg_filter: tol must be >= 0");
-  if (o.gram != BF_GRAM_FP32 && o.gram != BF_GRAM_BF16 && o.gram != BF_GRAM_BF16X3)
+  if (o.gram != BF_GRAM_FP32 && o.gram != BF_GRAM_BF16 && o.gram != BF_GRAM_BF16X3 && o.gram != BF_GRAM_BF16X6)
     return bf_fail(BF_EINVAL, "lobpcg_filter: bad gram mode");
   cudaStream_t s = (cudaStream_t)stream;
   if (g->esize == 4)
