@@ -754,6 +754,7 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
     l0 = bf.launch_count()
     ms_b = timed(lambda: B.cg(x0s, kmax, outs=outs, sync=False))
     lb = (bf.launch_count() - l0) / (reps + 1)
+    ms_pers = timed(lambda: B.cg_persistent(x0s, kmax, outs=outs))
 
     def plain():
         for G, x, o in zip(graphs, x0s, outs):
@@ -764,6 +765,9 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
                         "lengths log-uniform in [1e3, 1e6]; CG 50 (Jacobi), FP32",
             "samples": total, "cg_iters": kmax,
             "batched_mpix_s": total / (ms_b * 1e-3) / 1e6, "batched_ms": ms_b,
+            "persistent_mpix_s": total / (ms_pers * 1e-3) / 1e6, "persistent_ms": ms_pers,
+            "persistent_note": "one cooperative launch, bounded grid barriers between phases; "
+                               "includes the host read of the barrier flag",
             "plain_mpix_s": total / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,
             "batched_kernels_per_run": lb, "tile_shape_timings_ms": tune_ms,
             "tile_shape": ["32x8", "64x4", "16x16"][variant]}

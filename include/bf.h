@@ -317,6 +317,14 @@ int bf_batch_free(bf_batch* b);
  * or a host array of count bf_info, filled after synchronising the stream. */
 int bf_batch_cg(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
                 const bf_cg_opts* opts, bf_info* infos, void* stream);
+/* The same run as bf_batch_cg in one persistent, cooperative launch: every CTA walks the
+ * work lists of all instances phase by phase (start, then per iteration the direction and
+ * the update jobs), the phases separated by a grid-wide barrier in device memory.  Same
+ * jobs and reduction order as bf_batch_cg, so the results are identical.  Every barrier
+ * wait is bounded (1 s): if one gives up, the kernel returns and the call reports
+ * BF_ETIMEOUT (the instance vectors are then undefined).  Synchronises the stream. */
+int bf_batch_cg_persistent(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
+                           const bf_cg_opts* opts, bf_info* infos, void* stream);
 /* Autotuner: time `iters` iterations with each candidate tile shape of the image class
  * (32 x 8, 64 x 4, 16 x 16 pixels) on these vectors and keep the fastest; ms_out (host,
  * 3 floats) receives the timings.  Synchronises the stream. */

@@ -49,6 +49,13 @@ int bf_gram_tc_test(const float* S0, const float* S1, const float* S2, const flo
  * intact.  Synchronises the stream. */
 int bf_wait_test(int iters, int arrive, void* stream);
 
+/* bf_batch_cg_persistent (Jacobi, flexible beta, no shift) with CTA 0 leaving before its
+ * first grid barrier, so that every other CTA's bounded wait runs out: returns
+ * BF_ETIMEOUT and leaves the context usable.  Needs the batch type from bf.h. */
+struct bf_batch;
+int bf_batch_barrier_test(struct bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,8 @@ def _load():
         "bf_batch_free": [vp],
         "bf_batch_cg": [vp, vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, vp],
         "bf_batch_tune": [vp, vp, vp, i32, vp, vp],
+        "bf_batch_cg_persistent": [vp, vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, vp],
+        "bf_batch_barrier_test": [vp, vp, vp, i32, vp],
         "bf_batch_tiles": [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
@@ -462,6 +464,23 @@ class Batch:
         _check(_lib.bf_batch_cg(self.handle, self._ptrs(x0s), self._ptrs(outs), kmax, ctypes.byref(o),
                                 infos, _stream(stream)))
         return outs, ([_info(i) for i in infos] if infos is not None else None)
+
+    def cg_persistent(self, x0s, kmax: int, precond: str = "jacobi", beta: str = "flexible",
+                      shift: float = 0.0, tol: float = 0.0, outs=None, stream=None):
+        """The same run in one persistent cooperative launch (bf_batch_cg_persistent);
+        synchronises.  Returns (outs, infos)."""
+        outs = [torch.empty_like(x) for x in x0s] if outs is None else outs
+        o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS[beta], shift=shift, tol=tol, hist=None, net=None)
+        infos = (bf_info * len(x0s))()
+        _check(_lib.bf_batch_cg_persistent(self.handle, self._ptrs(x0s), self._ptrs(outs), kmax, ctypes.byref(o),
+                                           infos, _stream(stream)))
+        return outs, [_info(i) for i in infos]
+
+    def barrier_test(self, x0s, kmax: int = 2, outs=None, stream=None):
+        """Persistent run with one CTA that never reaches the first grid barrier
+        (include/bf_testing.h): raises BFError(BF_ETIMEOUT)."""
+        outs = [torch.empty_like(x) for x in x0s] if outs is None else outs
+        _check(_lib.bf_batch_barrier_test(self.handle, self._ptrs(x0s), self._ptrs(outs), kmax, _stream(stream)))
 
     def tune(self, x0s, iters: int = 5, outs=None, stream=None):
         """Autotune the image tile shape; returns the timings (ms) of the three candidates."""

@@ -110,14 +110,12 @@ __device__ __forceinline__ void bstage(const BInst& in, int bx, int by, float* s
 
 // r = -L x0, x = x0, s = T r; sums s^T r, s^T s, r^T r, x0^T x0; state of the instance.
 template <class SH>
-__global__ void __launch_bounds__(BF_THREADS) k_bcg_init(const Geom<float> g, const BArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void bcg_init_job(const Geom<float>& g, const BArgs& a, int job, unsigned char* smem) {
   __shared__ double red[4 * (BF_THREADS / 32)];
   __shared__ int last;
   float* sx = reinterpret_cast<float*>(smem);
   float* sg = sx + SH::hp;
   float* sval = sg + SH::hp;
-  const int job = blockIdx.x;
   const BJob jb = a.jobs[job];
   BInst& in = a.inst[jb.inst];
   const int lx = threadIdx.x % SH::tw, ly = threadIdx.x / SH::tw;
@@ -163,14 +161,20 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_init(const Geom<float> g, co
   }
 }
 
-// p = s + beta p_old on tile + halo (first iteration: p = s), q = (L + shift I) p, p^T q, alpha.
 template <class SH>
-__global__ void __launch_bounds__(BF_THREADS) k_bcg_dir(const Geom<float> g, const BArgs a) {
-  const int job = blockIdx.x;
+__global__ void __launch_bounds__(BF_THREADS) k_bcg_init(const Geom<float> g, const BArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bcg_init_job<SH>(g, a, blockIdx.x, smem);
+}
+
+// p = s + beta p_old on tile + halo (first iteration: p = s), q = (L + shift I) p, p^T q, alpha.
+// (An instance's status changes only in the last block of its jobs in a phase, after all
+// others have finished theirs, so every block reads the same value.)
+template <class SH>
+__device__ __forceinline__ void bcg_dir_job(const Geom<float>& g, const BArgs& a, int job, unsigned char* smem) {
   const BJob jb = a.jobs[job];
   BInst& in = a.inst[jb.inst];
   if (in.st.status != B_RUN) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[BF_THREADS / 32];
   __shared__ int last;
   float* sx = reinterpret_cast<float*>(smem);
@@ -217,11 +221,15 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_dir(const Geom<float> g, con
   }
 }
 
-// x += alpha p, r -= alpha q, s = T r on the tile; sums; beta and the stopping tests.
 template <class SH>
-__global__ void __launch_bounds__(BF_THREADS) k_bcg_update(const BArgs a) {
-  // one block per chunk of up to BUPD_CHUNK consecutive samples of one instance
-  const int job = blockIdx.x;
+__global__ void __launch_bounds__(BF_THREADS) k_bcg_dir(const Geom<float> g, const BArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bcg_dir_job<SH>(g, a, blockIdx.x, smem);
+}
+
+// x += alpha p, r -= alpha q, s = T r on a chunk of up to BUPD_CHUNK consecutive samples of
+// one instance; sums; beta and the stopping tests.
+__device__ __forceinline__ void bcg_update_job(const BArgs& a, int job) {
   const BJob jb = a.jobs[job];
   BInst& in = a.inst[jb.inst];
   if (in.st.status != B_RUN) return;
@@ -258,6 +266,11 @@ __global__ void __launch_bounds__(BF_THREADS) k_bcg_update(const BArgs a) {
   }
 }
 
+template <class SH>
+__global__ void __launch_bounds__(BF_THREADS) k_bcg_update(const BArgs a) {
+  bcg_update_job(a, blockIdx.x);
+}
+
 // candidate tile shapes of the image class (the autotuner's choices)
 typedef WinShapeT<3, 3, false, 32, 8> R3_32x8;
 typedef WinShapeT<3, 3, false, 64, 4> R3_64x4;
@@ -266,6 +279,110 @@ enum { CLS_R3 = 0, CLS_R5 = 1, CLS_X1 = 2, NCLS = 3 };
 #define BUPD_CHUNK 4096           // samples per block of the update kernel (16 per thread)
 #define BTILE_GROUP 8             // consecutive tiles of one row per block of the operator kernels
 const int R3_TW[3] = {32, 64, 16}, R3_TH[3] = {8, 4, 16};
+
+// ---- persistent form: one cooperative launch for the whole run ----------------------------
+// Every CTA walks the work lists of all classes phase by phase (start; then per iteration
+// the direction jobs, then the update jobs), the phases separated by a grid barrier.  The
+// per-instance reductions are those of the per-phase kernels (same jobs, same order), so
+// the results are identical.  The barrier is bounded: a CTA that waits longer than
+// BAR_WAIT_NS records a timeout and leaves; so does every other CTA at its next wait.
+#define BAR_WAIT_NS 1000000000ull      // 1 s
+
+struct BGeoms {
+  Geom<float> g[NCLS];
+};
+
+struct BPArgs {
+  BArgs op[NCLS];                      // operator work lists
+  BArgs up[NCLS];                      // update work lists
+  int njobs[NCLS], nupd[NCLS];
+  int has[NCLS];
+  int kmax;
+  unsigned* bar;                       // [0]: arrivals, [1]: generation
+  int* err;                            // 1: a barrier wait gave up
+  int skip;                            // testing: CTA 0 leaves without arriving at barrier 1
+};
+
+__device__ __forceinline__ unsigned long long b_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier with a bounded wait; returns false (block-uniform) when it gave up or
+// an earlier wait of the run did.
+__device__ bool b_grid_barrier(const BPArgs& pa, int index) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = *(volatile int*)pa.err == 0;
+    if (ok && pa.skip && index == 1 && blockIdx.x == 0) ok = 0;   // testing: never arrives
+    if (ok) {
+      volatile unsigned* gen = pa.bar + 1;
+      const unsigned g0 = *gen;
+      __threadfence();
+      if (atomicAdd(pa.bar, 1u) == gridDim.x - 1) {
+        pa.bar[0] = 0u;
+        __threadfence();
+        atomicAdd(pa.bar + 1, 1u);
+      } else {
+        const unsigned long long t0 = b_now_ns();
+        while (*gen == g0) {
+          if (*(volatile int*)pa.err) {       // another CTA gave up: leave now
+            ok = 0;
+            break;
+          }
+          if (b_now_ns() - t0 > BAR_WAIT_NS) {
+            atomicExch(pa.err, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+template <class SHR3>
+__device__ __forceinline__ void b_phase(const BGeoms& G, const BPArgs& pa, int phase, unsigned char* smem) {
+  for (int c = 0; c < NCLS; ++c) {
+    if (!pa.has[c]) continue;
+    const int nj = phase == 2 ? pa.nupd[c] : pa.njobs[c];
+    for (int job = blockIdx.x; job < nj; job += gridDim.x) {
+      if (phase == 2) {
+        bcg_update_job(pa.up[c], job);
+      } else if (c == CLS_R3) {
+        if (phase == 0) bcg_init_job<SHR3>(G.g[c], pa.op[c], job, smem);
+        else bcg_dir_job<SHR3>(G.g[c], pa.op[c], job, smem);
+      } else if (c == CLS_R5) {
+        if (phase == 0) bcg_init_job<ShapeR5>(G.g[c], pa.op[c], job, smem);
+        else bcg_dir_job<ShapeR5>(G.g[c], pa.op[c], job, smem);
+      } else {
+        if (phase == 0) bcg_init_job<ShapeX1>(G.g[c], pa.op[c], job, smem);
+        else bcg_dir_job<ShapeX1>(G.g[c], pa.op[c], job, smem);
+      }
+      __syncthreads();                 // the job's shared memory is free
+    }
+  }
+}
+
+template <class SHR3>
+__global__ void __launch_bounds__(BF_THREADS) k_bcg_persistent(const __grid_constant__ BGeoms G, const BPArgs pa) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int bi = 0;
+  b_phase<SHR3>(G, pa, 0, smem);
+  if (!b_grid_barrier(pa, ++bi)) return;
+  for (int it = 0; it < pa.kmax; ++it) {
+    b_phase<SHR3>(G, pa, 1, smem);
+    if (!b_grid_barrier(pa, ++bi)) return;
+    b_phase<SHR3>(G, pa, 2, smem);
+    if (it + 1 < pa.kmax && !b_grid_barrier(pa, ++bi)) return;
+  }
+}
 
 }  // namespace
 
@@ -285,6 +402,7 @@ struct bf_batch {
   BJob* d_upd[NCLS];                 // update chunks {instance, first sample, count}
   double* d_part[NCLS];
   void* d_vec;                       // r, s, q, p0, p1 of every instance
+  void* d_bar;                       // persistent run: barrier counters and timeout flag
   std::vector<BInst> h_inst;
   // captured run
   cudaGraphExec_t exec;
@@ -410,6 +528,7 @@ extern "C" int bf_batch_create(const bf_graph* const* graphs, int count, bf_batc
   b->r3_variant = 0;
   b->d_inst = nullptr;
   b->d_vec = nullptr;
+  b->d_bar = nullptr;
   b->exec = nullptr;
   b->graph_kernels = 0;
   b->exec_kmax = -1;
@@ -495,6 +614,7 @@ extern "C" int bf_batch_free(bf_batch* b) {
   }
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_vec) cudaFree(b->d_vec);
+  if (b->d_bar) cudaFree(b->d_bar);
   delete b;
   return BF_OK;
 }
@@ -577,6 +697,104 @@ extern "C" int bf_batch_cg(bf_batch* b, const float* const* x0, float* const* x_
     }
   }
   return BF_OK;
+}
+
+template <class SHR3>
+static int launch_persistent(bf_batch* b, const BGeoms& G, const BPArgs& pa, size_t smem, cudaStream_t s) {
+  const void* fn = (const void*)k_bcg_persistent<SHR3>;
+  int rc = bf_smem_attr(fn, (int)smem, "cudaFuncSetAttribute(k_bcg_persistent)");
+  if (rc) return rc;
+  int per = 0, nsm = 0;
+  BF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bcg_persistent<SHR3>, BF_THREADS, smem));
+  BF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
+  int most = 1;
+  for (int c = 0; c < NCLS; ++c) most = std::max(most, std::max(b->njobs[c], b->nupd[c]));
+  const int grid = std::max(1, std::min(per * nsm, most));
+  BGeoms g = G;
+  BPArgs a = pa;
+  void* args[] = {(void*)&g, (void*)&a};
+  BF_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BF_THREADS), args, smem, s));
+  bf_count_launches(1);
+  return BF_OK;
+}
+
+// The persistent run: one cooperative launch; skip (testing) makes CTA 0 leave before its
+// first barrier.
+static int batch_run_persistent(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
+                                const bf_cg_opts* opts, bf_info* infos, int skip, cudaStream_t s) {
+  if (!b || !x0 || !x_out) return bf_fail(BF_EINVAL, "bf_batch_cg_persistent: NULL argument");
+  if (kmax < 0) return bf_fail(BF_EINVAL, "bf_batch_cg_persistent: kmax < 0");
+  bf_cg_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY)
+    return bf_fail(BF_EINVAL, "bf_batch_cg_persistent: precond must be Jacobi or identity");
+  if (o.beta != BF_BETA_FLEXIBLE && o.beta != BF_BETA_PRINTED)
+    return bf_fail(BF_EINVAL, "bf_batch_cg_persistent: bad beta");
+  if (!(o.shift >= 0.0) || !(o.tol >= 0.0))
+    return bf_fail(BF_EINVAL, "bf_batch_cg_persistent: shift and tol must be >= 0");
+  for (int i = 0; i < b->count; ++i)
+    if (!x0[i] || !x_out[i]) return bf_fail(BF_EINVAL, "bf_batch_cg_persistent: NULL instance vector");
+  if (!b->d_bar) BF_CUDA(cudaMalloc(&b->d_bar, 4 * sizeof(unsigned)));
+  int rc = batch_upload(b, x0, x_out, o, s);
+  if (rc) return rc;
+  BF_CUDA(cudaMemsetAsync(b->d_bar, 0, 4 * sizeof(unsigned), s));
+  BGeoms G;
+  BPArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  size_t smem = 0;
+  for (int c = 0; c < NCLS; ++c) {
+    G.g[c] = b->geom[c];
+    pa.has[c] = b->has[c] ? 1 : 0;
+    if (!b->has[c]) continue;
+    pa.op[c] = make_args(b, c, o);
+    pa.up[c] = pa.op[c];
+    pa.up[c].jobs = b->d_upd[c];
+    pa.njobs[c] = b->njobs[c];
+    pa.nupd[c] = b->nupd[c];
+  }
+  if (b->has[CLS_R3]) {
+    const size_t r3[3] = {bsmem<R3_32x8>(), bsmem<R3_64x4>(), bsmem<R3_16x16>()};
+    smem = std::max(smem, r3[b->r3_variant]);
+  }
+  if (b->has[CLS_R5]) smem = std::max(smem, bsmem<ShapeR5>());
+  if (b->has[CLS_X1]) smem = std::max(smem, bsmem<ShapeX1>());
+  pa.kmax = kmax;
+  pa.bar = reinterpret_cast<unsigned*>(b->d_bar);
+  pa.err = reinterpret_cast<int*>(b->d_bar) + 2;
+  pa.skip = skip;
+  if (b->r3_variant == 1) rc = launch_persistent<R3_64x4>(b, G, pa, smem, s);
+  else if (b->r3_variant == 2) rc = launch_persistent<R3_16x16>(b, G, pa, smem, s);
+  else rc = launch_persistent<R3_32x8>(b, G, pa, smem, s);
+  if (rc) return rc;
+  std::vector<BInst> h(b->count);
+  int err = 0;
+  BF_CUDA(cudaMemcpyAsync(&err, pa.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (infos) BF_CUDA(cudaMemcpyAsync(h.data(), b->d_inst, b->count * sizeof(BInst), cudaMemcpyDeviceToHost, s));
+  BF_CUDA(cudaStreamSynchronize(s));
+  if (err) return bf_fail(BF_ETIMEOUT, "bf_batch_cg_persistent: a grid-barrier wait gave up");
+  if (infos) {
+    for (int i = 0; i < b->count; ++i) {
+      const BState& st = h[i].st;
+      infos[i].iters = st.iter;
+      infos[i].status = st.status == B_CONV ? BF_CG_CONVERGED : (st.status == B_BREAK ? BF_CG_BREAKDOWN : 0);
+      infos[i].restarts = 0;
+      infos[i].reserved = st.status == B_NONFINITE ? 1 : 0;
+      infos[i].rnorm = sqrt(st.rr);
+      infos[i].ref = sqrt(st.ref2);
+    }
+  }
+  return BF_OK;
+}
+
+extern "C" int bf_batch_cg_persistent(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
+                                      const bf_cg_opts* opts, bf_info* infos, void* stream) {
+  return batch_run_persistent(b, x0, x_out, kmax, opts, infos, 0, (cudaStream_t)stream);
+}
+
+extern "C" int bf_batch_barrier_test(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
+                                     void* stream) {
+  return batch_run_persistent(b, x0, x_out, kmax, nullptr, nullptr, 1, (cudaStream_t)stream);
 }
 
 // Autotune the image class's tile shape: time `iters` CG iterations of the batch with each

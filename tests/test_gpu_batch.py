@@ -85,3 +85,37 @@ def test_batch_rejects_unsupported_graphs():
     Gs = bf().bf_weights(dev(noisy), 3, 2.0, 0.08, weight_mode="stored_f32")
     with pytest.raises(bf().BFError):
         bf().Batch([Gs])
+
+
+@pytest.mark.parametrize("shift,tol", [(0.0, 0.0), (1e-2, 0.0), (1e-1, 1e-4)])
+def test_persistent_run_equals_graph_run(shift, tol):
+    """One cooperative launch with grid barriers gives the per-phase run's results exactly
+    (same jobs, same reduction order) and matches the oracle."""
+    cases = mixed(seed=7)
+    B = bf().Batch([c[0] for c in cases])
+    x0s = [dev(c[2]) for c in cases]
+    kmax = 200 if tol > 0 else 12
+    outs_g, infos_g = B.cg(x0s, kmax, shift=shift, tol=tol)
+    outs_p, infos_p = B.cg_persistent(x0s, kmax, shift=shift, tol=tol)
+    for (G, O, x0), xg, xp, ig, ip in zip(cases, outs_g, outs_p, infos_g, infos_p):
+        assert torch.equal(xg, xp)
+        assert ig.iters == ip.iters and ig.status == ip.status
+        if tol == 0.0:
+            ref = solvers.cg(O, x0.astype(np.float64), kmax, shift=shift)
+            assert rel_l2(host(xp), ref["x"]) <= TOL_F32
+
+
+def test_persistent_barrier_wait_gives_up_and_context_survives():
+    """A CTA that never reaches the first grid barrier: every other CTA's bounded wait runs
+    out (1 s), the call reports BF_ETIMEOUT, and the next run on the same batch is right."""
+    cases = mixed(seed=9)
+    B = bf().Batch([c[0] for c in cases])
+    x0s = [dev(c[2]) for c in cases]
+    with pytest.raises(bf().BFError) as ei:
+        B.barrier_test(x0s, kmax=3)
+    assert ei.value.code == bf().BF_ETIMEOUT
+    outs, infos = B.cg_persistent(x0s, 8)
+    for (G, O, x0), x, info in zip(cases, outs, infos):
+        ref = solvers.cg(O, x0.astype(np.float64), 8)
+        assert info.iters == 8
+        assert rel_l2(host(x), ref["x"]) <= TOL_F32

@@ -35,6 +35,10 @@ def test_batch_256_instances_every_instance_against_oracle():
         x0s.append(t.reshape(-1))
     B = bf().Batch(graphs)
     outs, infos = B.cg(x0s, CG_ITERS)
+    # the persistent (one cooperative launch) form gives the same results exactly
+    outs_p, infos_p = B.cg_persistent(x0s, CG_ITERS)
+    assert all(torch.equal(a, b) for a, b in zip(outs, outs_p))
+    assert all(a.iters == b.iters for a, b in zip(infos, infos_p))
     jobs = [(i, nd, ny, nx, host(x)) for i, ((nd, ny, nx), x) in enumerate(zip(sizes, outs))]
     for G in graphs:
         G.free()
