@@ -245,6 +245,30 @@ int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, int k, int km
                   const bf_lobpcg_opts* opts, void* X_out, double* theta_out,
                   double* resid_out, void* y_out, bf_info* info, void* stream);
 
+/* r_out = shift (x0 - x) - L x, the residual of the shifted system (L + shift I) x =
+ * shift x0 of cg_filter (A9's Tikhonov filter; the learned preconditioner's training pairs
+ * solve (L + shift I) z = r for such r).  n elements of the graph's dtype each; r_out must
+ * not alias x0 or x.  Asynchronous. */
+int bf_shifted_residual(const bf_graph* g, const void* x0, const void* x, double shift, void* r_out,
+                        void* stream);
+
+/* The shifted system (L + shift I) x = shift x0 of cg_filter solved to a TRUE relative
+ * residual ||shift x0 - (L + shift I) x|| / ||shift x0|| <= tol by mixed-precision
+ * refinement (the FP32 recurrence of Algorithm 2 alone stalls near eps_32 times the
+ * condition number): each outer step forms the residual r in FP64 on g64 and solves
+ * (L + shift I) e = r by cg_filter on g32 (started at r / shift, options `inner`: T,
+ * beta, inner tolerance inner->tol (default 1e-3), learned net) for at most inner_kmax
+ * iterations, then x += e.  g64 (BF_F64) and g32 (BF_F32) are graphs of the same guide
+ * and shape.  x0, x_out: n doubles (may be the same array).  Stops after outer_max
+ * corrections.  info (may be NULL): iters = inner iterations in total, restarts = outer
+ * steps, rnorm = ||r||, ref = ||shift x0||, status = BF_CG_CONVERGED once tol is met.
+ * Uses the CG workspaces of both graphs; synchronises the stream once per outer step.
+ * Errors: BF_EINVAL (graphs, shift <= 0, tol <= 0), those of cg_filter for an inner solve
+ * (BF_EBREAKDOWN, ...), BF_ENONFINITE for a non-finite residual. */
+int cg_refine(const bf_graph* g64, const bf_graph* g32, const double* x0, double shift, double tol,
+              const bf_cg_opts* inner, int inner_kmax, int outer_max, double* x_out, bf_info* info,
+              void* stream);
+
 /* cg_filter without any device allocation (the paper has no counterpart: this is a
  * deployment variant).  cg_filter keeps its vectors in the graph's workspace, which grows
  * with cudaMalloc -- and cudaFree, which synchronises the whole device -- when a larger

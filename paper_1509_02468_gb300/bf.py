@@ -90,6 +90,9 @@ def _load():
                           ctypes.POINTER(bf_info), vp],
         "bf_rayleigh_ritz": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
         "cg_filter_noalloc": [vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, ctypes.POINTER(bf_info), vp],
+        "cg_refine": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(bf_cg_opts), i32, i32, vp,
+                      ctypes.POINTER(bf_info), vp],
+        "bf_shifted_residual": [vp, vp, vp, ctypes.c_double, vp, vp],
         "bf_net_nweights": [],
         "bf_net_create": [vp, ctypes.POINTER(vp)],
         "bf_net_free": [vp],
@@ -319,6 +322,29 @@ def cg_filter_noalloc(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jac
                                   ctypes.byref(info) if info is not None else None,
                                   _stream(stream)))
     return out, (_info(info) if info is not None else None)
+
+
+def shifted_residual(g: Graph, x0: torch.Tensor, x: torch.Tensor, shift: float, out=None, stream=None):
+    """r = shift (x0 - x) - L x (bf_shifted_residual)."""
+    out = torch.empty_like(x) if out is None else out
+    _check(_lib.bf_shifted_residual(g.handle, _ptr(x0), _ptr(x), shift, _ptr(out), _stream(stream)))
+    return out
+
+
+def cg_refine(g64: Graph, g32: Graph, x0: torch.Tensor, shift: float, tol: float, precond: str = "jacobi",
+              inner_tol: float = 1e-3, inner_kmax: int = 3000, outer_max: int = 30, net: "Net | None" = None,
+              out=None, stream=None):
+    """(L + shift I) x = shift x0 to a true relative residual tol (cg_refine: FP64 residuals
+    on g64, FP32 inner CG on g32).  x0: float64 CUDA tensor.  Returns (x, info)."""
+    if x0.dtype != torch.float64:
+        raise ValueError("x0 must be float64")
+    out = torch.empty_like(x0) if out is None else out
+    o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS["flexible"], shift=shift, tol=inner_tol, hist=None,
+                   net=net.handle if net is not None else None)
+    info = bf_info()
+    _check(_lib.cg_refine(g64.handle, g32.handle, _ptr(x0), shift, tol, ctypes.byref(o), inner_kmax, outer_max,
+                          _ptr(out), ctypes.byref(info), _stream(stream)))
+    return out, _info(info)
 
 
 def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",

@@ -13,6 +13,8 @@
 // return at once, so the host loop needs no read-back.
 #include <math.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <mutex>
 
@@ -913,6 +915,139 @@ extern "C" int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_c
   cudaStream_t s = (cudaStream_t)stream;
   if (g->esize == 4) return cg_run<float>(g, (const float*)x0, kmax, o, (float*)x_out, info, s);
   return cg_run<double>(g, (const double*)x0, kmax, o, (double*)x_out, info, s);
+}
+
+// ==================================================================== refinement
+// (L + sigma I) x = sigma x0 to a TRUE relative residual: each outer step forms the
+// residual r = sigma (x0 - x) - L x in FP64 on the FP64 graph, and solves the correction
+// (L + sigma I) e = r by the FP32 CG filter on the FP32 graph to an inner tolerance; the
+// FP32 recurrence alone stalls near eps_32 times the condition number.
+namespace {
+
+// r = sigma (x0 - x) - q (q = L x), rhs = r / sigma in FP32; sums r^T r and x0^T x0.
+__global__ void __launch_bounds__(BF_THREADS) k_ref_resid(const double* x0, const double* x, const double* q,
+                                                          double sigma, int64_t n, float* rhs, double* partials,
+                                                          unsigned* counter, double* out) {
+  __shared__ double red[2 * (BF_THREADS / 32)];
+  __shared__ int last;
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * BF_THREADS) {
+    const double r = sigma * (x0[i] - x[i]) - q[i];
+    rhs[i] = (float)(r / sigma);
+    v[0] = fma(r, r, v[0]);
+    v[1] = fma(x0[i], x0[i], v[1]);
+  }
+  double blk[2], tot[2];
+  block_sum<2, double>(v, red, blk);
+  if (grid_sum_last<2>(blk, partials, counter, tot, &last)) {
+    out[0] = tot[0];
+    out[1] = tot[1];
+  }
+}
+
+// x += e (the FP32 correction) and x = x0.
+__global__ void __launch_bounds__(BF_THREADS) k_ref_add(double* x, const float* e, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * BF_THREADS)
+    x[i] += (double)e[i];
+}
+
+}  // namespace
+
+extern "C" int cg_refine(const bf_graph* g64, const bf_graph* g32, const double* x0, double shift, double tol,
+                         const bf_cg_opts* inner, int inner_kmax, int outer_max, double* x_out, bf_info* info,
+                         void* stream) {
+  if (!g64 || !g32 || !x0 || !x_out) return bf_fail(BF_EINVAL, "cg_refine: NULL argument");
+  if (g64->esize != 8 || g32->esize != 4 || g64->n != g32->n || g64->nx != g32->nx || g64->ny != g32->ny)
+    return bf_fail(BF_EINVAL, "cg_refine: needs an FP64 and an FP32 graph of the same shape");
+  if (!(shift > 0.0) || !(tol > 0.0) || inner_kmax < 1 || outer_max < 0)
+    return bf_fail(BF_EINVAL, "cg_refine: need shift > 0, tol > 0, inner_kmax >= 1, outer_max >= 0");
+  if ((uintptr_t)x0 % 8 || (uintptr_t)x_out % 8) return bf_fail(BF_EINVAL, "cg_refine: misaligned vector");
+  bf_cg_opts o;
+  memset(&o, 0, sizeof(o));
+  if (inner) o = *inner;
+  if (!(o.tol > 0.0)) o.tol = 1e-3;
+  o.shift = shift;
+  o.hist = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = g64->n;
+  // the refinement's vectors live in the FP64 graph's CG workspace (the inner CG uses the
+  // FP32 graph's): q (FP64), rhs and e (FP32), partial sums, counter and the two sums
+  bf_graph* gm = const_cast<bf_graph*>(g64);
+  const size_t vd = ((size_t)n * 8 + 255) & ~(size_t)255, vf = ((size_t)n * 4 + 255) & ~(size_t)255;
+  const unsigned nb = (unsigned)std::min<int64_t>((n + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms());
+  const size_t pb = (((size_t)nb * 2 * sizeof(double)) + 255) & ~(size_t)255;
+  int rc = bf_ws_reserve(gm, BF_WS_CG, vd + 2 * vf + pb + 256);
+  if (rc) return rc;
+  char* w = (char*)gm->ws[BF_WS_CG];
+  double* q = (double*)w;
+  float* rhs = (float*)(w + vd);
+  float* e = (float*)(w + vd + vf);
+  double* partials = (double*)(w + vd + 2 * vf);
+  unsigned* counter = (unsigned*)(w + vd + 2 * vf + pb);
+  double* sums = (double*)(w + vd + 2 * vf + pb + 16);
+  BF_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+  if (x_out != x0) BF_CUDA(cudaMemcpyAsync(x_out, x0, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+  int inner_total = 0, outer = 0;
+  double rel = 0.0, rr = 0.0, bb = 0.0;
+  for (;; ++outer) {
+    if ((rc = bf_apply_f64(g64, BF_OP_L, x_out, 1, 1, q, 1, nullptr, s))) return rc;
+    BF_LAUNCH(k_ref_resid<<<nb, BF_THREADS, 0, s>>>(x0, x_out, q, shift, n, rhs, partials, counter, sums));
+    BF_CUDA(cudaGetLastError());
+    double h[2];
+    BF_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    rr = h[0];
+    bb = shift * shift * h[1];
+    if (!std::isfinite(rr)) return bf_fail(BF_ENONFINITE, "cg_refine: non-finite residual");
+    rel = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    if (rel <= tol || outer == outer_max) break;
+    bf_info ii;
+    if ((rc = cg_filter(g32, rhs, inner_kmax, &o, e, &ii, stream))) return rc;
+    inner_total += ii.iters;
+    BF_LAUNCH(k_ref_add<<<nb, BF_THREADS, 0, s>>>(x_out, e, n));
+  }
+  if (info) {
+    info->iters = inner_total;
+    info->status = rel <= tol ? BF_CG_CONVERGED : 0;
+    info->restarts = outer;
+    info->reserved = 0;
+    info->rnorm = std::sqrt(rr);
+    info->ref = std::sqrt(bb);
+  }
+  return BF_OK;
+}
+
+// r = shift (x0 - x) - L x: the residual of (L + shift I) x = shift x0 (the training pairs
+// of the learned preconditioner are built from it).
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(BF_THREADS) k_shifted_resid(const T* x0, const T* x, T shift, int64_t n, T* r) {
+  for (int64_t i = (int64_t)blockIdx.x * BF_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * BF_THREADS)
+    r[i] = fma(shift, x0[i] - x[i], -r[i]);
+}
+}  // namespace
+
+extern "C" int bf_shifted_residual(const bf_graph* g, const void* x0, const void* x, double shift, void* r_out,
+                                   void* stream) {
+  if (!g || !x0 || !x || !r_out) return bf_fail(BF_EINVAL, "bf_shifted_residual: NULL argument");
+  if (!(shift >= 0.0)) return bf_fail(BF_EINVAL, "bf_shifted_residual: shift must be >= 0");
+  if ((uintptr_t)x0 % g->esize || (uintptr_t)x % g->esize || (uintptr_t)r_out % g->esize)
+    return bf_fail(BF_EINVAL, "bf_shifted_residual: misaligned vector");
+  if (r_out == x || r_out == x0) return bf_fail(BF_EINVAL, "bf_shifted_residual: r_out must not alias x0 or x");
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned nb = (unsigned)std::min<int64_t>((g->n + BF_THREADS - 1) / BF_THREADS, 8 * cg_num_sms());
+  int rc;
+  if (g->esize == 4) {
+    if ((rc = bf_apply_f32(g, BF_OP_L, (const float*)x, 1, 1, (float*)r_out, 1, nullptr, s))) return rc;
+    BF_LAUNCH(k_shifted_resid<float><<<nb, BF_THREADS, 0, s>>>((const float*)x0, (const float*)x, (float)shift,
+                                                               g->n, (float*)r_out));
+  } else {
+    if ((rc = bf_apply_f64(g, BF_OP_L, (const double*)x, 1, 1, (double*)r_out, 1, nullptr, s))) return rc;
+    BF_LAUNCH(k_shifted_resid<double><<<nb, BF_THREADS, 0, s>>>((const double*)x0, (const double*)x, shift, g->n,
+                                                                (double*)r_out));
+  }
+  BF_CUDA(cudaGetLastError());
+  return BF_OK;
 }
 
 // ==================================================================== allocation-free CG

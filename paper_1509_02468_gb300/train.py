@@ -42,12 +42,6 @@ def initial_weights(noise: float = 1e-2, seed: int = 0):
     return [W1.astype(np.float32), W2.astype(np.float32), W3.astype(np.float32)]
 
 
-def shifted_residual(G, x0, x, sigma):
-    """r = sigma x0 - (L + sigma I) x."""
-    Lx = bf.bf_apply(G, "L", x)
-    return sigma * (x0 - x) - Lx
-
-
 def make_pairs(seeds, side: int, sigma: float = SIGMA, picks=CG_PICKS, tol: float = 1e-8,
                kmax_solve: int = 20000, device="cuda"):
     """[(graph, r, z)] for the given image seeds (graphs kept alive with the pairs)."""
@@ -60,7 +54,7 @@ def make_pairs(seeds, side: int, sigma: float = SIGMA, picks=CG_PICKS, tol: floa
         x0 = g32.reshape(-1).contiguous()
         for j in picks:
             x = x0.clone() if j == 0 else bf.cg_filter(G, x0, j, shift=sigma)[0]
-            r = shifted_residual(G, x0, x, sigma)
+            r = bf.shifted_residual(G, x0, x, sigma)
             z, info, _ = bf.cg_filter(G64, (r / sigma).double(), kmax_solve, shift=sigma, tol=tol)
             out.append((G, r.contiguous(), z.float().contiguous()))
     return out
@@ -102,28 +96,16 @@ def mean_loss(net, pairs):
 
 def refined_cg(G32, G64, x0, sigma: float, tol: float, precond: str, net=None, inner_tol: float = 1e-3,
                inner_kmax: int = 3000, outer_max: int = 30):
-    """(L + sigma I) x = sigma x0 to a true relative residual tol: FP64 residuals on G64, each
-    correction solved by FP32 flexible CG on G32 to inner_tol (the FP32 recurrence alone
-    stalls near eps_32 times the condition number).  Returns (x, rel, inner iterations,
-    outer steps)."""
-    b = sigma * x0.double()
-    nb = float(torch.linalg.vector_norm(b))
-    x = x0.double().clone()
-    inner = 0
-    rel = float("inf")
-    for outer in range(outer_max + 1):
-        r = b - bf.bf_apply(G64, "L", x) - sigma * x
-        rel = float(torch.linalg.vector_norm(r)) / nb
-        if rel <= tol or outer == outer_max:
-            return x, rel, inner, outer
-        try:
-            e, info, _ = bf.cg_filter(G32, (r / sigma).float(), inner_kmax, precond=precond, net=net,
-                                      shift=sigma, tol=inner_tol)
-        except bf.BFError:                      # breakdown or non-finite scalars: give up
-            return x, float("nan"), inner, outer
-        inner += info.iters
-        x += e.double()
-    return x, rel, inner, outer_max
+    """(L + sigma I) x = sigma x0 to a true relative residual tol by the library's
+    mixed-precision refinement (cg_refine: FP64 residuals on G64, FP32 flexible CG on G32 to
+    inner_tol).  Returns (x, rel, inner iterations, outer steps); rel is NaN when an inner
+    solve broke down."""
+    try:
+        x, info = bf.cg_refine(G64, G32, x0.double().contiguous(), sigma, tol, precond=precond, net=net,
+                               inner_tol=inner_tol, inner_kmax=inner_kmax, outer_max=outer_max)
+    except bf.BFError:                          # breakdown or non-finite scalars: give up
+        return x0.double(), float("nan"), 0, 0
+    return x, info.rnorm / info.ref, info.iters, info.restarts
 
 
 def evaluate(net, side: int, seed: int, sigma: float = SIGMA, tol: float = 1e-5, reps: int = 2,

@@ -6,7 +6,8 @@
   (the oracle runs in a pool of spawned worker processes).
 * The 1024 x 1024 image of the shifted-system workload: cg_filter on (L + sigma I) x =
   sigma x0 with sigma = 1e-2, at a fixed iteration count and with the tolerance the
-  refinement's inner solves use, against the oracle.
+  refinement's inner solves use, against the oracle; and cg_refine to a true residual of
+  1e-5, checked with the oracle's FP64 matrices.
 """
 import multiprocessing as mp
 import os
@@ -77,3 +78,12 @@ def test_shifted_cg_1024_fixed_count_and_inner_tolerance():
     assert abs(info.iters - ref["iters"]) <= 1
     same = solvers.cg(O, x0, info.iters, shift=sigma)
     assert rel_l2(host(x), same["x"]) <= TOL_F32
+    # the same system to a TRUE relative residual of 1e-5 by mixed-precision refinement
+    # (FP64 residuals, FP32 inner CG to 1e-3), checked with the oracle's FP64 matrices
+    import scipy.sparse as sp
+    G64 = bf().bf_weights(dev(noisy, torch.float64), 3, 2.0, 0.08)
+    x, info = bf().cg_refine(G64, G, dev(x0, torch.float64), sigma, 1e-5)
+    assert info.status == "converged"
+    A = (O.L + sigma * sp.identity(O.n, format="csr")).tocsr()
+    rel = float(np.linalg.norm(sigma * x0 - A @ host(x)) / np.linalg.norm(sigma * x0))
+    assert rel <= 1.01e-5
