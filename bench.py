@@ -16,7 +16,8 @@ HBM), `cg_2048` (CG 50 on the 2048 x 2048 image against HBM), `roofline_apply16_
 on a k = 16 block of the step's image, bound by the FP32 pipe), `roofline_2048` (the same
 on a 2048 x 2048 image, X and Y far larger than L2),
 `roofline_dominant` (the Rayleigh-Ritz solve, the largest share of the step's GPU time),
-`batched` (CG on 256 uneven instances, one CUDA graph, against plain calls),
+`batched` (CG on 256 uneven instances, one CUDA graph and one persistent launch, against
+plain calls; block LOBPCG on the same instances over a pool of streams against plain calls),
 `cpu_baseline` (the FP64 CPU oracle, one thread, on
 one full step of the same workload), `e2e` (the same pipeline from pinned host memory to
 host results), `clocks` (nvidia-smi sampled during the timed region) and `gpu_launches`
@@ -578,9 +579,10 @@ def _time_rr(bf, torch, stream, flush, m=48, k=16, reps=20):
 # the diag-L scaling 16), one step D^-1 W x at k = 1 (read x 4, guide 4, 1/d 4, write 4)
 REGUIDED_BYTES_PER_PX = 8 + 20 + 16
 # the step is bound by its Eq. 2 exponentials, one per (pixel, neighbour) pair of the 7 x 7
-# window, against the SFU's nominal 16 ex2 per clock per SM
+# window, against the SFU's 31.7 ex2 per clock per SM (a throughput microbenchmark of
+# ex2.approx on this GB300; twice Blackwell's 16)
 REGUIDED_EXPS_PER_PX = 48
-SFU_EX2_PER_SM_CLK = 16
+SFU_EX2_PER_SM_CLK = 31.7
 
 
 def _run_reguided(bf, torch, stream, flush, peak, iters=10, reps=5):
@@ -619,7 +621,7 @@ def _run_reguided(bf, torch, stream, flush, peak, iters=10, reps=5):
         out[f"{side}x{side}"] = {"ms": ms, "us_per_step": 1e3 * ms / iters,
                                  "mpix_steps_per_s": npx * iters / (ms * 1e-3) / 1e6,
                                  "sfu": {"achieved": exps, "peak": sfu_peak, "unit": "T exp/s",
-                                         "frac": exps / sfu_peak, "peak_source": "nominal",
+                                         "frac": exps / sfu_peak, "peak_source": "measured (microbenchmark)",
                                          "exps_per_px_step": REGUIDED_EXPS_PER_PX},
                                  "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s",
                                          "frac": gbs / peak,
@@ -760,12 +762,28 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
         for G, x, o in zip(graphs, x0s, outs):
             bf.cg_filter(G, x, kmax, out=o, sync=False)
     ms_p = timed(plain)
+    # block LOBPCG (k = 16, 30 iterations) on every instance: over a pool of 32 streams
+    # (bf_batch_lobpcg) against one lobpcg_filter call after another on one stream
+    import numpy as np
+
+    from paper_1509_02468_gb300 import synth
+    X0s = [torch.as_tensor(synth.block_start(x.cpu().numpy(), 16, seed=4000 + i, dtype=np.float32)).cuda()
+           for i, x in enumerate(x0s)]
+    ms_lb = timed(lambda: B.lobpcg(X0s, 30, nstreams=32, sync=False))
+
+    def plain_lob():
+        for G, X0 in zip(graphs, X0s):
+            bf.lobpcg_filter(G, X0, 30, want_X=False, sync=False)
+    ms_lp = timed(plain_lob)
     B.free()
     return {"workload": "256 instances: 192 images, sides log-uniform in [64, 1024]; 64 signals, "
                         "lengths log-uniform in [1e3, 1e6]; CG 50 (Jacobi), FP32",
             "samples": total, "cg_iters": kmax,
             "batched_mpix_s": total / (ms_b * 1e-3) / 1e6, "batched_ms": ms_b,
             "persistent_mpix_s": total / (ms_pers * 1e-3) / 1e6, "persistent_ms": ms_pers,
+            "lobpcg_k16x30": {"batched_ms": ms_lb, "batched_mpix_s": total / (ms_lb * 1e-3) / 1e6,
+                              "plain_ms": ms_lp, "plain_mpix_s": total / (ms_lp * 1e-3) / 1e6,
+                              "streams": 32},
             "persistent_note": "one cooperative launch, bounded grid barriers between phases; "
                                "includes the host read of the barrier flag",
             "plain_mpix_s": total / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,

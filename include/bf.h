@@ -349,6 +349,18 @@ int bf_batch_cg(bf_batch* b, const float* const* x0, float* const* x_out, int km
  * BF_ETIMEOUT (the instance vectors are then undefined).  Synchronises the stream. */
 int bf_batch_cg_persistent(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
                            const bf_cg_opts* opts, bf_info* infos, void* stream);
+/* Algorithm 3 (block LOBPCG, as lobpcg_filter) on every instance of the batch: instance i
+ * runs on internal stream i % S (S = nstreams, 1..64), enqueued by S host threads, so the
+ * Rayleigh-Ritz solves of different instances (one SM each) and their data-parallel
+ * kernels run side by side.  X0: HOST array of device pointers, [n_i][k] floats each
+ * (ld = k; column 0 the signal to filter); theta_out, y_out: NULL or HOST arrays of device
+ * pointers (k doubles, n_i floats).  opts as for lobpcg_filter.  Needs 3k <= n_i.  The
+ * work is ordered after the caller's stream and the caller's stream waits for it; with
+ * infos (host array of count) every instance's call synchronises its stream and fills its
+ * entry.  Each graph's LOBPCG workspace is used, so no other LOBPCG call may run on these
+ * graphs meanwhile.  Errors: the first failing instance's code and message. */
+int bf_batch_lobpcg(bf_batch* b, const float* const* X0, int k, int kmax, const bf_lobpcg_opts* opts,
+                    double* const* theta_out, float* const* y_out, int nstreams, bf_info* infos, void* stream);
 /* Autotuner: time `iters` iterations with each candidate tile shape of the image class
  * (32 x 8, 64 x 4, 16 x 16 pixels) on these vectors and keep the fastest; ms_out (host,
  * 3 floats) receives the timings.  Synchronises the stream. */

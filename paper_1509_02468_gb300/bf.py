@@ -110,6 +110,7 @@ def _load():
         "bf_batch_tune": [vp, vp, vp, i32, vp, vp],
         "bf_batch_cg_persistent": [vp, vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, vp],
         "bf_batch_barrier_test": [vp, vp, vp, i32, vp],
+        "bf_batch_lobpcg": [vp, vp, i32, i32, ctypes.POINTER(bf_lobpcg_opts), vp, vp, i32, vp, vp],
         "bf_batch_tiles": [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
@@ -507,6 +508,22 @@ class Batch:
         (include/bf_testing.h): raises BFError(BF_ETIMEOUT)."""
         outs = [torch.empty_like(x) for x in x0s] if outs is None else outs
         _check(_lib.bf_batch_barrier_test(self.handle, self._ptrs(x0s), self._ptrs(outs), kmax, _stream(stream)))
+
+    def lobpcg(self, X0s, kmax: int, nstreams: int = 32, pencil: str = "D", precond: str = "jacobi",
+               constrain: bool = False, gram: str = "fp32", sync: bool = True, stream=None):
+        """Algorithm 3 on every instance (bf_batch_lobpcg); X0s: list of (n_i, k) float32 blocks.
+        Returns (thetas, ys, infos) -- infos None unless sync."""
+        k = X0s[0].shape[1]
+        thetas = [torch.empty(k, dtype=torch.float64, device=X.device) for X in X0s]
+        ys = [torch.empty(X.shape[0], dtype=X.dtype, device=X.device) for X in X0s]
+        o = bf_lobpcg_opts(pencil=PENCILS[pencil], precond=PRECONDS[precond], constrain_e=int(constrain),
+                           gram=GRAMS[gram], tol=0.0, theta_hist=None, net=None)
+        infos = (bf_info * len(X0s))() if sync else None
+        _check(_lib.bf_batch_lobpcg(self.handle, self._ptrs(X0s), k, kmax, ctypes.byref(o), self._ptrs(thetas),
+                                    self._ptrs(ys), nstreams, infos, _stream(stream)))
+        if sync:
+            torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return thetas, ys, ([_info(i) for i in infos] if infos is not None else None)
 
     def tune(self, x0s, iters: int = 5, outs=None, stream=None):
         """Autotune the image tile shape; returns the timings (ms) of the three candidates."""

@@ -16,6 +16,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "bf_internal.cuh"
@@ -403,6 +405,8 @@ struct bf_batch {
   double* d_part[NCLS];
   void* d_vec;                       // r, s, q, p0, p1 of every instance
   void* d_bar;                       // persistent run: barrier counters and timeout flag
+  std::vector<cudaStream_t> lob_streams;   // batched LOBPCG: internal streams
+  std::vector<cudaEvent_t> lob_events;     // one per internal stream, and one for the start
   std::vector<BInst> h_inst;
   // captured run
   cudaGraphExec_t exec;
@@ -615,6 +619,8 @@ extern "C" int bf_batch_free(bf_batch* b) {
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_vec) cudaFree(b->d_vec);
   if (b->d_bar) cudaFree(b->d_bar);
+  for (cudaStream_t st : b->lob_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->lob_events) cudaEventDestroy(ev);
   delete b;
   return BF_OK;
 }
@@ -795,6 +801,68 @@ extern "C" int bf_batch_cg_persistent(bf_batch* b, const float* const* x0, float
 extern "C" int bf_batch_barrier_test(bf_batch* b, const float* const* x0, float* const* x_out, int kmax,
                                      void* stream) {
   return batch_run_persistent(b, x0, x_out, kmax, nullptr, nullptr, 1, (cudaStream_t)stream);
+}
+
+// ---- batched LOBPCG ---------------------------------------------------------------------------
+// Algorithm 3 on every instance: instance i runs lobpcg_filter on internal stream i % S,
+// enqueued by S host threads (one per stream), so that the Rayleigh-Ritz solves of the
+// instances -- each on one SM -- and their data-parallel kernels run side by side.  Each
+// graph keeps its own LOBPCG workspace, so the instances do not share memory.
+extern "C" int bf_batch_lobpcg(bf_batch* b, const float* const* X0, int k, int kmax, const bf_lobpcg_opts* opts,
+                               double* const* theta_out, float* const* y_out, int nstreams, bf_info* infos,
+                               void* stream) {
+  if (!b || !X0) return bf_fail(BF_EINVAL, "bf_batch_lobpcg: NULL argument");
+  if (k < 1 || kmax < 0) return bf_fail(BF_EINVAL, "bf_batch_lobpcg: need k >= 1 and kmax >= 0");
+  for (int i = 0; i < b->count; ++i) {
+    if (!X0[i]) return bf_fail(BF_EINVAL, "bf_batch_lobpcg: NULL instance block");
+    if (3 * (int64_t)k > b->graphs[i]->n) return bf_fail(BF_EINVAL, "bf_batch_lobpcg: an instance has n < 3k");
+  }
+  const int S = std::max(1, std::min(nstreams, std::min(64, b->count)));
+  int dev = 0;
+  BF_CUDA(cudaGetDevice(&dev));
+  while ((int)b->lob_streams.size() < S) {
+    cudaStream_t st;
+    BF_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    b->lob_streams.push_back(st);
+  }
+  while ((int)b->lob_events.size() < S + 1) {
+    cudaEvent_t ev;
+    BF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b->lob_events.push_back(ev);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BF_CUDA(cudaEventRecord(b->lob_events[S], s));                 // the inputs are ready
+  for (int t = 0; t < S; ++t) BF_CUDA(cudaStreamWaitEvent(b->lob_streams[t], b->lob_events[S], 0));
+  std::vector<int> rc(S, BF_OK);
+  std::vector<std::string> msg(S);
+  auto worker = [&](int t) {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      rc[t] = BF_ECUDA;
+      msg[t] = "bf_batch_lobpcg: cudaSetDevice failed in a worker";
+      return;
+    }
+    for (int i = t; i < b->count; i += S) {
+      const int r = lobpcg_filter(b->graphs[i], X0[i], k, k, kmax, opts, nullptr, theta_out ? theta_out[i] : nullptr,
+                                  nullptr, y_out ? y_out[i] : nullptr, infos ? &infos[i] : nullptr,
+                                  (void*)b->lob_streams[t]);
+      if (r != BF_OK) {
+        rc[t] = r;
+        msg[t] = std::string("bf_batch_lobpcg: instance ") + std::to_string(i) + ": " + bf_last_error();
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < S; ++t) pool.emplace_back(worker, t);
+  worker(0);
+  for (std::thread& th : pool) th.join();
+  for (int t = 0; t < S; ++t) {
+    BF_CUDA(cudaEventRecord(b->lob_events[t], b->lob_streams[t]));
+    BF_CUDA(cudaStreamWaitEvent(s, b->lob_events[t], 0));      // the caller's stream waits for all
+  }
+  for (int t = 0; t < S; ++t)
+    if (rc[t] != BF_OK) return bf_fail(rc[t], msg[t]);
+  return BF_OK;
 }
 
 // Autotune the image class's tile shape: time `iters` CG iterations of the batch with each

@@ -27,3 +27,22 @@ def batch_cg_error(job):
     ref = solvers.cg(Graph(g64, (ny, nx), r, ss, sr), g64.reshape(-1), CG_ITERS)
     x = np.asarray(x_gpu, np.float64).reshape(-1)
     return i, ref["iters"], float(np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]))
+
+
+def batch_lobpcg_error(job):
+    """(i, Ritz-value error by the A8 reading, relative L2 error of y, largest absolute
+    Ritz-value error, the oracle's Ritz value where the A8 error is largest) of the GPU
+    results against the oracle's LOBPCG(k, kmax) on instance i from the given FP32 block
+    start."""
+    from oracle import solvers
+    from oracle.graph import Graph
+    i, nd, ny, nx, X0, kmax, theta, y = job
+    noisy, (r, ss, sr) = batch_instance(i, nd, ny, nx)
+    g64 = np.asarray(noisy, np.float32).astype(np.float64)
+    ref = solvers.lobpcg(Graph(g64, (ny, nx), r, ss, sr), np.asarray(X0, np.float64), kmax)
+    th_ref = ref["theta"]
+    scale = np.maximum(np.abs(th_ref), 1e-3 * np.abs(th_ref).max())
+    dth = np.abs(np.asarray(theta, np.float64) - th_ref)
+    e_th = float(np.max(dth / scale))
+    e_y = float(np.linalg.norm(np.asarray(y, np.float64) - ref["y"]) / np.linalg.norm(ref["y"]))
+    return i, e_th, e_y, float(dth.max()), float(th_ref[int(np.argmax(dth / scale))])

@@ -119,3 +119,23 @@ def test_persistent_barrier_wait_gives_up_and_context_survives():
         ref = solvers.cg(O, x0.astype(np.float64), 8)
         assert info.iters == 8
         assert rel_l2(host(x), ref["x"]) <= TOL_F32
+
+
+def test_batched_lobpcg_equals_single_calls_and_oracle():
+    """Algorithm 3 on every instance over a pool of streams: each instance's Ritz values and
+    filtered signal equal those of its own lobpcg_filter call exactly, and the oracle's."""
+    from paper_1509_02468_gb300 import synth
+    from tests.gpu_helpers import TOL_RITZ_SMALL_F32
+    cases = mixed(seed=11)
+    B = bf().Batch([c[0] for c in cases])
+    k, kmax = 4, 10
+    X0s = [dev(synth.block_start(c[2], k, seed=11 + i)) for i, c in enumerate(cases)]
+    thetas, ys, infos = B.lobpcg(X0s, kmax, nstreams=3)
+    for (G, O, x0), X0, th, y, info in zip(cases, X0s, thetas, ys, infos):
+        single = bf().lobpcg_filter(G, X0, kmax, want_X=False)
+        assert torch.equal(th, single["theta"]) and torch.equal(y, single["y"])
+        assert info.iters == kmax
+        ref = solvers.lobpcg(O, host(X0), kmax)
+        scale = np.maximum(np.abs(ref["theta"]), 1e-3 * np.abs(ref["theta"]).max())
+        assert np.max(np.abs(host(th) - ref["theta"]) / scale) <= TOL_RITZ_SMALL_F32
+        assert rel_l2(host(y), ref["y"]) <= 1e-4

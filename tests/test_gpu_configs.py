@@ -22,7 +22,7 @@ from tests.gpu_helpers import TOL_F32, bf, dev, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-from tests.oracle_jobs import BATCH_SEED, CG_ITERS, batch_cg_error, batch_instance
+from tests.oracle_jobs import BATCH_SEED, CG_ITERS, batch_cg_error, batch_instance, batch_lobpcg_error
 
 
 def test_batch_256_instances_every_instance_against_oracle():
@@ -87,3 +87,37 @@ def test_shifted_cg_1024_fixed_count_and_inner_tolerance():
     A = (O.L + sigma * sp.identity(O.n, format="csr")).tocsr()
     rel = float(np.linalg.norm(sigma * x0 - A @ host(x)) / np.linalg.norm(sigma * x0))
     assert rel <= 1.01e-5
+
+
+
+def test_batch_256_instances_lobpcg():
+    """Block LOBPCG (k = 16, 30 iterations) on all 256 instances over a pool of streams:
+    every instance equals its own lobpcg_filter call exactly; the instances of at most
+    2^16 samples are compared with the oracle: the filtered signal to the FP32 bar 1e-5,
+    the Ritz values by the A8 reading (1e-6) or, for the tiny smallest Ritz values of small
+    instances (A8 floor below 1e-5), within 2^-22 absolute: the FP32 Gram entries of the
+    residual directions carry absolute errors of order 2^-24 times the pencil's spectral
+    radius (< 2), which bound the Ritz values' absolute error (Weyl)."""
+    from tests.gpu_helpers import TOL_F32, TOL_RITZ
+    sizes = synth.batch_sizes(BATCH_SEED)
+    graphs, X0s = [], []
+    for i, (nd, ny, nx) in enumerate(sizes):
+        noisy, (r, ss, sr) = batch_instance(i, nd, ny, nx)
+        t = dev(noisy)
+        graphs.append(bf().bf_weights(t, r, ss, sr))
+        X0s.append(dev(synth.block_start(noisy.reshape(-1), 16, seed=4000 + i)))
+    B = bf().Batch(graphs)
+    thetas, ys, infos = B.lobpcg(X0s, 30, nstreams=32)
+    for G, X0, th, y, info in zip(graphs, X0s, thetas, ys, infos):
+        single = bf().lobpcg_filter(G, X0, 30, want_X=False)
+        assert torch.equal(th, single["theta"]) and torch.equal(y, single["y"])
+        assert info.iters == 30
+    jobs = [(i, nd, ny, nx, host(X0s[i]), 30, host(thetas[i]), host(ys[i]))
+            for i, (nd, ny, nx) in enumerate(sizes) if ny * nx <= 1 << 16]
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        results = list(ex.map(batch_lobpcg_error, sorted(jobs, key=lambda j: -j[2] * j[3]), chunksize=1))
+    assert len(results) >= 100
+    for i, e_th, e_y, e_abs, _ in results:
+        assert e_th <= TOL_RITZ or e_abs <= 2.0 ** -22, (i, sizes[i], e_th, e_abs)
+        assert e_y <= TOL_F32, (i, sizes[i], e_y)
