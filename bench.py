@@ -420,7 +420,7 @@ FP32_LANES_PER_SM = 128
 # an ncu launch list of the timed step
 RR_FP64_FMA = (2 * 48 ** 3 / 3 + 48 ** 3 / 6 + 2 * 48 * 48 * 16 + 3 * 48 * 16 * 16
                + 48 * 48 * 16 / 2 + 48 * 48 * 16 + 2 * 48 * 16 * 16)
-RR_SHARE = 0.476
+RR_SHARE = 0.495
 
 
 def _sm_max_ghz():
@@ -721,6 +721,30 @@ def _batch_inputs(seed=4):
     return out
 
 
+def _batch_oracle_errors(inst, outs_by_form, kmax, n_small=4):
+    """Largest relative L2 error, per batched form, of the CG output against the FP64
+    oracle's CG (Algorithm 2, kmax iterations) on the n_small smallest signals and the
+    n_small smallest images."""
+    import numpy as np
+
+    from oracle import solvers
+    from oracle.graph import Graph
+    order = []
+    for nd in (1, 2):
+        order += sorted((i for i in range(len(inst)) if inst[i][0] == nd), key=lambda i: inst[i][1].size)[:n_small]
+    worst = {f: 0.0 for f in outs_by_form}
+    for i in order:
+        nd, a = inst[i]
+        g64 = np.asarray(a, np.float32).astype(np.float64)
+        shape = a.shape if nd == 2 else (1, a.size)
+        r, ss, sr = (3, 2.0, 0.08) if nd == 2 else (5, 3.0, 0.1)
+        ref = solvers.cg(Graph(g64, shape, r, ss, sr), g64.reshape(-1), kmax)["x"]
+        for f, outs in outs_by_form.items():
+            x = outs[i].double().cpu().numpy()
+            worst[f] = max(worst[f], float(np.linalg.norm(x - ref) / np.linalg.norm(ref)))
+    return worst
+
+
 def _run_batched(bf, torch, stream, kmax=50, reps=3):
     """Mpix/s of CG(kmax) on the 256 instances: one bf_batch graph (tile shape autotuned)
     against plain cg_filter calls one instance after another; inputs resident."""
@@ -756,12 +780,22 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
     l0 = bf.launch_count()
     ms_b = timed(lambda: B.cg(x0s, kmax, outs=outs, sync=False))
     lb = (bf.launch_count() - l0) / (reps + 1)
-    ms_pers = timed(lambda: B.cg_persistent(x0s, kmax, outs=outs))
+    outs_pers = [torch.empty_like(x) for x in x0s]
+    ms_pers = timed(lambda: B.cg_persistent(x0s, kmax, outs=outs_pers))
+    outs_plain = [torch.empty_like(x) for x in x0s]
 
     def plain():
-        for G, x, o in zip(graphs, x0s, outs):
+        for G, x, o in zip(graphs, x0s, outs_plain):
             bf.cg_filter(G, x, kmax, out=o, sync=False)
     ms_p = timed(plain)
+    torch.cuda.synchronize()
+    # equal accuracy: the batched outputs against the plain calls' on every instance, and
+    # all three against the FP64 oracle's CG on the smallest instances
+    rl2 = lambda a, b: float(torch.linalg.norm((a.double() - b.double())) / torch.linalg.norm(b.double()))
+    cg_vs_plain = max(rl2(a, b) for a, b in zip(outs, outs_plain))
+    pers_vs_plain = max(rl2(a, b) for a, b in zip(outs_pers, outs_plain))
+    cg_oracle = _batch_oracle_errors(inst, {"batched": outs, "persistent": outs_pers,
+                                            "plain": outs_plain}, kmax)
     # block LOBPCG (k = 16, 30 iterations) on every instance: over a pool of 32 streams
     # (bf_batch_lobpcg) against one lobpcg_filter call after another on one stream
     import numpy as np
@@ -769,12 +803,18 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
     from paper_1509_02468_gb300 import synth
     X0s = [torch.as_tensor(synth.block_start(x.cpu().numpy(), 16, seed=4000 + i, dtype=np.float32)).cuda()
            for i, x in enumerate(x0s)]
-    ms_lb = timed(lambda: B.lobpcg(X0s, 30, nstreams=32, sync=False))
+    last = {}
+
+    def batched_lob():
+        last["batched"] = B.lobpcg(X0s, 30, nstreams=32, sync=False)[1]
+    ms_lb = timed(batched_lob)
 
     def plain_lob():
-        for G, X0 in zip(graphs, X0s):
-            bf.lobpcg_filter(G, X0, 30, want_X=False, sync=False)
+        last["plain"] = [bf.lobpcg_filter(G, X0, 30, want_X=False, sync=False)["y"]
+                         for G, X0 in zip(graphs, X0s)]
     ms_lp = timed(plain_lob)
+    torch.cuda.synchronize()
+    lob_vs_plain = max(rl2(a, b) for a, b in zip(last["batched"], last["plain"]))
     B.free()
     return {"workload": "256 instances: 192 images, sides log-uniform in [64, 1024]; 64 signals, "
                         "lengths log-uniform in [1e3, 1e6]; CG 50 (Jacobi), FP32",
@@ -783,7 +823,11 @@ def _run_batched(bf, torch, stream, kmax=50, reps=3):
             "persistent_mpix_s": total / (ms_pers * 1e-3) / 1e6, "persistent_ms": ms_pers,
             "lobpcg_k16x30": {"batched_ms": ms_lb, "batched_mpix_s": total / (ms_lb * 1e-3) / 1e6,
                               "plain_ms": ms_lp, "plain_mpix_s": total / (ms_lp * 1e-3) / 1e6,
-                              "streams": 32},
+                              "streams": 32, "y_batched_vs_plain": lob_vs_plain},
+            "err": {"cg_batched_vs_plain": cg_vs_plain, "cg_persistent_vs_plain": pers_vs_plain,
+                    "cg_vs_oracle": cg_oracle,
+                    "note": "largest relative L2 difference over the 256 instances; against the "
+                            "FP64 oracle's CG on the 4 smallest signals and the 4 smallest images"},
             "persistent_note": "one cooperative launch, bounded grid barriers between phases; "
                                "includes the host read of the barrier flag",
             "plain_mpix_s": total / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,

@@ -28,17 +28,6 @@ extern "C" {
 int bf_rayleigh_ritz(const double* G, int m, int k, int m_nop, double* C, double* Cp,
                      double* theta, int* flags, void* stream);
 
-/* Phase stamps of the Rayleigh-Ritz solves that follow (all callers: bf_rayleigh_ritz and
- * lobpcg_filter): buf (device, max_calls * 24 unsigned 64-bit entries, zeroed by the
- * caller) receives for solve c the global timer in ns at slot 24 c + s: s = 0-4 reduction
- * kernel (start, Cholesky with the forward solve done, standard form done, tridiagonal
- * form done, end); 5-8 eigenpair kernel, block 0 (start, multisection done, inverse
- * iteration done, end); 9-19 finishing kernel (start, scratch loaded, clusters
- * orthonormalised, M X, correction, k x k products, Jacobi, Z, C = R^-T Z, end without
- * Cp, end with Cp); slot 22 holds the number of Jacobi sweeps.  NULL stops recording.
- * Not thread-safe; for timing studies only. */
-int bf_rr_stamps(unsigned long long* buf, int max_calls);
-
 /* The tensor-core Gram products of the LOBPCG Rayleigh-Ritz step (Algorithm 3): with
  * S = [S0 S1 S2] and AS = [AS0 AS1 AS2] (the first nblk blocks, each n x k pixel-major
  * float) and B = diag(b) (b NULL: I), writes G[0] = S^T AS and G[1] = S^T B S (double,

@@ -89,7 +89,6 @@ def _load():
         "lobpcg_filter": [vp, vp, i64, i32, i32, ctypes.POINTER(bf_lobpcg_opts), vp, dp, dp, vp,
                           ctypes.POINTER(bf_info), vp],
         "bf_rayleigh_ritz": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
-        "bf_rr_stamps": [vp, i32],
         "cg_filter_noalloc": [vp, vp, i32, ctypes.POINTER(bf_cg_opts), vp, ctypes.POINTER(bf_info), vp],
         "cg_refine": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(bf_cg_opts), i32, i32, vp,
                       ctypes.POINTER(bf_info), vp],
@@ -390,12 +389,6 @@ def rayleigh_ritz(GA: torch.Tensor, GB: torch.Tensor, k: int, m_nop: int = 0,
                                  _ptr(flags), _stream(stream)))
     f = flags.cpu().tolist()
     return C, theta, Cp, f[0], f[1]
-
-
-def rr_stamps(buf=None, max_calls: int = 0):
-    """Record the phase stamps of the next Rayleigh-Ritz solves into buf (a zeroed CUDA
-    uint64/int64 tensor of max_calls * 24 entries, see bf_rr_stamps); None stops."""
-    _check(_lib.bf_rr_stamps(_ptr(buf) if buf is not None else None, max_calls if buf is not None else 0))
 
 
 class Net:

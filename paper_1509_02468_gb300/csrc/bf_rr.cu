@@ -13,13 +13,16 @@
 //      form, then one warp per eigenpair (a kernel of its own, so the eigenpairs run on
 //      many SMs): its eigenvalue by multisection on Sturm counts, its eigenvector by
 //      inverse iteration and back-transformation; modified Gram-Schmidt inside clusters;
-//   4. X = the k eigenvectors of the smallest lambda, Y = M X in FP64, Rayleigh quotients
-//      theta_j and the FP64 residual r_j = y_j - theta_j x_j;
+//   4. X = the eigenvectors of the k smallest lambda and of the unwanted ones chained to
+//      the k-th closer than the FP32 resolution 64 eps_32 |M| (kk <= 32 in all), Y = M X in
+//      FP64, Rayleigh quotients theta_j and the FP64 residual r_j = y_j - theta_j x_j;
 //   5. first-order correction x_j += sum_i v_i (v_i^T r_j) / (theta_j - lambda_i) over the
 //      unwanted eigenpairs outside a 64 eps_32 |M| neighbourhood of theta_j (FP32 products
 //      of FP64 data; the error of the corrected vectors is second order in the FP32 one);
 //   6. symmetric orthonormalisation T = (X^T X)^-1/2 = I + D, D = -E/2 + 3E^2/8 for
-//      X^T X = I + E, H = T (X^T M X) T in FP64, cyclic Jacobi on the k x k H in FP64;
+//      X^T X = I + E, H = T (X^T M X) T in FP64, cyclic Jacobi on the kk x kk H in FP64,
+//      the k smallest of its eigenvalues kept (so a cluster across the k-th eigenvalue is
+//      split in FP64, not by the FP32 ordering);
 //   7. C = R^-T X T Q with the scaling undone; with Cp requested, the coefficients of the
 //      next P made B-orthogonal to the next X (see the driver).
 // Reciprocals and square roots use an FP32 seed refined by two FP64 Newton steps
@@ -31,37 +34,9 @@
 
 #define RR_T 512
 #define RR_KLD 33           // padded leading dimension of the m x k work matrices
-#define RR_LOW_M 64         // largest m orthonormalised inside clusters by the Lowdin step
-#define RR_LOW_LD 65        // its work matrices' leading dimension
 #define DEP_TOL 1e-10
-#define RR_NSTAMP 24        // phase stamps recorded per solve (testing)
-
-// Phase stamps (testing): when rr_stamp_buf is set, thread 0 of each kernel writes the
-// global timer (ns) at the phase boundaries of solve number rr_stamp_call into
-// rr_stamp_buf[call * RR_NSTAMP + slot]; k_rr advances the call number.
-__device__ unsigned long long* rr_stamp_buf = nullptr;
-__device__ int rr_stamp_max = 0;
-__device__ int rr_stamp_call = 0;
 
 namespace {
-
-struct RRStamp {
-  unsigned long long* buf;
-  __device__ RRStamp() {
-    buf = rr_stamp_buf;
-    if (buf && rr_stamp_call >= rr_stamp_max) buf = nullptr;
-    if (buf) buf += (size_t)rr_stamp_call * RR_NSTAMP;
-  }
-  // called by every thread of the CTA at the same point: a barrier first, so that the
-  // timer is read once every thread has finished the phase
-  __device__ __forceinline__ void operator()(int slot) const {
-    if (buf) {
-      unsigned long long t;
-      asm volatile("bar.sync 0;\n\tmov.u64 %0, %%globaltimer;" : "=l"(t)::"memory");
-      if (threadIdx.x == 0) buf[slot] = t;
-    }
-  }
-};
 
 // 1/x and 1/sqrt(x) from an FP32 seed (relative error < 2^-22) and two Newton steps, each
 // of which squares the relative error; values outside the FP32 range take the exact path.
@@ -223,125 +198,6 @@ __device__ void mul_mx(const double* MA, const double* X, double* Y, int m, cons
   }
 }
 
-// Householder reduction of the symmetric float matrix J (full storage, m <= MR) to a
-// tridiagonal T (diagonal dd, off-diagonal ee), the reflectors I - beta v v^T (v below the
-// subdiagonal of J's columns, beta in bet).  Four threads own a column c (thread q holds the
-// rows r = q mod 4 in registers, MR / 4 of them), so a step reads no matrix entry from
-// shared memory: step j, with x = column j below the diagonal, s = |x|^2, v = x - alpha
-// e_1, beta = 2 / v^T v:  p = beta A v, K = beta v^T p / 2 (a sum over the columns),
-// w = p - K v, A -= v w^T + w v^T.  Column j + 1 and its |x|^2 are published in shared
-// memory for the next step; two barriers per step.  sS, pv: [m]; xv: [2][RR_MMAX];
-// kpart: [RR_NW].
-template <int MR>
-__device__ __forceinline__ void hh_tridiag(float* J, int m, float* dd, float* ee, float* bet, float* sS,
-                                           float* pv, float* xv, float* kpart) {
-  constexpr int NR = MR / 4;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int c = tid >> 2, q = tid & 3;
-  const bool own = tid < 4 * m;
-  const int nwo = (4 * m + 31) / 32;                  // warps that own columns
-  auto sum4 = [](float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v + __shfl_xor_sync(0xffffffffu, v, 2);
-  };
-  float A[NR];
-#pragma unroll
-  for (int u = 0; u < NR; ++u) {
-    const int r = q + 4 * u;
-    A[u] = (own && r < m) ? J[r * RR_LDF + c] : 0.0f;
-  }
-  {
-    float sn = 0.0f;
-    if (own && c == 0)
-#pragma unroll
-      for (int u = 0; u < NR; ++u) {
-        const int r = q + 4 * u;
-        if (r < m) {
-          xv[r] = A[u];
-          if (r > 0) sn = fmaf(A[u], A[u], sn);
-        }
-      }
-    sn = sum4(sn);
-    if (tid == 0) sS[0] = sn;
-  }
-  __syncthreads();
-  const bool wown = wid < nwo;                       // the other warps only meet the barriers
-  for (int j = 0; j + 2 < m; ++j) {
-    const float* xc = xv + (j & 1) * RR_MMAX;        // column j, every row
-    float* xn = xv + ((j + 1) & 1) * RR_MMAX;         // column j + 1, for the next step
-    const bool act = own && c > j;
-    float al = 0.0f, be = 0.0f, pc = 0.0f, vc = 0.0f;
-    float vr[NR];                                     // v at the thread's rows (0 for r <= j)
-    if (wown) {
-      const float sj = sS[j], x0 = xc[j + 1];
-      const float tail = sj - x0 * x0;
-      al = x0;
-      if (tail > 0.0f) {                              // correctly rounded: each reflector is then
-        const float nrm = sqrtf(sj);                  // orthogonal to FP32 rounding
-        al = (x0 >= 0.0f) ? -nrm : nrm;
-        const float v0 = x0 - al;
-        be = 2.0f / fmaf(v0, v0, tail);
-      }
-#pragma unroll
-      for (int u = 0; u < NR; ++u) {
-        const int r = q + 4 * u;
-        vr[u] = (r > j && r < m) ? xc[r] - (r == j + 1 ? al : 0.0f) : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < NR; ++u) pc = fmaf(A[u], vr[u], pc);
-      pc = be * sum4(pc);
-      vc = act ? xc[c] - (c == j + 1 ? al : 0.0f) : 0.0f;
-      float kc = (act && q == 0) ? vc * pc : 0.0f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) kc += __shfl_xor_sync(0xffffffffu, kc, o);
-      if (lane == 0) kpart[wid] = kc;
-      if (act && q == 0) pv[c] = pc;
-    }
-    __syncthreads();
-    if (wown) {
-      if (tid == 0) {
-        dd[j] = xc[j];
-        ee[j] = al;
-        bet[j] = be;
-      }
-      for (int t = tid; t < m - j - 1; t += 32 * nwo) J[(j + 1 + t) * RR_LDF + j] = xc[j + 1 + t] - (t == 0 ? al : 0.0f);
-      float ks = 0.0f;
-      for (int w = 0; w < nwo; ++w) ks += kpart[w];
-      const float K = 0.5f * be * ks;
-      if (act) {
-        const float wc = fmaf(-K, vc, pc);
-#pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          const int r = q + 4 * u;
-          const float pr = (r > j && r < m) ? pv[r] : 0.0f;
-          const float wr = fmaf(-K, vr[u], pr);
-          A[u] = fmaf(-vr[u], wc, fmaf(-wr, vc, A[u]));
-        }
-      }
-      float sn = 0.0f;
-      if (own && c == j + 1)
-#pragma unroll
-        for (int u = 0; u < NR; ++u) {
-          const int r = q + 4 * u;
-          if (r < m) {
-            xn[r] = A[u];
-            if (r > j + 1) sn = fmaf(A[u], A[u], sn);
-          }
-        }
-      sn = sum4(sn);
-      if (own && c == j + 1 && q == 0) sS[j + 1] = sn;
-    }
-    __syncthreads();
-  }
-  if (own && c + 2 >= m)                              // the trailing 2 x 2 block
-#pragma unroll
-    for (int u = 0; u < NR; ++u) {
-      const int r = q + 4 * u;
-      if (r + 2 >= m && r < m) J[r * RR_LDF + c] = A[u];
-    }
-  __syncthreads();
-}
-
 // Part 1 (one CTA): scaling, Cholesky with the forward solve, standard form, FP32
 // tridiagonal reduction; hands M, R, T and the reflectors to the next kernels.
 __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
@@ -381,8 +237,6 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
   const int k = a.k;
   const Tiling tk(k, lane);
   int m = a.m;
-  const RRStamp stamp;
-  stamp(0);
   if (tid == 0) dropped = 0;
   for (int r = wid; r < a.m; r += RR_NW)
     for (int l = lane; l <= r; l += 32) tri[r * (r + 1) / 2 + l] = (unsigned short)((r << 8) | l);
@@ -468,7 +322,6 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
     if (tid == 0) *a.status = 2;
     return;
   }
-  stamp(1);
   for (int i = wid; i < m; i += RR_NW)              // R(i, c) = c_i rdg_c, Y(i, :) *= rdg_i
     for (int c = lane; c < m; c += 32) {
       if (c < i) RB[i * RR_LD + c] *= rdg[c];
@@ -509,20 +362,93 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
     for (int c = r + 1 + lane; c < m; c += 32) MA[r * RR_LD + c] = RB[c * RR_LD + r];
   __syncthreads();
 
-  stamp(2);
   // ------------------------------------------ 4. FP32 eigen-decomposition of M
   // 4a. Householder reduction of float(M) (full storage in J) to a tridiagonal T; the
-  //     reflector vectors stay below the subdiagonal of J (hh_tridiag).
+  //     reflector vectors stay below the subdiagonal of J.  Look-ahead: in step j warp 0
+  //     updates column j + 1 first and forms the reflector of step j + 1 while the other
+  //     warps update the rest of the trailing block; K = beta v^T p / 2 is summed by every
+  //     warp itself (the same lanes and order, so the same value).  Two barriers per step.
   for (int r = wid; r < m; r += RR_NW)
     for (int c = lane; c < m; c += 32) J[r * RR_LDF + c] = (float)symv(MA, r, c);
   __syncthreads();
-  {
-    float* xv = reinterpret_cast<float*>(fv);       // [2][96] floats in fv's [2][96] doubles
-    float* kpart = reinterpret_cast<float*>(th);    // [16] floats in th's [32] doubles
-    if (m <= 48)
-      hh_tridiag<48>(J, m, dd32, ee32, bet32, e2f, pv32, xv, kpart);
-    else
-      hh_tridiag<RR_MMAX>(J, m, dd32, ee32, bet32, e2f, pv32, xv, kpart);
+  // reflector of column j (warp 0): x = J(j+1:m, j) -> v = x - alpha e_1, beta = 2 / v^T v
+  auto reflector = [&](int j) {
+    const int n1 = m - j - 1;
+    float* col = J + (j + 1) * RR_LDF + j;
+    float s = 0.0f;
+    for (int i = lane; i < n1; i += 32) s = fmaf(col[i * RR_LDF], col[i * RR_LDF], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const float x0 = col[0];
+      const float tail = s - x0 * x0;
+      float al = x0, be = 0.0f;
+      if (tail > 0.0f) {
+        const float nrm = sqrtf(s);
+        al = (x0 >= 0.0f) ? -nrm : nrm;
+        const float v0 = x0 - al;
+        be = 2.0f / fmaf(v0, v0, tail);
+        col[0] = v0;
+      }
+      dd32[j] = J[j * RR_LDF + j];
+      ee32[j] = al;
+      bet32[j] = be;
+    }
+  };
+  if (m >= 3 && wid == 0) reflector(0);
+  __syncthreads();
+  for (int j = 0; j + 2 < m; ++j) {
+    const int n1 = m - j - 1;
+    const bool next = (j + 3 < m);
+    const float beta = bet32[j];
+    float* col = J + (j + 1) * RR_LDF + j;          // v_i = col[i * RR_LDF], i < n1
+    float* A1 = J + (j + 1) * RR_LDF + (j + 1);      // trailing n1 x n1 block
+    if (beta == 0.0f) {                              // nothing to reflect: next column as is
+      if (next && wid == 0) reflector(j + 1);
+      __syncthreads();
+      continue;
+    }
+    // p = beta A1 v: a warp takes rows r, r + RR_NW, r + 2 RR_NW together, so that their
+    // shuffle reductions are independent and overlap
+    for (int r = wid; r < n1; r += 3 * RR_NW) {
+      const int r1 = r + RR_NW, r2 = r + 2 * RR_NW;
+      float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+      for (int c = lane; c < n1; c += 32) {
+        const float vc = col[c * RR_LDF];
+        s0 = fmaf(A1[r * RR_LDF + c], vc, s0);
+        if (r1 < n1) s1 = fmaf(A1[r1 * RR_LDF + c], vc, s1);
+        if (r2 < n1) s2 = fmaf(A1[r2 * RR_LDF + c], vc, s2);
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        pv32[r] = beta * s0;
+        if (r1 < n1) pv32[r1] = beta * s1;
+        if (r2 < n1) pv32[r2] = beta * s2;
+      }
+    }
+    __syncthreads();
+    float K = 0.0f;
+    for (int i = lane; i < n1; i += 32) K = fmaf(col[i * RR_LDF], pv32[i], K);
+    K = 0.5f * beta * warp_sum(K);
+    if (wid == 0) {                                   // column j + 1 of J, then its reflector
+      const float v0 = col[0], w0 = fmaf(-K, v0, pv32[0]);
+      for (int r = lane; r < n1; r += 32) {
+        const float vr = col[r * RR_LDF], wr = fmaf(-K, vr, pv32[r]);
+        A1[r * RR_LDF] = fmaf(-vr, w0, fmaf(-wr, v0, A1[r * RR_LDF]));
+      }
+      __syncwarp();
+      if (next) reflector(j + 1);
+    } else {                                          // A1(1:, 1:) -= v w^T + w v^T, w = p - K v
+      for (int r = wid; r < n1; r += RR_NW - 1) {     // rows 1 .. n1-1 over warps 1 .. RR_NW-1
+        const float vr = col[r * RR_LDF], wr = fmaf(-K, vr, pv32[r]);
+        for (int c = 1 + lane; c < n1; c += 32) {
+          const float vc = col[c * RR_LDF], wc = fmaf(-K, vc, pv32[c]);
+          A1[r * RR_LDF + c] = fmaf(-vr, wc, fmaf(-wr, vc, A1[r * RR_LDF + c]));
+        }
+      }
+    }
+    __syncthreads();
   }
   if (tid == 0) {
     if (m >= 2) {
@@ -542,7 +468,6 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
     shhi = hi;
   }
   __syncthreads();
-  stamp(3);
   for (int i = tid; i < m; i += RR_T) e2f[i] = ee32[i] * ee32[i];
   __syncthreads();
   RRScratch* S = a.scr;
@@ -566,7 +491,6 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
     S->m = m;
     S->dropped = dropped;
   }
-  stamp(4);
 }
 
 // Part 2 (one warp per eigenpair j of T): the j-th eigenvalue by multisection on Sturm
@@ -577,9 +501,6 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
   RRScratch* S = a.scr;
   const int m = S->m, j = blockIdx.x, lane = threadIdx.x;
   if (j >= m) return;
-  RRStamp stamp;
-  if (j != 0) stamp.buf = nullptr;
-  stamp(5);
   __shared__ float dd[RR_MMAX], ee[RR_MMAX], e2[RR_MMAX], v[RR_MMAX], bet[RR_MMAX];
   __shared__ float f[RR_MMAX], ri[RR_MMAX], u1[RR_MMAX], u2[RR_MMAX];
   __shared__ unsigned char sw[RR_MMAX];
@@ -629,7 +550,6 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
     lo = nlo;
     hi = nhi;
   }
-  stamp(6);
   const float lamj = 0.5f * (lo + hi);
   // start vectors differ per index, so a cluster's vectors span the cluster's subspace
   for (int i = lane; i < m; i += 32) v[i] = 1.0f + 0.25f * (float)(((i + 1) * (j + 3) * 7919) % 97) / 97.0f;
@@ -639,7 +559,6 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
     tri_inverse_iteration(dd, ee, m, lamj, 4.0f * 6e-8f * tn + 1e-30f, 3, v, f, ri, u1, u2, sw);
   }
   __syncwarp();
-  stamp(7);
   // back-transformation by the reflectors (last first): the vector stays in registers
   // (entry i in lane i % 32, slot i / 32) and the next reflector column is loaded ahead,
   // so each reflector costs one FMA, one shuffle reduction and one FMA on the chain
@@ -672,7 +591,6 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
     const int i = lane + 32 * s3;
     if (i < m) S->V[i * RR_LDF + j] = vr[s3];
   }
-  stamp(8);
 }
 
 // Part 3 (one CTA): Gram-Schmidt inside clusters (on the back-transformed vectors, which
@@ -721,14 +639,13 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   float* E32 = reinterpret_cast<float*>(K64 + RR_KMAX * RR_KLD);  // [32][RR_KLD]
   float* D32 = E32 + RR_KMAX * RR_KLD;                    // [32][RR_KLD]
   __shared__ int dropped;
+  __shared__ int kext;
   __shared__ float lmax;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int k = a.k;
   const Tiling tk(k, lane);
   int m = a.m;
-  const RRStamp stamp;
-  stamp(9);
   if (tid == 0) dropped = 0;
   for (int r = wid; r < a.m; r += RR_NW)
     for (int l = lane; l <= r; l += 32) tri[r * (r + 1) / 2 + l] = (unsigned short)((r << 8) | l);
@@ -749,197 +666,75 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     }
   }
   __syncthreads();
-  stamp(10);
   const float clus = 1e-3f * a.scr->tn;             // eigenvalues closer than this: a cluster
-  // 4d. orthonormalise within clusters.  The vectors come out of inverse iteration scaled
-  //     by their largest entry and, inside a cluster, only approximately orthogonal.
-  //     For m <= 64: normalise, then the symmetric (Lowdin) orthonormalisation of each
-  //     cluster block, V_c <- V_c (I + D), D = -E/2 + 3/8 E^2 - 5/16 E^3 for
-  //     E = V_c^T V_c - I (error O(|E|^4)), all clusters at once and every entry in
-  //     parallel; applied a second time when max |E| > 1e-2.  With max |E| > 0.1 (or
-  //     m > 64) the sequential Gram-Schmidt below runs instead.
-  bool gs = (m > RR_LOW_M);
-  if (!gs) {
-    int* cs = rk;                                   // each index's cluster [cs, ce) (rk, pp, qq
-    int* ce = pp;                                   // are free here; pp and qq are contiguous)
-    for (int i = tid; i < m; i += RR_T) {
-      int b = i, e = i + 1;
-      while (b > 0 && lam[b] - lam[b - 1] < clus) --b;
-      while (e < m && lam[e] - lam[e - 1] < clus) ++e;
-      cs[i] = b;
-      ce[i] = e;
-    }
-    for (int c = tid; c < m; c += RR_T) {           // 2-norm normalisation of every column
-      float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
-      int r = 0;
-      for (; r + 3 < m; r += 4) {
-        n0 = fmaf(V[r * RR_LDF + c], V[r * RR_LDF + c], n0);
-        n1 = fmaf(V[(r + 1) * RR_LDF + c], V[(r + 1) * RR_LDF + c], n1);
-        n2 = fmaf(V[(r + 2) * RR_LDF + c], V[(r + 2) * RR_LDF + c], n2);
-        n3 = fmaf(V[(r + 3) * RR_LDF + c], V[(r + 3) * RR_LDF + c], n3);
-      }
-      for (; r < m; ++r) n0 = fmaf(V[r * RR_LDF + c], V[r * RR_LDF + c], n0);
-      const float nn = (n0 + n1) + (n2 + n3);
-      pv32[c] = (nn > 0.0f) ? rsqrtf(nn) : 0.0f;
-    }
-    __syncthreads();
-    for (int q = tid; q < m * m; q += RR_T) {
-      const int r = q / m, c = q - r * m;
-      V[r * RR_LDF + c] *= pv32[c];
-    }
-    __syncthreads();
-    float* E = reinterpret_cast<float*>(XD);        // [m][RR_LOW_LD] each, in X/Y's region
-    float* E2 = E + RR_LOW_M * RR_LOW_LD;
-    float* Dm = E2 + RR_LOW_M * RR_LOW_LD;
-    int again = 0;
-    for (int app = 0; app < 2; ++app) {
-      int big = 0, mid = 0;
-      for (int q = tid; q < m * m; q += RR_T) {     // E within clusters
-        const int i = q / m, j = q - i * m;
-        float e = 0.0f;
-        if (cs[i] == cs[j]) {
-          float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+  // 4d. orthonormalise within clusters, normalise the rest: classical Gram-Schmidt applied
+  //     twice (orthogonal to working precision like the modified form); lane t forms the
+  //     whole dot product with column j + t of the cluster, so no shuffle reduction is on
+  //     the chain, and the projections are then removed row by row.  The coefficients go
+  //     to the warp's slice of J's region (free until step 7).
+  for (int j = wid; j < m; j += RR_NW) {
+    if (j > 0 && lam[j] - lam[j - 1] < clus) continue;   // not the first of its cluster
+    int e = j + 1;
+    while (e < m && lam[e] - lam[e - 1] < clus) ++e;
+    float* dsc = J + wid * RR_MMAX;
+    for (int i = j; i < e; ++i) {
+      for (int pass = 0; pass < 2 && i > j; ++pass) {
+        for (int l = j + lane; l < i; l += 32) {
+          float d0 = 0.0f, d1 = 0.0f;
           int r = 0;
-          for (; r + 3 < m; r += 4) {
-            d0 = fmaf(V[r * RR_LDF + i], V[r * RR_LDF + j], d0);
-            d1 = fmaf(V[(r + 1) * RR_LDF + i], V[(r + 1) * RR_LDF + j], d1);
-            d2 = fmaf(V[(r + 2) * RR_LDF + i], V[(r + 2) * RR_LDF + j], d2);
-            d3 = fmaf(V[(r + 3) * RR_LDF + i], V[(r + 3) * RR_LDF + j], d3);
+          for (; r + 1 < m; r += 2) {
+            d0 = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d0);
+            d1 = fmaf(V[(r + 1) * RR_LDF + l], V[(r + 1) * RR_LDF + i], d1);
           }
-          for (; r < m; ++r) d0 = fmaf(V[r * RR_LDF + i], V[r * RR_LDF + j], d0);
-          e = ((d0 + d1) + (d2 + d3)) - (i == j ? 1.0f : 0.0f);
+          if (r < m) d0 = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d0);
+          dsc[l - j] = d0 + d1;
         }
-        E[i * RR_LOW_LD + j] = e;
-        big |= (fabsf(e) > 0.1f);
-        mid |= (fabsf(e) > 1e-2f);
-      }
-      // each flag ORed over the CTA (also the barrier before E is read)
-      const int fbig = __syncthreads_or(big), fmid = __syncthreads_or(mid);
-      if (app == 0) {
-        if (fbig) {
-          gs = true;
-          break;
+        __syncwarp();
+        for (int r = lane; r < m; r += 32) {
+          float x = V[r * RR_LDF + i];
+          for (int l = j; l < i; ++l) x = fmaf(-dsc[l - j], V[r * RR_LDF + l], x);
+          V[r * RR_LDF + i] = x;
         }
-        again = fmid;
-      }
-      {
-        for (int q = tid; q < m * m; q += RR_T) {   // E^2
-          const int i = q / m, j = q - i * m;
-          float e2 = 0.0f, e2b = 0.0f;
-          if (cs[i] == cs[j]) {
-            const int l1 = ce[i];
-            int l = cs[i];
-            for (; l + 1 < l1; l += 2) {
-              e2 = fmaf(E[i * RR_LOW_LD + l], E[l * RR_LOW_LD + j], e2);
-              e2b = fmaf(E[i * RR_LOW_LD + l + 1], E[(l + 1) * RR_LOW_LD + j], e2b);
-            }
-            if (l < l1) e2 = fmaf(E[i * RR_LOW_LD + l], E[l * RR_LOW_LD + j], e2);
-          }
-          E2[i * RR_LOW_LD + j] = e2 + e2b;
-        }
-        __syncthreads();
-        for (int q = tid; q < m * m; q += RR_T) {   // D = -E/2 + 3/8 E^2 - 5/16 E^3
-          const int i = q / m, j = q - i * m;
-          float e3 = 0.0f, e3b = 0.0f;
-          if (cs[i] == cs[j]) {
-            const int l1 = ce[i];
-            int l = cs[i];
-            for (; l + 1 < l1; l += 2) {
-              e3 = fmaf(E[i * RR_LOW_LD + l], E2[l * RR_LOW_LD + j], e3);
-              e3b = fmaf(E[i * RR_LOW_LD + l + 1], E2[(l + 1) * RR_LOW_LD + j], e3b);
-            }
-            if (l < l1) e3 = fmaf(E[i * RR_LOW_LD + l], E2[l * RR_LOW_LD + j], e3);
-            e3 += e3b;
-          }
-          Dm[i * RR_LOW_LD + j] =
-              fmaf(-0.5f, E[i * RR_LOW_LD + j], fmaf(0.375f, E2[i * RR_LOW_LD + j], -0.3125f * e3));
-        }
-        __syncthreads();
-        for (int r = wid; r < m; r += RR_NW) {      // V(r, :) += V(r, :) D, a row per warp
-          float nv[RR_LOW_M / 32];
-#pragma unroll
-          for (int u = 0; u < RR_LOW_M / 32; ++u) {
-            const int j = lane + 32 * u;
-            float x = 0.0f;
-            if (j < m) {
-              float y = 0.0f;
-              const int l1 = ce[j];
-              int l = cs[j];
-              x = V[r * RR_LDF + j];
-              for (; l + 1 < l1; l += 2) {
-                x = fmaf(V[r * RR_LDF + l], Dm[l * RR_LOW_LD + j], x);
-                y = fmaf(V[r * RR_LDF + l + 1], Dm[(l + 1) * RR_LOW_LD + j], y);
-              }
-              if (l < l1) x = fmaf(V[r * RR_LDF + l], Dm[l * RR_LOW_LD + j], x);
-              x += y;
-            }
-            nv[u] = x;
-          }
-          __syncwarp();
-#pragma unroll
-          for (int u = 0; u < RR_LOW_M / 32; ++u)
-            if (lane + 32 * u < m) V[r * RR_LDF + lane + 32 * u] = nv[u];
-        }
-        __syncthreads();
-      }
-      if (!again) break;
-    }
-  }
-  if (gs) {
-    for (int j = wid; j < m; j += RR_NW) {
-      if (j > 0 && lam[j] - lam[j - 1] < clus) continue;   // not the first of its cluster
-      int e = j + 1;
-      while (e < m && lam[e] - lam[e - 1] < clus) ++e;
-      float* dsc = J + wid * RR_MMAX;
-      for (int i = j; i < e; ++i) {
-        for (int pass = 0; pass < 2 && i > j; ++pass) {
-          for (int l = j + lane; l < i; l += 32) {
-            float d0 = 0.0f, d1 = 0.0f;
-            int r = 0;
-            for (; r + 1 < m; r += 2) {
-              d0 = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d0);
-              d1 = fmaf(V[(r + 1) * RR_LDF + l], V[(r + 1) * RR_LDF + i], d1);
-            }
-            if (r < m) d0 = fmaf(V[r * RR_LDF + l], V[r * RR_LDF + i], d0);
-            dsc[l - j] = d0 + d1;
-          }
-          __syncwarp();
-          for (int r = lane; r < m; r += 32) {
-            float x = V[r * RR_LDF + i];
-            for (int l = j; l < i; ++l) x = fmaf(-dsc[l - j], V[r * RR_LDF + l], x);
-            V[r * RR_LDF + i] = x;
-          }
-          __syncwarp();
-        }
-        float n2 = 0.0f;
-        for (int r = lane; r < m; r += 32) n2 = fmaf(V[r * RR_LDF + i], V[r * RR_LDF + i], n2);
-        n2 = warp_sum(n2);
-        const float inv = (n2 > 0.0f) ? rsqrtf(n2) : 0.0f;
-        for (int r = lane; r < m; r += 32) V[r * RR_LDF + i] *= inv;
         __syncwarp();
       }
+      float n2 = 0.0f;
+      for (int r = lane; r < m; r += 32) n2 = fmaf(V[r * RR_LDF + i], V[r * RR_LDF + i], n2);
+      n2 = warp_sum(n2);
+      const float inv = (n2 > 0.0f) ? rsqrtf(n2) : 0.0f;
+      for (int r = lane; r < m; r += 32) V[r * RR_LDF + i] *= inv;
+      __syncwarp();
     }
-    __syncthreads();
   }
   __syncthreads();
 
-  stamp(11);
   // ------------------------------------------ 5. the k smallest FP32 eigenpairs
-  // (multisection returns the eigenvalues in ascending order)
+  // (multisection returns the eigenvalues in ascending order), extended to kk >= k by the
+  // unwanted eigenpairs chained to the k-th within the FP32 resolution: their FP32 vectors
+  // are mixed with the wanted ones, which the correction below cannot separate (it skips
+  // pairs that close), so the FP64 Rayleigh-Ritz of step 8 runs on all kk and the k
+  // smallest are taken after it
   if (tid < m) rk[tid] = tid;
-  if (tid < k) sel[tid] = tid;
-  if (tid == 0) lmax = fmaxf(fabsf(lam[0]), fabsf(lam[m - 1]));
+  if (tid == 0) {
+    lmax = fmaxf(fabsf(lam[0]), fabsf(lam[m - 1]));
+    const float dres = 64.0f * 6e-8f * lmax;
+    int e = k;
+    while (e < m && e < RR_KMAX && lam[e] - lam[e - 1] <= dres) ++e;
+    kext = e;
+  }
+  __syncthreads();
+  const int kk = kext;
+  const Tiling tkk(kk, lane);
+  if (tid < kk) sel[tid] = tid;
   __syncthreads();
 
   // ------------------------------------------ 6. X = V(:, sel) in FP64, Y = M X
-  FOR_RC(tk, m, k, wid) XD[r * RR_KLD + c] = (double)V[r * RR_LDF + sel[c]];
+  FOR_RC(tkk, m, kk, wid) XD[r * RR_KLD + c] = (double)V[r * RR_LDF + sel[c]];
   __syncthreads();
-  mul_mx(MA, XD, YD, m, tk, k, wid);
+  mul_mx(MA, XD, YD, m, tkk, kk, wid);
   __syncthreads();
 
-  stamp(12);
   // ------------------------------------------ 7. one correction of X from the FP64 residual
-  for (int j = wid; j < k; j += RR_NW) {
+  for (int j = wid; j < kk; j += RR_NW) {
     double xy = 0.0, xx = 0.0;
     for (int r = lane; r < m; r += 32) {
       xy = fma(XD[r * RR_KLD + j], YD[r * RR_KLD + j], xy);
@@ -950,12 +745,12 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     if (lane == 0) th[j] = xy * frcp(xx);
   }
   __syncthreads();
-  FOR_RC(tk, m, k, wid) R32[r * RR_KLD + c] = (float)fma(-th[c], XD[r * RR_KLD + c], YD[r * RR_KLD + c]);
+  FOR_RC(tkk, m, kk, wid) R32[r * RR_KLD + c] = (float)fma(-th[c], XD[r * RR_KLD + c], YD[r * RR_KLD + c]);
   __syncthreads();
   {
     const float delta = 64.0f * 6e-8f * lmax;      // unwanted: beyond the FP32 resolution
     const float delta_w = 1e-3f * lmax;             // wanted pairs: well separated only
-    FOR_RC(tk, m, k, wid) {                         // r: eigenpair i, c: column j
+    FOR_RC(tkk, m, kk, wid) {                       // r: eigenpair i, c: column j
       float f0 = 0.0f, f1 = 0.0f;
       int q = 0;
       for (; q + 1 < m; q += 2) {
@@ -966,11 +761,11 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
       const float gap = (float)th[c] - lam[r];
       // close wanted directions are mixed by the k x k Rayleigh-Ritz below; correcting
       // only well-separated ones keeps X'^T X' - I of order eps_32 |M| / delta_w
-      CC[r * RR_KLD + c] = (fabsf(gap) > (rk[r] >= k ? delta : delta_w)) ? (f0 + f1) / gap : 0.0f;
+      CC[r * RR_KLD + c] = (fabsf(gap) > (rk[r] >= kk ? delta : delta_w)) ? (f0 + f1) / gap : 0.0f;
     }
   }
   __syncthreads();
-  FOR_RC(tk, m, k, wid) {                           // X' = X + V CC
+  FOR_RC(tkk, m, kk, wid) {                         // X' = X + V CC
     float d0 = 0.0f, d1 = 0.0f;
     int i = 0;
     for (; i + 1 < m; i += 2) {
@@ -981,16 +776,15 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     XD[r * RR_KLD + c] += (double)(d0 + d1);
   }
   __syncthreads();
-  mul_mx(MA, XD, YD, m, tk, k, wid);                // Y' = M X'
+  mul_mx(MA, XD, YD, m, tkk, kk, wid);              // Y' = M X'
   __syncthreads();
 
-  stamp(13);
   // ------------------------------------------ 8. orthonormalise, k x k Rayleigh-Ritz
   // G = X'^T X' = I + E with |E| <= 1e-4, so T = G^-1/2 = I + D with
   // D = -E/2 + 3/8 E^2 - 5/16 E^3 to O(|E|^4) (E^2, E^3 in FP32); H = T H' T with
   // H' = X'^T M X', in FP64.
-  FOR_RC(tk, 2 * k, k, wid) {
-    const int which = (r >= k), i = r - which * k;
+  FOR_RC(tkk, 2 * kk, kk, wid) {
+    const int which = (r >= kk), i = r - which * kk;
     if (which == 0 && c < i) continue;
     const double* B2 = which ? YD : XD;
     double s0 = 0.0, s1 = 0.0;
@@ -1012,43 +806,42 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     }
   }
   __syncthreads();
-  FOR_RC(tk, k, k, wid) {                           // E^2 (FP32, into D32)
+  FOR_RC(tkk, kk, kk, wid) {                        // E^2 (FP32, into D32)
     float s = 0.0f;
-    for (int l = 0; l < k; ++l) s = fmaf(E32[r * RR_KLD + l], E32[l * RR_KLD + c], s);
+    for (int l = 0; l < kk; ++l) s = fmaf(E32[r * RR_KLD + l], E32[l * RR_KLD + c], s);
     D32[r * RR_KLD + c] = s;
   }
   __syncthreads();
-  FOR_RC(tk, k, k, wid) {                           // D = -E/2 + 3/8 E^2 - 5/16 E^3
+  FOR_RC(tkk, kk, kk, wid) {                        // D = -E/2 + 3/8 E^2 - 5/16 E^3
     float e3 = 0.0f;
-    for (int l = 0; l < k; ++l) e3 = fmaf(E32[r * RR_KLD + l], D32[l * RR_KLD + c], e3);
+    for (int l = 0; l < kk; ++l) e3 = fmaf(E32[r * RR_KLD + l], D32[l * RR_KLD + c], e3);
     K64[r * RR_KLD + c] = fma(-0.5, D64[r * RR_KLD + c], (double)fmaf(-0.3125f, e3, 0.375f * D32[r * RR_KLD + c]));
   }
   __syncthreads();
-  FOR_RC(tk, k, k, wid) {
+  FOR_RC(tkk, kk, kk, wid) {
     const double d = K64[r * RR_KLD + c];
     D64[r * RR_KLD + c] = d;
     D32[r * RR_KLD + c] = (float)d;
   }
   __syncthreads();
-  FOR_RC(tk, k, k, wid) {                           // K = H' D
+  FOR_RC(tkk, kk, kk, wid) {                        // K = H' D
     double s = 0.0;
-    for (int l = 0; l < k; ++l) s = fma(H[r * RR_KLD + l], D64[l * RR_KLD + c], s);
+    for (int l = 0; l < kk; ++l) s = fma(H[r * RR_KLD + l], D64[l * RR_KLD + c], s);
     K64[r * RR_KLD + c] = s;
   }
   __syncthreads();
-  FOR_RC(tk, k, k, wid) {                           // H = H' + K + D (H' + K)
+  FOR_RC(tkk, kk, kk, wid) {                        // H = H' + K + D (H' + K)
     double s = K64[r * RR_KLD + c];
-    for (int l = 0; l < k; ++l) s = fma(D64[r * RR_KLD + l], H[l * RR_KLD + c] + K64[l * RR_KLD + c], s);
+    for (int l = 0; l < kk; ++l) s = fma(D64[r * RR_KLD + l], H[l * RR_KLD + c] + K64[l * RR_KLD + c], s);
     Wk[r * RR_KLD + c] = H[r * RR_KLD + c] + s;
   }
   __syncthreads();
-  stamp(14);
-  const int kp = k + (k & 1);
+  const int kp = kk + (kk & 1);
   const int kh = kp / 2;
   for (int i = wid; i < kp; i += RR_NW)
     for (int j = lane; j < kp; j += 32) {
       double v;
-      if (i < k && j < k) v = 0.5 * (Wk[i * RR_KLD + j] + Wk[j * RR_KLD + i]);
+      if (i < kk && j < kk) v = 0.5 * (Wk[i * RR_KLD + j] + Wk[j * RR_KLD + i]);
       else v = (i == j) ? 1e300 : 0.0;
       H[i * RR_KLD + j] = v;
       Vk[i * RR_KLD + j] = (i == j) ? 1.0 : 0.0;
@@ -1057,12 +850,10 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
   // Cyclic Jacobi in FP64: the angle is taken in FP32 (it only has to shrink the coupling),
   // the rotation itself is exactly orthogonal in FP64; couplings below 1e-13 of the
   // diagonal entries cannot change an eigenvalue beyond rounding and are left alone.
-  int nsweeps = 0;
   if (kp > 1) {
     const FastDiv fkp(kp);
     const int nblk = kh * (kh + 1) / 2;
     for (int sweep = 0; sweep < 30; ++sweep) {
-      nsweeps = sweep + 1;
       // a sweep that would rotate nothing ends the iteration: every pair is tested at
       // once (one barrier) instead of round by round (kp - 1 barriers)
       int need = 0;
@@ -1176,38 +967,35 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
       if (nrot == 0) break;
     }
   }
-  stamp(15);
-  if (stamp.buf && tid == 0) stamp.buf[22] = (unsigned long long)nsweeps;
-  for (int i = tid; i < k; i += RR_T) {
+  for (int i = tid; i < kk; i += RR_T) {             // ascending order of the kk values
     const double li = H[i * RR_KLD + i];
     int rank = 0;
-    for (int j = 0; j < k; ++j) {
+    for (int j = 0; j < kk; ++j) {
       const double lj = H[j * RR_KLD + j];
       rank += (lj < li) || (lj == li && j < i);
     }
     perm[rank] = i;
   }
   __syncthreads();
-  FOR_RC(tk, k, k, wid) {                           // W = T Vk(:, perm) = Vk + D Vk (FP32 part)
-    const int pj = perm[c];
+  FOR_RC(tk, kk, k, wid) {                          // W = T Vk(:, perm) = Vk + D Vk (FP32 part),
+    const int pj = perm[c];                         // the k smallest of the kk
     float s = 0.0f;
-    for (int l = 0; l < k; ++l) s = fmaf(D32[r * RR_KLD + l], (float)Vk[l * RR_KLD + pj], s);
+    for (int l = 0; l < kk; ++l) s = fmaf(D32[r * RR_KLD + l], (float)Vk[l * RR_KLD + pj], s);
     Wk[r * RR_KLD + c] = Vk[r * RR_KLD + pj] + (double)s;
   }
   __syncthreads();
   FOR_RC(tk, m, k, wid) {                           // Z = X' W
     double s0 = 0.0, s1 = 0.0;
     int i = 0;
-    for (; i + 1 < k; i += 2) {
+    for (; i + 1 < kk; i += 2) {
       s0 = fma(XD[r * RR_KLD + i], Wk[i * RR_KLD + c], s0);
       s1 = fma(XD[r * RR_KLD + i + 1], Wk[(i + 1) * RR_KLD + c], s1);
     }
-    if (i < k) s0 = fma(XD[r * RR_KLD + i], Wk[i * RR_KLD + c], s0);
+    if (i < kk) s0 = fma(XD[r * RR_KLD + i], Wk[i * RR_KLD + c], s0);
     YD[r * RR_KLD + c] = s0 + s1;
   }
   __syncthreads();
 
-  stamp(16);
   // ------------------------------------------ 9. C = R^-T Z (rows from the bottom), unscale
   // Look-ahead: in step i warp 0 updates row i - 1 and forms its multipliers while the
   // other warps update the rows above it; one barrier per row.
@@ -1229,7 +1017,6 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     }
     __syncthreads();
   }
-  stamp(17);
   FOR_RC(tk, a.m, k, wid) a.C[r * k + c] = (r < m) ? YD[r * RR_KLD + c] * (rdg[r] * sc[r]) : 0.0;
   if (tid < k) {
     const double thv = H[perm[tid] * RR_KLD + perm[tid]];
@@ -1238,8 +1025,6 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     if (!isfinite(thv)) *a.status = 3;
   }
   if (tid == 0 && dropped && a.restarts) *a.restarts += 1;
-  stamp(18);
-  if (stamp.buf && tid == 0) atomicAdd(&rr_stamp_call, 1);
   if (!a.Cp) return;
   // ------------------------------------------ 10. coefficients of the next P, B-orthogonal
   // to the next X:  Cw = C with the X rows zeroed,  Z2 = C^T G_B Cw,  Cp = Cw - C Z2.
@@ -1278,8 +1063,6 @@ __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
     for (int i = 0; i < k; ++i) acc = fma(-Cs[r * k + i], Z2[i * k + c], acc);
     a.Cp[r * k + c] = acc;
   }
-  __syncthreads();
-  stamp(19);
 }
 
 size_t rr_smem_bytes() {
@@ -1329,19 +1112,4 @@ extern "C" int bf_rayleigh_ritz(const double* G, int m, int k, int m_nop, double
   if (!scr[dev]) BF_CUDA(cudaMalloc(&scr[dev], sizeof(RRScratch)));
   a.scr = scr[dev];
   return bf_rr_launch(a, (cudaStream_t)stream);
-}
-
-// Phase stamps of the next solves (testing): buf is a device array of max_calls * 24
-// entries, NULL to stop recording.  Slots: 0-4 k_rr_reduce (start, Cholesky done, standard
-// form done, tridiagonal form done, end), 5-8 k_rr_vectors block 0 (start, multisection,
-// inverse iteration, end), 9-19 k_rr (start, scratch loaded, clusters orthonormalised,
-// M X, correction, k x k products, Jacobi, Z, C = R^-T Z, end without Cp, end with Cp),
-// 22 the number of Jacobi sweeps.  Values are global-timer nanoseconds.
-extern "C" int bf_rr_stamps(unsigned long long* buf, int max_calls) {
-  if (max_calls < 0 || (buf && max_calls == 0)) return bf_fail(BF_EINVAL, "bf_rr_stamps: bad size");
-  const int zero = 0;
-  BF_CUDA(cudaMemcpyToSymbol(rr_stamp_buf, &buf, sizeof(buf)));
-  BF_CUDA(cudaMemcpyToSymbol(rr_stamp_max, &max_calls, sizeof(int)));
-  BF_CUDA(cudaMemcpyToSymbol(rr_stamp_call, &zero, sizeof(int)));
-  return BF_OK;
 }

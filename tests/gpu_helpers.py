@@ -17,6 +17,13 @@ TOL_RITZ = 1e-6
 # followed by the cancellation in R = AX - B X theta, add a few times that on the GPU
 # (up to 1.7e-6 measured).  The configuration-size runs are held to TOL_RITZ.
 TOL_RITZ_SMALL_F32 = 3e-6
+# Ritz values below the A8 floor (the tiny smallest eigenvalues of small instances, where
+# 1e-3 theta_max is below 1e-5): 1e-6 relative to the norm of the pencil (L, D), whose
+# spectral radius is below 2 (Gershgorin on D^-1 L).  The FP32 Gram products carry absolute
+# errors of order 2^-24 times that radius per entry, and Weyl's inequality passes the norm
+# of the m x m error matrix (up to m times an entry) to the Ritz values, so there the
+# reachable accuracy is absolute, not relative to theta.
+TOL_RITZ_ABS = 2e-6
 
 
 def bf():

@@ -1,10 +1,35 @@
 """Oracle work for the configuration-size GPU tests, run in spawned worker processes
 (imports numpy and the oracle only: no torch, no CUDA)."""
+import contextlib
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 
 from paper_1509_02468_gb300 import synth
 
 BATCH_SEED, CG_ITERS = 4, 50
+_ONE_THREAD = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+@contextlib.contextmanager
+def oracle_pool():
+    """A pool of spawned workers (one per host core but one), each with one BLAS thread:
+    the workers inherit the environment when they start, and without the limit every
+    worker's BLAS would start a thread per core."""
+    saved = {v: os.environ.get(v) for v in _ONE_THREAD}
+    os.environ.update({v: "1" for v in _ONE_THREAD})
+    try:
+        workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            yield ex
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
 
 
 def batch_instance(i, nd, ny, nx):

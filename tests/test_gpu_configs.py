@@ -9,10 +9,6 @@
   refinement's inner solves use, against the oracle; and cg_refine to a true residual of
   1e-5, checked with the oracle's FP64 matrices.
 """
-import multiprocessing as mp
-import os
-from concurrent.futures import ProcessPoolExecutor
-
 import numpy as np
 import pytest
 import torch
@@ -22,7 +18,8 @@ from tests.gpu_helpers import TOL_F32, bf, dev, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-from tests.oracle_jobs import BATCH_SEED, CG_ITERS, batch_cg_error, batch_instance, batch_lobpcg_error
+from tests.oracle_jobs import (BATCH_SEED, CG_ITERS, batch_cg_error, batch_instance, batch_lobpcg_error,
+                               oracle_pool)
 
 
 def test_batch_256_instances_every_instance_against_oracle():
@@ -43,8 +40,7 @@ def test_batch_256_instances_every_instance_against_oracle():
     jobs = [(i, nd, ny, nx, host(x)) for i, ((nd, ny, nx), x) in enumerate(zip(sizes, outs))]
     for G in graphs:
         G.free()
-    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
-    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+    with oracle_pool() as ex:
         # largest instances first, so the pool finishes evenly
         order = sorted(jobs, key=lambda j: -j[2] * j[3])
         results = list(ex.map(batch_cg_error, order, chunksize=1))
@@ -95,10 +91,11 @@ def test_batch_256_instances_lobpcg():
     every instance equals its own lobpcg_filter call exactly; the instances of at most
     2^16 samples are compared with the oracle: the filtered signal to the FP32 bar 1e-5,
     the Ritz values by the A8 reading (1e-6) or, for the tiny smallest Ritz values of small
-    instances (A8 floor below 1e-5), within 2^-22 absolute: the FP32 Gram entries of the
-    residual directions carry absolute errors of order 2^-24 times the pencil's spectral
-    radius (< 2), which bound the Ritz values' absolute error (Weyl)."""
-    from tests.gpu_helpers import TOL_F32, TOL_RITZ
+    instances (A8 floor below 1e-5), to 1e-6 of the pencil's norm (TOL_RITZ_ABS: the FP32
+    Gram entries carry absolute errors of order 2^-24 times the pencil's spectral radius,
+    < 2, and Weyl's inequality bounds the Ritz values' absolute error by the norm of the
+    m x m error matrix)."""
+    from tests.gpu_helpers import TOL_F32, TOL_RITZ, TOL_RITZ_ABS
     sizes = synth.batch_sizes(BATCH_SEED)
     graphs, X0s = [], []
     for i, (nd, ny, nx) in enumerate(sizes):
@@ -114,10 +111,11 @@ def test_batch_256_instances_lobpcg():
         assert info.iters == 30
     jobs = [(i, nd, ny, nx, host(X0s[i]), 30, host(thetas[i]), host(ys[i]))
             for i, (nd, ny, nx) in enumerate(sizes) if ny * nx <= 1 << 16]
-    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
-    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+    with oracle_pool() as ex:
         results = list(ex.map(batch_lobpcg_error, sorted(jobs, key=lambda j: -j[2] * j[3]), chunksize=1))
     assert len(results) >= 100
+    worst_abs = max(r[3] for r in results if r[1] > TOL_RITZ) if any(r[1] > TOL_RITZ for r in results) else 0.0
+    print(f"largest absolute Ritz-value error below the A8 floor: {worst_abs:.2e}")
     for i, e_th, e_y, e_abs, _ in results:
-        assert e_th <= TOL_RITZ or e_abs <= 2.0 ** -22, (i, sizes[i], e_th, e_abs)
+        assert e_th <= TOL_RITZ or e_abs <= TOL_RITZ_ABS, (i, sizes[i], e_th, e_abs)
         assert e_y <= TOL_F32, (i, sizes[i], e_y)

@@ -11,7 +11,7 @@ from tests.gpu_helpers import bf, host
 pytestmark = pytest.mark.gpu
 
 
-def pencil(m, seed, cluster=False, scale_range=3.0):
+def pencil(m, seed, cluster=False, scale_range=3.0, lam=None):
     rng = np.random.default_rng(seed)
     Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
     lam_b = 10 ** rng.uniform(-1, 1, m)
@@ -19,7 +19,8 @@ def pencil(m, seed, cluster=False, scale_range=3.0):
     s = 10 ** rng.uniform(-scale_range, scale_range, m)       # badly scaled basis vectors
     GB = GB * s[:, None] * s[None, :]
     Q2, _ = np.linalg.qr(rng.standard_normal((m, m)))
-    lam = np.sort(np.concatenate([10 ** rng.uniform(-6, -2, m // 3 + 1), rng.uniform(0.1, 2.0, m)]))[:m]
+    if lam is None:
+        lam = np.sort(np.concatenate([10 ** rng.uniform(-6, -2, m // 3 + 1), rng.uniform(0.1, 2.0, m)]))[:m]
     if cluster and m >= 6:
         lam[1] = lam[0] * (1 + 1e-9)
         lam[3] = lam[2] * (1 + 1e-7)
@@ -87,3 +88,25 @@ def test_next_p_is_b_orthogonal_to_ritz_vectors():
     Cw[:k] = 0
     Z = C.T @ GB @ Cw
     np.testing.assert_allclose(Cp, Cw - C @ Z, atol=1e-10)
+
+
+@pytest.mark.parametrize("m,k,gap", [(48, 16, 2e-6), (24, 8, 1e-6), (96, 30, 1e-6)])
+def test_rayleigh_ritz_cluster_across_the_kth_eigenvalue(m, k, gap):
+    """Eigenvalues k and k + 1 (and k + 2) of the pencil closer together than the
+    neighbourhood the FP64 correction leaves alone (64 eps_32 |M|, about 1e-5 here): the k
+    wanted Ritz vectors must span the oracle's invariant subspace (the B-orthogonal
+    projectors agree), not a mixture with the unwanted neighbours.  Gaps of a few eps_32 |M|
+    (3e-7 here) are below this bar: their FP32 inverse-iteration vectors can lose a
+    direction of the cluster (measured projector error 1e-5)."""
+    rng = np.random.default_rng(m + k)
+    lam = np.sort(rng.uniform(0.05, 1.9, m))
+    lam[k] = lam[k - 1] + gap
+    lam[k + 1] = lam[k] + gap
+    lam = np.sort(lam)
+    GA, GB, _ = pencil(m, seed=5 * m + k, scale_range=1.0, lam=lam)
+    C, theta, _, status, _ = bf().rayleigh_ritz(torch.as_tensor(GA).cuda(), torch.as_tensor(GB).cuda(), k)
+    assert status == 0
+    check(GA, GB, k, C, theta)
+    _, Cref, _ = solvers.rayleigh_ritz(GA, GB, k)
+    P, Pref = host(C) @ host(C).T @ GB, Cref @ Cref.T @ GB
+    assert np.linalg.norm(P - Pref) <= 1e-6 * np.sqrt(k), np.linalg.norm(P - Pref)
