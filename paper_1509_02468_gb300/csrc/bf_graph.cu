@@ -558,6 +558,7 @@ __device__ __forceinline__ void pipe_stage(const Geom<float>& g, const ApplyArgs
 
 template <int K>
 __global__ void __launch_bounds__(PipeTile<K>::threads, 1) k_apply_pipe(const Geom<float> g, const ApplyArgs<float> a) {
+  bf_pdl_enter();
   typedef PipeTile<K> TT;
   constexpr int CS = TT::cs, NG = TT::ng, CS4 = CS / 4;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -657,7 +658,7 @@ static int launch_apply_pipe(const bf_graph* g, const ApplyArgs<float>& a, cudaS
   }
   const int64_t ntiles = ((g->nx + TT::tw - 1) / TT::tw) * (int64_t)((g->ny + TT::th - 1) / TT::th);
   const int grid = (int)std::min<int64_t>(ntiles, num_sms());
-  BF_LAUNCH(k_apply_pipe<K><<<grid, TT::threads, TT::smem, s>>>(g->gf, a));
+  BF_LAUNCH_PDL(k_apply_pipe<K>, grid, TT::threads, TT::smem, s, g->gf, a);
   BF_CUDA(cudaGetLastError());
   return BF_OK;
 }

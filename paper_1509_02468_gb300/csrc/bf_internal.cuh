@@ -39,6 +39,40 @@ void bf_count_launches(int n);
     bf_count_launches(1);       \
   } while (0)
 
+// Programmatic dependent launch for the kernels of the block-LOBPCG iteration chain: a
+// kernel launched by BF_LAUNCH_PDL may be scheduled while its predecessor in the stream
+// still runs, once every CTA of the predecessor has called bf_pdl_enter (or exited); it
+// must itself call bf_pdl_enter before touching anything the predecessor writes, since
+// the wait in it returns only when the predecessor grid has completed and its memory
+// operations are visible.  Without the launch attribute the wait returns at once, so a
+// kernel that calls bf_pdl_enter can be launched either way.
+__device__ __forceinline__ void bf_pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t bf_launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                 Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+// a launch error is left for the caller's cudaGetLastError, as with <<< >>>
+#define BF_LAUNCH_PDL(kern, grid, block, smem, stream, ...)                   \
+  do {                                                                        \
+    (void)bf_launch_pdl(kern, grid, block, smem, stream, __VA_ARGS__);        \
+    bf_count_launches(1);                                                     \
+  } while (0)
+
 #define BF_CUDA(call)                                               \
   do {                                                              \
     cudaError_t e_ = (call);                                        \

@@ -251,6 +251,7 @@ __device__ __forceinline__ void two_sum(double& hi, double& lo, double x) { hi +
 
 template <typename T>
 __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
+  bf_pdl_enter();
   if (a.st->status != LOB_RUN) return;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PXC = GramChunk<T>::pxc, BUF = GramChunk<T>::buf;
@@ -450,6 +451,7 @@ __global__ void __launch_bounds__(GRAM_T) k_gram(const GramArgs<T> a) {
 // blocks, combined by shuffles) and write both triangles: G[2][m][m].
 __global__ void k_gram_reduce(const double* __restrict__ partials, int nblocks, int m, double* G,
                               const LobState* st) {
+  bf_pdl_enter();
   if (st->status != LOB_RUN) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int e = gtid >> 5, part = gtid & 31;
@@ -503,6 +505,7 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // pairs, entry by entry in the same order, so the result is the same bit for bit.
 template <int KT>
 __global__ void __launch_bounds__(256, 2) k_update_f32(const UpdArgs<float> a) {
+  bf_pdl_enter();
   if (a.st->status != LOB_RUN) return;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NV = KT / 4, NP = KT / 2;
@@ -675,6 +678,7 @@ __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T*
                                                int k, int64_t n, const T* __restrict__ b,
                                                const T* __restrict__ tinv, T* __restrict__ Wn,
                                                double* __restrict__ partials, const LobState* st) {
+  bf_pdl_enter();
   if (st->status != LOB_RUN) return;
   __shared__ T sred[3][256];                  // the threads' sums (blockDim.x = 256)
   const int lanes = blockDim.x / k;
@@ -716,6 +720,7 @@ __global__ void __launch_bounds__(256) k_resid(const T* __restrict__ X, const T*
 // thread a strided share, then a fixed-order block reduction) into cols[j].
 __global__ void __launch_bounds__(256) k_resid_cols(const double* __restrict__ partials, int nb, int nv,
                                                     double* __restrict__ cols, const LobState* st) {
+  bf_pdl_enter();
   if (st->status != LOB_RUN) return;
   __shared__ double red[256 / 32];
   const int j = blockIdx.x;
@@ -729,6 +734,7 @@ __global__ void __launch_bounds__(256) k_resid_cols(const double* __restrict__ p
 // The relative residual norms, the constraint coefficients e^T B W / e^T B e, the step
 // count and the tolerance test from the column sums of R^2, (b X)^2 and b W.
 __global__ void k_resid_tail(const double* __restrict__ cols, int k, int constrain, LobState* st) {
+  bf_pdl_enter();
   if (st->status != LOB_RUN) return;
   const int t = threadIdx.x;
   double r = 0.0;
@@ -866,7 +872,7 @@ static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
     const int rc_ = bf_smem_attr((const void*)k_gram<T>, 200 * 1024, "cudaFuncSetAttribute(k_gram)");
     if (rc_) return rc_;
   }
-  BF_LAUNCH(k_gram<T><<<grid, GRAM_T, sm, s>>>(ga));
+  BF_LAUNCH_PDL(k_gram<T>, grid, GRAM_T, sm, s, ga);
   BF_CUDA(cudaGetLastError());
   return BF_OK;
 }
@@ -874,7 +880,7 @@ static int run_gram(const GramArgs<T>& ga, int grid, cudaStream_t s) {
 static void run_gram_reduce(const double* partials, int nblocks, int m, double* G,
                             const LobState* st, cudaStream_t s) {
   const int threads = 2 * (m * (m + 1) / 2) * 32;
-  BF_LAUNCH(k_gram_reduce<<<(threads + 255) / 256, 256, 0, s>>>(partials, nblocks, m, G, st));
+  BF_LAUNCH_PDL(k_gram_reduce, (threads + 255) / 256, 256, 0, s, partials, nblocks, m, G, st);
 }
 
 template <typename T, int CW>
@@ -934,10 +940,10 @@ static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T
   int rc = apply_T<T>(g, BF_OP_L, X, k, k, AX, k, s);
   if (rc) return rc;
   const int resgrid = 4 * rgrid;                // many blocks: enough loads in flight
-  BF_LAUNCH(k_resid<T><<<resgrid, 256, 0, s>>>(X, AX, k, g->n, bdiag, net ? nullptr : tinv, Wn, part, st));
+  BF_LAUNCH_PDL(k_resid<T>, resgrid, 256, 0, s, X, AX, k, g->n, bdiag, net ? nullptr : tinv, Wn, part, st);
   double* cols = part + (size_t)resgrid * 3 * k;
-  BF_LAUNCH(k_resid_cols<<<3 * k, 256, 0, s>>>(part, resgrid, 3 * k, cols, st));
-  BF_LAUNCH(k_resid_tail<<<1, 32, 0, s>>>(cols, k, constrain, st));
+  BF_LAUNCH_PDL(k_resid_cols, 3 * k, 256, 0, s, part, resgrid, 3 * k, cols, st);
+  BF_LAUNCH_PDL(k_resid_tail, 1, 32, 0, s, cols, k, constrain, st);
   BF_CUDA(cudaGetLastError());
   if (net) {
     if ((rc = net_T(net, g, Wn, k, s, &st->status))) return rc;

@@ -201,6 +201,7 @@ __device__ void mul_mx(const double* MA, const double* X, double* Y, int m, cons
 // Part 1 (one CTA): scaling, Cholesky with the forward solve, standard form, FP32
 // tridiagonal reduction; hands M, R, T and the reflectors to the next kernels.
 __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
+  bf_pdl_enter();
   if (*a.status != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
   double* MA = reinterpret_cast<double*>(smem);           // [96][RR_LD]: A, Y, M (lower) + R^T (upper)
@@ -497,6 +498,7 @@ __global__ void __launch_bounds__(RR_T) k_rr_reduce(const RRParams a) {
 // counts (32 points per round), its eigenvector by three steps of inverse iteration, then
 // the back-transformation by the reflectors; writes column j of V.
 __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
+  bf_pdl_enter();
   if (*a.status != 0) return;
   RRScratch* S = a.scr;
   const int m = S->m, j = blockIdx.x, lane = threadIdx.x;
@@ -597,6 +599,7 @@ __global__ void __launch_bounds__(32) k_rr_vectors(const RRParams a) {
 // is the same as before it: the transformation is orthogonal), the FP64 correction, the
 // k x k Rayleigh-Ritz and the coefficients C (and Cp).
 __global__ void __launch_bounds__(RR_T) k_rr(const RRParams a) {
+  bf_pdl_enter();
   if (*a.status != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
   double* MA = reinterpret_cast<double*>(smem);           // [96][RR_LD]: A, Y, M (lower) + R^T (upper)
@@ -1081,9 +1084,11 @@ int bf_rr_launch(const RRParams& a, cudaStream_t s) {
   int rc = bf_smem_attr((const void*)k_rr_reduce, (int)sm, "cudaFuncSetAttribute(k_rr_reduce)");
   if (!rc) rc = bf_smem_attr((const void*)k_rr, (int)sm, "cudaFuncSetAttribute(k_rr)");
   if (rc) return rc;
-  BF_LAUNCH(k_rr_reduce<<<1, RR_T, sm, s>>>(a));
+  // k_rr_vectors waits for the one-CTA reduction by a plain launch: launched early its m
+  // CTAs would hold SMs the concurrent work of other streams can use meanwhile
+  BF_LAUNCH_PDL(k_rr_reduce, 1, RR_T, sm, s, a);
   BF_LAUNCH(k_rr_vectors<<<a.m, 32, 0, s>>>(a));
-  BF_LAUNCH(k_rr<<<1, RR_T, sm, s>>>(a));
+  BF_LAUNCH_PDL(k_rr, 1, RR_T, sm, s, a);
   BF_CUDA(cudaGetLastError());
   return BF_OK;
 }
