@@ -138,4 +138,4 @@ def test_batched_lobpcg_equals_single_calls_and_oracle():
         ref = solvers.lobpcg(O, host(X0), kmax)
         scale = np.maximum(np.abs(ref["theta"]), 1e-3 * np.abs(ref["theta"]).max())
         assert np.max(np.abs(host(th) - ref["theta"]) / scale) <= TOL_RITZ_SMALL_F32
-        assert rel_l2(host(y), ref["y"]) <= 1e-4
+        assert rel_l2(host(y), ref["y"]) <= TOL_F32          # measured <= 7.5e-7

@@ -80,8 +80,8 @@ def test_guided_apply_smooth_vector_and_dots():
     x = (1.0 + 0.001 * xx + 0.0005 * yy).reshape(-1, 1)
     y, dots = bf().bf_apply(G, "L", dev(x), dots=True)
     ref = O.L @ host(dev(x))
-    assert rel_l2(host(y), ref) < 1e-4
-    np.testing.assert_allclose(host(dots), [float(host(dev(x)).reshape(-1) @ ref.reshape(-1))], rtol=1e-4)
+    assert rel_l2(host(y), ref) < 1e-5                          # measured 1.6e-7
+    np.testing.assert_allclose(host(dots), [float(host(dev(x)).reshape(-1) @ ref.reshape(-1))], rtol=1e-5)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
@@ -139,7 +139,7 @@ def test_guided_lobpcg(dtype):
     th, rt = host(out["theta"]), np.asarray(ref["theta"])
     err = np.max(np.abs(th - rt) / np.maximum(np.abs(rt), 1e-3 * np.abs(rt).max()))
     assert err < (1e-9 if dtype == torch.float64 else TOL_RITZ_SMALL_F32), err
-    assert rel_l2(host(out["y"]), ref["y"]) < (1e-9 if dtype == torch.float64 else 1e-4)
+    assert rel_l2(host(out["y"]), ref["y"]) < (1e-9 if dtype == torch.float64 else 1e-5)   # FP32: 3.9e-7
 
 
 def test_guided_graph_rejects_and_reports():

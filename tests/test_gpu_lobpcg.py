@@ -61,8 +61,10 @@ def test_lobpcg_small_image_fp32(k, constrain):
     assert e < TOL_RITZ_SMALL_F32, e
     th = host(out["theta_hist"])
     np.testing.assert_allclose(th[-1], host(out["theta"]))
-    assert rel_l2(host(out["y"]), ref["y"]) < 1e-4
-    assert subspace_gap(host(out["X"]), ref["X"], O.d) < 1e-3
+    # the filtered signal at the FP32 bar (measured <= 1.9e-7), the Ritz subspace to 1e-5
+    # (measured <= 1.2e-6)
+    assert rel_l2(host(out["y"]), ref["y"]) < TOL_F32
+    assert subspace_gap(host(out["X"]), ref["X"], O.d) < 1e-5
 
 
 def test_lobpcg_image_512_k16_fp32():
