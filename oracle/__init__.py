@@ -15,6 +15,9 @@ Plain numpy / scipy.sparse in float64, written step by step from the paper
 * ``spectral`` -- dense eigendecompositions (Eq. 8) used as pins: the CG polynomial
                   filter evaluated spectrally, and exact low-pass projections.
 * ``convnet``  -- the small conv net used as a learned preconditioner (forward, backward).
+* ``precond_spd`` -- a learned symmetric positive definite preconditioner
+                  T = D^-1/2 (I + K^T K) D^-1/2 (K a small convolution), its A-norm
+                  training loss and gradient.
 * ``guided``   -- Section 3's guided filter: Algorithm 1 with truncated mean filters and
                   the matrix of Eq. 6 it applies (degree, Laplacian) as explicit CSR.
 

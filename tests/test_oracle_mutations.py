@@ -64,6 +64,13 @@ MUTATIONS = [
     # Adam's bias corrections without the step exponent (equal to the right ones at t = 1)
     ("oracle/convnet.py", "mh = mm / (1 - b1 ** t)", "mh = mm / (1 - b1)"),
     ("oracle/convnet.py", "vh = vv / (1 - b2 ** t)", "vh = vv / (1 - b2)"),
+    # the symmetric positive definite T: transposed kernel, adjoint without the turn, the
+    # outer D^-1/2 dropped, the loss gradient's sign and its second term
+    ("oracle/precond_spd.py", "y[i0:i1, j0:j1] += K[a + h, b + h] *", "y[i0:i1, j0:j1] += K[b + h, a + h] *"),
+    ("oracle/precond_spd.py", "return correlate(y, np.asarray(K)[::-1, ::-1])", "return correlate(y, np.asarray(K))"),
+    ("oracle/precond_spd.py", "return dh * t.reshape(-1)", "return t.reshape(-1)"),
+    ("oracle/precond_spd.py", "hv = (dh * (-2.0 * Ae / c))", "hv = (dh * (2.0 * Ae / c))"),
+    ("oracle/precond_spd.py", "grad[a + hk, b + hk] = s1 + s2", "grad[a + hk, b + hk] = s1"),
 ]
 
 
@@ -79,7 +86,8 @@ def test_pins_catch_planted_mistake(tmp_path, path, old, new):
     assert old in src, f"mutation anchor not found in {path}: {old!r}"
     target.write_text(src.replace(old, new, 1))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_graph.py", "tests/test_oracle_solvers.py",
-                        "tests/test_oracle_convnet.py", "tests/test_oracle_guided.py"],
+                        "tests/test_oracle_precond_spd.py", "tests/test_oracle_graph.py",
+                        "tests/test_oracle_solvers.py", "tests/test_oracle_convnet.py",
+                        "tests/test_oracle_guided.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake not caught: {path}: {new!r}\n{r.stdout[-2000:]}"
