@@ -18,6 +18,8 @@ on a 2048 x 2048 image, X and Y far larger than L2),
 `roofline_dominant` (the Rayleigh-Ritz solve, the largest share of the step's GPU time),
 `batched` (CG on 256 uneven instances, one CUDA graph and one persistent launch, against
 plain calls; block LOBPCG on the same instances over a pool of streams against plain calls),
+`precond_spd` (the shifted system of a held-out 1024 x 1024 image to a true residual of 1e-5
+with T = Jacobi and with the learned SPD preconditioner trained by the library's kernels),
 `cpu_baseline` (the FP64 CPU oracle, one thread, on
 one full step of the same workload), `e2e` (the same pipeline from pinned host memory to
 host results), `clocks` (nvidia-smi sampled during the timed region) and `gpu_launches`
@@ -367,6 +369,13 @@ def run_gpu(args):
     reguided = None if args.no_batch else _run_reguided(bf, torch, stream, flush, peak)
     # ---- the guided filter's graph (Section 3)
     guided = None if args.no_batch else _run_guided(bf, torch, stream, flush, peak, alu_peak)
+    # ---- the learned SPD preconditioner against Jacobi on the shifted system
+    spd = None
+    if not args.no_batch:
+        try:
+            spd = _run_spd(bf, torch)
+        except Exception as exc:                # reported in the line, not fatal to it
+            spd = {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
     # ---- CPU baseline: the oracle on one full step (rank 0, N = 1 only)
     cpu = None
@@ -397,7 +406,7 @@ def run_gpu(args):
                 "roofline": roofline, "apply_modes_2048": apply_modes, "cg_2048": cg_2048,
                 "roofline_apply16_512": roofline_512, "roofline_2048": roofline_2048,
                 "roofline_dominant": roofline_rr, "cpu_baseline": cpu, "err": err,
-                "batched": batched, "reguided": reguided, "guided": guided,
+                "batched": batched, "reguided": reguided, "guided": guided, "precond_spd": spd,
                 "e2e": {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "clocks": clk.summary(), "gpu_launches": launches}
@@ -703,6 +712,41 @@ def _run_guided(bf, torch, stream, flush, peak, alu_peak, r=2, eps=1e-2, k=16, r
             out["cpu_baseline"] = {"value": npx / t / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                                    "sample": "Algorithm 1 once (one column) on the 512x512 image"}
         G.free()
+    return out
+
+
+def _run_spd(bf, torch, side=1024, seed=5, tol=1e-5, reps=2):
+    """The shifted system (L + sigma I) x = sigma x0 of the held-out 1024 x 1024 image solved
+    to a true relative residual tol (cg_refine: FP64 residuals, FP32 inner CG to 1e-3) with
+    T = Jacobi and with the learned SPD preconditioner T = D^-1/2 (I + K^T K) D^-1/2, K a
+    7 x 7 kernel trained here by the library's kernels (36 pairs of six 128 x 128 images,
+    200 full-batch Adam steps on the A-norm loss)."""
+    from paper_1509_02468_gb300 import synth, train
+    t0 = time.perf_counter()
+    pairs = train.make_random_pairs(range(1000, 1006), 128, 6)
+    T = bf.Spd(3, train.spd_initial_kernel(3))
+    hist = train.train_spd(T, pairs, epochs=200, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    _, noisy = synth.polygon_image(side, side, seed)
+    g32 = torch.as_tensor(noisy, device="cuda")
+    G32 = bf.bf_weights(g32, train.RADIUS, train.SIGMA_S, train.SIGMA_R)
+    G64 = bf.bf_weights(g32.double(), train.RADIUS, train.SIGMA_S, train.SIGMA_R)
+    out = {"workload": f"(L + sigma I) x = sigma x0, {side}x{side} held-out image (seed {seed}), sigma "
+                       f"{train.SIGMA}, to a true relative residual {tol}; FP64 refinement, FP32 inner CG",
+           "train_seconds": t_train, "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]}
+    for name, kw in (("jacobi", dict(precond="jacobi")), ("spd", dict(precond="spd", spd=T))):
+        train.refined_cg(G32, G64, g32.reshape(-1), train.SIGMA, tol, **kw)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(reps):
+            x, rel, inner, outer = train.refined_cg(G32, G64, g32.reshape(-1), train.SIGMA, tol, **kw)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t1) / reps
+        out[name] = {"inner_iters": inner, "outer": outer, "rel_residual": rel, "ms": 1e3 * dt,
+                     "mpix_s": noisy.size / dt / 1e6}
+    out["speedup"] = out["jacobi"]["ms"] / out["spd"]["ms"]
+    T.free()
     return out
 
 

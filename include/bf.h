@@ -63,6 +63,7 @@ extern "C" {
 #define BF_PRECOND_JACOBI   0 /* T = D^-1 (Algorithm 2's preconditioner)                  */
 #define BF_PRECOND_IDENTITY 1 /* T = I                                                    */
 #define BF_PRECOND_NET      2 /* T = the learned conv net of a bf_net (FP32 graphs)        */
+#define BF_PRECOND_SPD      3 /* T = D^-1/2 (I + K^T K) D^-1/2 of a bf_spd (FP32 graphs)    */
 
 #define BF_BETA_FLEXIBLE  0   /* beta = s^T (r - r_old) / (s_old^T r_old)                 */
 #define BF_BETA_PRINTED   1   /* beta = s^T (r - r_old) / (s_old^T s_old), as printed     */
@@ -107,6 +108,7 @@ typedef struct bf_guided_params {
 
 typedef struct bf_graph bf_graph;   /* opaque */
 typedef struct bf_net bf_net;       /* opaque: the learned preconditioner (see below) */
+typedef struct bf_spd bf_spd;       /* opaque: the learned SPD preconditioner (see below) */
 
 typedef struct bf_info {
   int32_t iters;         /* iterations completed                                            */
@@ -124,6 +126,7 @@ typedef struct bf_cg_opts {
   double  tol;           /* > 0: stop once ||r|| <= tol * ||b|| (||r_0|| if b = 0)          */
   double* hist;          /* optional device array [2 * kmax]: alpha_j, beta_j per iteration */
   const bf_net* net;     /* BF_PRECOND_NET: the preconditioner (else ignored)               */
+  const bf_spd* spd;     /* BF_PRECOND_SPD: the preconditioner (else ignored)               */
 } bf_cg_opts;
 
 typedef struct bf_lobpcg_opts {
@@ -134,6 +137,7 @@ typedef struct bf_lobpcg_opts {
   double  tol;           /* > 0: stop once max_j ||L x_j - theta_j B x_j|| / ||B x_j|| <= tol */
   double* theta_hist;    /* optional device array [(kmax + 1) * k]: Ritz values per step    */
   const bf_net* net;     /* BF_PRECOND_NET: the preconditioner (else ignored)               */
+  const bf_spd* spd;     /* BF_PRECOND_SPD: the preconditioner (else ignored)               */
 } bf_lobpcg_opts;
 
 /* ---- graph ------------------------------------------------------------------------ */
@@ -228,7 +232,8 @@ int bf_reguided_filter(bf_graph* g, const void* x0, int iters, void* x_out, void
  * scalar state is initialised by a kernel, not copied from the host), so it can be
  * captured in a CUDA graph once an uncaptured call on the same graph has sized the
  * workspace (the first call, or one with a larger problem, may allocate it).
- * BF_PRECOND_NET takes T from opts->net. */
+ * BF_PRECOND_NET takes T from opts->net, BF_PRECOND_SPD from opts->spd (both run s = T r
+ * by kernels of their own after each update of x and r). */
 int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_cg_opts* opts,
               void* x_out, bf_info* info, void* stream);
 
@@ -323,6 +328,46 @@ int bf_net_grad(const bf_net* net, float* grad_host, double* loss_host, void* st
  * the accumulated gradient (scale = 1 / pairs for the mean); then resets the
  * accumulators. */
 int bf_net_adam(bf_net* net, float lr, float scale, void* stream);
+
+/* ---- the learned symmetric positive definite preconditioner ---------------------------
+ * T of Algorithms 2 and 3 (left open by the paper, Section 5; Section 8 names better
+ * preconditioners as future work), linear, symmetric and positive definite by
+ * construction, so that CG keeps Section 5's A-norm optimality and LOBPCG's Ritz vectors
+ * stay sign-free:
+ *   T r = D^-1/2 (u + K^T K u),   u = D^-1/2 r,
+ * K a (2h + 1) x (2h + 1) cross-correlation of the image-shaped u on the graph's grid
+ * (row-major taps K[dy][dx], zero outside the image), K^T its adjoint (K turned by 180
+ * degrees).  K = 0 is Jacobi.  Training pairs (r, z) solve A z = r, A = L + sigma I; the
+ * loss of a pair is the A-norm error of T r relative to z,
+ *   (z - T r)^T A (z - T r) / (z^T A z).
+ * A bf_spd owns K (FP32), its Adam state, gradient accumulators and a grow-only workspace
+ * (cudaMalloc on first use and when a larger image comes; the device is synchronised
+ * before a regrowth); calls that use one bf_spd must be ordered on one stream.  FP32
+ * bilateral graphs only; cg_filter_noalloc and the batched drivers do not take it. */
+/* New preconditioner of half-width h (1..4, K (2h+1)^2 taps, copied from K_host, NULL:
+ * zero); *out must be freed with bf_spd_free. */
+int bf_spd_create(int half, const float* K_host, bf_spd** out);
+int bf_spd_free(bf_spd* T);
+/* Number of taps (2h+1)^2 (0 for NULL). */
+int bf_spd_size(const bf_spd* T);
+/* Copy K to the host (bf_spd_size floats). */
+int bf_spd_weights(const bf_spd* T, float* K_host);
+/* Z[:, j] = T R[:, j] for k image-shaped columns on g's grid (pixel-major, ld >= k);
+ * Z may equal R. */
+int bf_spd_apply(const bf_spd* T, const bf_graph* g, const float* R, int64_t ldr, int k,
+                 float* Z, int64_t ldz, void* stream);
+/* Reset the accumulated gradient and loss. */
+int bf_spd_zero_grad(bf_spd* T, void* stream);
+/* Add the loss and its gradient with respect to K of the pair (r, z) (n floats each on
+ * g's grid, A z = r with A = L + shift I, shift >= 0). */
+int bf_spd_accumulate(bf_spd* T, const bf_graph* g, double shift, const float* r,
+                      const float* z, void* stream);
+/* Read the accumulated gradient (bf_spd_size doubles) and loss to the host (either may
+ * be NULL); synchronises the stream. */
+int bf_spd_grad(const bf_spd* T, double* grad_host, double* loss_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on scale times
+ * the accumulated gradient; then resets the accumulators. */
+int bf_spd_adam(bf_spd* T, float lr, float scale, void* stream);
 
 /* ---- batched CG -----------------------------------------------------------------------
  * Algorithm 2 on many instances (images and signals of uneven sizes) at once: every launch

@@ -20,7 +20,7 @@ F32, F64 = 0, 1
 WINDOWS = {"square": 0, "cross": 1}
 WEIGHT_MODES = {"onthefly": 0, "stored_f32": 1, "stored_bf16": 2}
 OPS = {"W": 0, "L": 1, "DINV_W": 2, "D": 3, "NSYM": 4, "NDIAGL": 5}
-PRECONDS = {"jacobi": 0, "identity": 1, "net": 2}
+PRECONDS = {"jacobi": 0, "identity": 1, "net": 2, "spd": 3}
 BETAS = {"flexible": 0, "printed": 1}
 PENCILS = {"D": 0, "I": 1}
 GRAMS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
@@ -57,14 +57,14 @@ class bf_info(ctypes.Structure):
 class bf_cg_opts(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("shift", ctypes.c_double), ("tol", ctypes.c_double),
-                ("hist", ctypes.c_void_p), ("net", ctypes.c_void_p)]
+                ("hist", ctypes.c_void_p), ("net", ctypes.c_void_p), ("spd", ctypes.c_void_p)]
 
 
 class bf_lobpcg_opts(ctypes.Structure):
     _fields_ = [("pencil", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("constrain_e", ctypes.c_int32), ("gram", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("theta_hist", ctypes.c_void_p),
-                ("net", ctypes.c_void_p)]
+                ("net", ctypes.c_void_p), ("spd", ctypes.c_void_p)]
 
 
 def _load():
@@ -102,6 +102,15 @@ def _load():
         "bf_net_accumulate": [vp, vp, vp, vp, vp],
         "bf_net_grad": [vp, vp, vp, vp],
         "bf_net_adam": [vp, ctypes.c_float, ctypes.c_float, vp],
+        "bf_spd_create": [i32, vp, ctypes.POINTER(vp)],
+        "bf_spd_free": [vp],
+        "bf_spd_size": [vp],
+        "bf_spd_weights": [vp, vp],
+        "bf_spd_apply": [vp, vp, vp, i64, i32, vp, i64, vp],
+        "bf_spd_zero_grad": [vp, vp],
+        "bf_spd_accumulate": [vp, vp, ctypes.c_double, vp, vp, vp],
+        "bf_spd_grad": [vp, vp, vp, vp],
+        "bf_spd_adam": [vp, ctypes.c_float, ctypes.c_float, vp],
         "bf_gram_tc_test": [vp, vp, vp, vp, vp, vp, vp, i32, i32, i64, i32, vp, vp],
         "bf_wait_test": [i32, i32, vp],
         "bf_batch_create": [vp, i32, ctypes.POINTER(vp)],
@@ -297,14 +306,16 @@ def reguided_filter(g: Graph, x0: torch.Tensor, iters: int, out=None, stream=Non
 
 def cg_filter(g: Graph, x0: torch.Tensor, kmax: int, precond: str = "jacobi",
               beta: str = "flexible", shift: float = 0.0, tol: float = 0.0,
-              hist: bool = False, out=None, sync: bool = True, stream=None, net: "Net | None" = None):
+              hist: bool = False, out=None, sync: bool = True, stream=None, net: "Net | None" = None,
+              spd: "Spd | None" = None):
     """Algorithm 2.  Returns (x, info, hist) -- info None unless sync, hist None unless asked.
-    precond="net" uses the learned preconditioner `net`."""
+    precond="net" uses the learned preconditioner `net`, precond="spd" the learned SPD one."""
     out = torch.empty_like(x0) if out is None else out
     h = torch.full((2 * max(kmax, 1),), float("nan"), dtype=torch.float64, device=x0.device) if hist else None
     o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS[beta], shift=shift, tol=tol,
                    hist=h.data_ptr() if h is not None else None,
-                   net=net.handle if net is not None else None)
+                   net=net.handle if net is not None else None,
+                   spd=spd.handle if spd is not None else None)
     info = bf_info() if sync else None
     _check(_lib.cg_filter(g.handle, _ptr(x0), kmax, ctypes.byref(o), _ptr(out),
                           ctypes.byref(info) if info is not None else None, _stream(stream)))
@@ -334,14 +345,14 @@ def shifted_residual(g: Graph, x0: torch.Tensor, x: torch.Tensor, shift: float, 
 
 def cg_refine(g64: Graph, g32: Graph, x0: torch.Tensor, shift: float, tol: float, precond: str = "jacobi",
               inner_tol: float = 1e-3, inner_kmax: int = 3000, outer_max: int = 30, net: "Net | None" = None,
-              out=None, stream=None):
+              out=None, stream=None, spd: "Spd | None" = None):
     """(L + shift I) x = shift x0 to a true relative residual tol (cg_refine: FP64 residuals
     on g64, FP32 inner CG on g32).  x0: float64 CUDA tensor.  Returns (x, info)."""
     if x0.dtype != torch.float64:
         raise ValueError("x0 must be float64")
     out = torch.empty_like(x0) if out is None else out
     o = bf_cg_opts(precond=PRECONDS[precond], beta=BETAS["flexible"], shift=shift, tol=inner_tol, hist=None,
-                   net=net.handle if net is not None else None)
+                   net=net.handle if net is not None else None, spd=spd.handle if spd is not None else None)
     info = bf_info()
     _check(_lib.cg_refine(g64.handle, g32.handle, _ptr(x0), shift, tol, ctypes.byref(o), inner_kmax, outer_max,
                           _ptr(out), ctypes.byref(info), _stream(stream)))
@@ -351,7 +362,8 @@ def cg_refine(g64: Graph, g32: Graph, x0: torch.Tensor, shift: float, tol: float
 def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
                   precond: str = "jacobi", constrain: bool = False, tol: float = 0.0,
                   want_X: bool = True, want_y: bool = True, theta_hist: bool = False,
-                  sync: bool = True, stream=None, net: "Net | None" = None, gram: str = "fp32"):
+                  sync: bool = True, stream=None, net: "Net | None" = None, gram: str = "fp32",
+                  spd: "Spd | None" = None):
     """Algorithm 3 on a block X0 of shape (n, k).  gram: "fp32" | "bf16" | "bf16x3" (tensor cores).  Returns a dict with X, theta, resid, y,
     theta_hist and info (entries None when not requested)."""
     Xb, k = _as_block(X0)
@@ -364,7 +376,8 @@ def lobpcg_filter(g: Graph, X0: torch.Tensor, kmax: int, pencil: str = "D",
     o = bf_lobpcg_opts(pencil=PENCILS[pencil], precond=PRECONDS[precond],
                        constrain_e=int(constrain), gram=GRAMS[gram], tol=tol,
                        theta_hist=th.data_ptr() if th is not None else None,
-                       net=net.handle if net is not None else None)
+                       net=net.handle if net is not None else None,
+                       spd=spd.handle if spd is not None else None)
     info = bf_info() if sync else None
     _check(_lib.lobpcg_filter(g.handle, _ptr(Xb), Xb.stride(0), k, kmax, ctypes.byref(o),
                               _ptr(X), _ptr(theta), _ptr(resid), _ptr(y),
@@ -454,6 +467,71 @@ class Net:
 
 def nweights() -> int:
     return int(_lib.bf_net_nweights())
+
+
+class Spd:
+    """The learned symmetric positive definite preconditioner (bf_spd):
+    T r = D^-1/2 (u + K^T K u), u = D^-1/2 r, K a (2h+1) x (2h+1) correlation kernel
+    (float32, row-major taps; None: zero, i.e. Jacobi)."""
+
+    def __init__(self, half: int, K=None):
+        import numpy as np
+        h = ctypes.c_void_p()
+        if K is not None:
+            Kc = np.ascontiguousarray(np.asarray(K, np.float32).reshape(-1))
+            if Kc.size != (2 * half + 1) ** 2:
+                raise ValueError(f"K must have {(2 * half + 1) ** 2} taps")
+            _check(_lib.bf_spd_create(half, Kc.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        else:
+            _check(_lib.bf_spd_create(half, None, ctypes.byref(h)))
+        self.half = half
+        self.handle = h.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            _lib.bf_spd_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def kernel(self):
+        """K as a (2h+1, 2h+1) float32 numpy array."""
+        import numpy as np
+        ks = 2 * self.half + 1
+        K = np.empty(ks * ks, np.float32)
+        _check(_lib.bf_spd_weights(self.handle, K.ctypes.data_as(ctypes.c_void_p)))
+        return K.reshape(ks, ks)
+
+    def apply(self, g: Graph, R: torch.Tensor, out=None, stream=None):
+        """Z = T R column by column; R is (n,) or (n, k)."""
+        Rb, k = _as_block(R)
+        Z = torch.empty_like(Rb) if out is None else out
+        _check(_lib.bf_spd_apply(self.handle, g.handle, _ptr(Rb), Rb.stride(0), k, _ptr(Z), Z.stride(0),
+                                 _stream(stream)))
+        return Z.view_as(R) if R.dim() == 1 else Z
+
+    def zero_grad(self, stream=None):
+        _check(_lib.bf_spd_zero_grad(self.handle, _stream(stream)))
+
+    def accumulate(self, g: Graph, shift: float, r: torch.Tensor, z: torch.Tensor, stream=None):
+        _check(_lib.bf_spd_accumulate(self.handle, g.handle, float(shift), _ptr(r), _ptr(z), _stream(stream)))
+
+    def grad(self, stream=None):
+        """(gradient as a (2h+1, 2h+1) float64 array, loss) accumulated since the last reset."""
+        import numpy as np
+        ks = 2 * self.half + 1
+        gr = np.empty(ks * ks, np.float64)
+        loss = ctypes.c_double()
+        _check(_lib.bf_spd_grad(self.handle, gr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss),
+                                _stream(stream)))
+        return gr.reshape(ks, ks), loss.value
+
+    def adam(self, lr: float, scale: float = 1.0, stream=None):
+        _check(_lib.bf_spd_adam(self.handle, ctypes.c_float(lr), ctypes.c_float(scale), _stream(stream)))
 
 
 class Batch:

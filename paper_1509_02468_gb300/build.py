@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libbf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["bf_graph.cu", "bf_cg.cu", "bf_lobpcg.cu", "bf_rr.cu", "bf_net.cu", "bf_batch.cu", "bf_gram_tc.cu",
-           "bf_guided.cu"]
+           "bf_guided.cu", "bf_spd.cu"]
 
 
 def nvcc() -> str:

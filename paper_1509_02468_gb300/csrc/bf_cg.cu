@@ -28,6 +28,8 @@ int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k,
                  int64_t ldy, double* dots, cudaStream_t s);
 int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
                      int64_t ldz, cudaStream_t s, const int* stop);
+int bf_spd_apply_f32(const bf_spd* T, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
+                     int64_t ldz, cudaStream_t s);
 
 namespace {
 
@@ -51,6 +53,18 @@ inline int net_precond(const bf_net* net, const bf_graph* g, const float* r, flo
 }
 inline int net_precond(const bf_net*, const bf_graph*, const double*, double*, cudaStream_t, const int*) {
   return bf_fail(BF_EINVAL, "cg_filter: the net preconditioner needs an FP32 graph");
+}
+// s = T r with the learned SPD preconditioner, or the net (the two T that are applied by
+// kernels of their own after the update of x and r)
+inline int own_precond(const bf_cg_opts& o, const bf_graph* g, const float* r, float* s, cudaStream_t st,
+                       const int* stop) {
+  if (o.precond == BF_PRECOND_SPD) return bf_spd_apply_f32(o.spd, g, r, 1, 1, s, 1, st);
+  return net_precond(o.net, g, r, s, st, stop);
+}
+inline int own_precond(const bf_cg_opts& o, const bf_graph* g, const double* r, double* s, cudaStream_t st,
+                       const int* stop) {
+  if (o.precond == BF_PRECOND_SPD) return bf_fail(BF_EINVAL, "cg_filter: the SPD preconditioner needs an FP32 graph");
+  return net_precond(o.net, g, r, s, st, stop);
 }
 
 struct CgState {
@@ -704,7 +718,7 @@ static void cg_launch_window(bool init, dim3 tg, size_t sm, cudaStream_t s, cons
 template <typename T>
 int cg_generic_loop(const bf_graph* g, CgArgs<T>& a, int kmax, const bf_cg_opts& o, cudaStream_t s,
                     T* const* pbuf, dim3 tg, size_t sm, unsigned nb_elem) {
-  const bool net = (o.precond == BF_PRECOND_NET);
+  const bool net = (o.precond == BF_PRECOND_NET || o.precond == BF_PRECOND_SPD);
   const bool guided = (g->kind == BF_KIND_GUIDED);
   int rc = BF_OK;
   if (guided) {
@@ -715,7 +729,7 @@ int cg_generic_loop(const bf_graph* g, CgArgs<T>& a, int kmax, const bf_cg_opts&
   }
   BF_CUDA(cudaGetLastError());
   if (net) {
-    if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
+    if ((rc = own_precond(o, g, a.r, a.s, s, &a.st->status))) return rc;
     BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 1));
   }
   for (int it = 0; it < kmax; ++it) {
@@ -731,7 +745,7 @@ int cg_generic_loop(const bf_graph* g, CgArgs<T>& a, int kmax, const bf_cg_opts&
     }
     if (net) {
       BF_LAUNCH(k_cg_xr<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
-      if ((rc = net_precond(o.net, g, a.r, a.s, s, &a.st->status))) return rc;
+      if ((rc = own_precond(o, g, a.r, a.s, s, &a.st->status))) return rc;
       BF_LAUNCH(k_cg_sdots<T><<<nb_elem, BF_THREADS, 0, s>>>(a, 0));
     } else {
       BF_LAUNCH(k_cg_update<T><<<nb_elem, BF_THREADS, 0, s>>>(a));
@@ -838,7 +852,7 @@ int cg_exec(const bf_graph* g, const T* x0, int kmax, const bf_cg_opts& o, T* x_
   const bool one_d = (g->ny == 1 && g->ry == 0);
   const size_t hp = (size_t)((one_d ? BF_TW1 : BF_TW2) + 2 * g->rx) * ((one_d ? 1 : BF_TH2) + 2 * g->ry);
   const size_t sm = hp * 2 * sizeof(T);
-  const bool net = (o.precond == BF_PRECOND_NET);
+  const bool net = (o.precond == BF_PRECOND_NET || o.precond == BF_PRECOND_SPD);
   const bool guided = (g->kind == BF_KIND_GUIDED);
   int rc = BF_OK;
   if (!guided && !net && sizeof(T) == 4 && fast_shape(g) == FAST_R3_2D && ((uintptr_t)x_out & 15) == 0) {
@@ -903,10 +917,13 @@ extern "C" int cg_filter(const bf_graph* g, const void* x0, int kmax, const bf_c
   bf_cg_opts o;
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET)
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET &&
+      o.precond != BF_PRECOND_SPD)
     return bf_fail(BF_EINVAL, "cg_filter: bad precond");
   if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4 || g->kind != BF_KIND_BILATERAL))
     return bf_fail(BF_EINVAL, "cg_filter: BF_PRECOND_NET needs a net and an FP32 bilateral graph");
+  if (o.precond == BF_PRECOND_SPD && (!o.spd || g->esize != 4 || g->kind != BF_KIND_BILATERAL))
+    return bf_fail(BF_EINVAL, "cg_filter: BF_PRECOND_SPD needs a bf_spd and an FP32 bilateral graph");
   if (o.beta != BF_BETA_FLEXIBLE && o.beta != BF_BETA_PRINTED)
     return bf_fail(BF_EINVAL, "cg_filter: bad beta");
   if (!(o.shift >= 0.0) || !(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "cg_filter: shift and tol must be >= 0");

@@ -23,6 +23,8 @@ int bf_apply_f32(const bf_graph* g, int op, const float* X, int64_t ldx, int k, 
                  int64_t ldy, double* dots, cudaStream_t s);
 int bf_net_apply_f32(const bf_net* net, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
                      int64_t ldz, cudaStream_t s, const int* stop);
+int bf_spd_apply_f32(const bf_spd* T, const bf_graph* g, const float* R, int64_t ldr, int k, float* Z,
+                     int64_t ldz, cudaStream_t s);
 int bf_gram_tc(const float* const* S, const float* const* AS, const float* b, int nblk, int k, int64_t n,
                int mode, double* partials, int grid, double* G, const int* status, int* err, cudaStream_t s);
 int bf_apply_f64(const bf_graph* g, int op, const double* X, int64_t ldx, int k, double* Y,
@@ -929,24 +931,35 @@ inline int net_T(const bf_net* net, const bf_graph* g, float* W, int k, cudaStre
 inline int net_T(const bf_net*, const bf_graph*, double*, int, cudaStream_t, const int*) {
   return bf_fail(BF_EINVAL, "lobpcg_filter: the net preconditioner needs an FP32 graph");
 }
+inline int spd_T(const bf_spd* T, const bf_graph* g, float* W, int k, cudaStream_t s) {
+  return bf_spd_apply_f32(T, g, W, k, k, W, k, s);
+}
+inline int spd_T(const bf_spd*, const bf_graph*, double*, int, cudaStream_t) {
+  return bf_fail(BF_EINVAL, "lobpcg_filter: the SPD preconditioner needs an FP32 graph");
+}
 
-// A X = L X, then the residual kernel: W = T (A X - B X theta) and its norms.  With the
-// learned preconditioner the kernel writes R = A X - B X theta, the net maps it to
-// W = T(R) in place and the constraint coefficients e^T B W / e^T B e are recomputed.
+// A X = L X, then the residual kernel: W = T (A X - B X theta) and its norms.  With a
+// learned preconditioner (the net or the SPD T) the kernel writes R = A X - B X theta, T
+// maps it to W = T(R) in place and the constraint coefficients e^T B W / e^T B e are
+// recomputed.
 template <typename T>
 static int run_resid(const bf_graph* g, const T* X, T* AX, int k, T* Wn, const T* bdiag,
                      const T* tinv, int constrain, double* part, LobState* st, int rgrid,
-                     cudaStream_t s, const bf_net* net = nullptr) {
+                     cudaStream_t s, const bf_net* net = nullptr, const bf_spd* spd = nullptr) {
   int rc = apply_T<T>(g, BF_OP_L, X, k, k, AX, k, s);
   if (rc) return rc;
   const int resgrid = 4 * rgrid;                // many blocks: enough loads in flight
-  BF_LAUNCH_PDL(k_resid<T>, resgrid, 256, 0, s, X, AX, k, g->n, bdiag, net ? nullptr : tinv, Wn, part, st);
+  BF_LAUNCH_PDL(k_resid<T>, resgrid, 256, 0, s, X, AX, k, g->n, bdiag, (net || spd) ? nullptr : tinv, Wn, part, st);
   double* cols = part + (size_t)resgrid * 3 * k;
   BF_LAUNCH_PDL(k_resid_cols, 3 * k, 256, 0, s, part, resgrid, 3 * k, cols, st);
   BF_LAUNCH_PDL(k_resid_tail, 1, 32, 0, s, cols, k, constrain, st);
   BF_CUDA(cudaGetLastError());
-  if (net) {
-    if ((rc = net_T(net, g, Wn, k, s, &st->status))) return rc;
+  if (net || spd) {
+    if (net) {
+      if ((rc = net_T(net, g, Wn, k, s, &st->status))) return rc;
+    } else if ((rc = spd_T(spd, g, Wn, k, s))) {
+      return rc;
+    }
     if (constrain) BF_LAUNCH(k_bsums<T><<<rgrid, 256, 0, s>>>(Wn, k, g->n, bdiag, part, st));
     BF_CUDA(cudaGetLastError());
   }
@@ -1071,7 +1084,8 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
   rc = run_update<T>(ua, ugrid, s);
   if (rc) return rc;
   const bf_net* net = (o.precond == BF_PRECOND_NET) ? o.net : nullptr;
-  rc = run_resid<T>(g, B.X[0], B.AX[0], k, B.W[0], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s, net);
+  const bf_spd* spd = (o.precond == BF_PRECOND_SPD) ? o.spd : nullptr;
+  rc = run_resid<T>(g, B.X[0], B.AX[0], k, B.W[0], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s, net, spd);
   if (rc) return rc;
   // the start step counted as one residual evaluation: iterations count from 0 after it
   BF_LAUNCH(k_state_iter0<<<1, 32, 0, s>>>(B.st));
@@ -1109,7 +1123,8 @@ int lob_run(const bf_graph* g, const T* X0, int64_t ldx0, int k, int kmax,
     if (rc) return rc;
     rc = apply_T<T>(g, BF_OP_L, B.P[nj], k, k, B.AP[nj], k, s);
     if (rc) return rc;
-    rc = run_resid<T>(g, B.X[nj], B.AX[nj], k, B.W[nj], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s, net);
+    rc = run_resid<T>(g, B.X[nj], B.AX[nj], k, B.W[nj], bdiag, tinv, o.constrain_e, B.part, B.st, rgrid, s, net,
+                      spd);
     if (rc) return rc;
   }
   // ---- outputs
@@ -1152,10 +1167,13 @@ extern "C" int lobpcg_filter(const bf_graph* g, const void* X0, int64_t ldx0, in
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   if (o.pencil != BF_PENCIL_D && o.pencil != BF_PENCIL_I) return bf_fail(BF_EINVAL, "lobpcg_filter: bad pencil");
-  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET)
+  if (o.precond != BF_PRECOND_JACOBI && o.precond != BF_PRECOND_IDENTITY && o.precond != BF_PRECOND_NET &&
+      o.precond != BF_PRECOND_SPD)
     return bf_fail(BF_EINVAL, "lobpcg_filter: bad precond");
   if (o.precond == BF_PRECOND_NET && (!o.net || g->esize != 4 || g->kind != BF_KIND_BILATERAL))
     return bf_fail(BF_EINVAL, "lobpcg_filter: BF_PRECOND_NET needs a net and an FP32 bilateral graph");
+  if (o.precond == BF_PRECOND_SPD && (!o.spd || g->esize != 4 || g->kind != BF_KIND_BILATERAL))
+    return bf_fail(BF_EINVAL, "lobpcg_filter: BF_PRECOND_SPD needs a bf_spd and an FP32 bilateral graph");
   if (!(o.tol >= 0.0)) return bf_fail(BF_EINVAL, "lobpcg_filter: tol must be >= 0");
   if (o.gram != BF_GRAM_FP32 && o.gram != BF_GRAM_BF16 && o.gram != BF_GRAM_BF16X3 && o.gram != BF_GRAM_BF16X6)
     return bf_fail(BF_EINVAL, "lobpcg_filter: bad gram mode");

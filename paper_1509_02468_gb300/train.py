@@ -8,6 +8,10 @@ with Adam, by the library's own forward and backward kernels, starting from weig
 which T is exactly Jacobi (D^-1).  Evaluation: iterations and time of flexible CG to a
 relative residual of 1e-5 with the trained net against Jacobi, on held-out images.
 
+The symmetric positive definite preconditioner (bf_spd, T = D^-1/2 (I + K^T K) D^-1/2) is
+trained the same way by its own kernels, on pairs with white-noise r (make_random_pairs)
+and the A-norm loss (z - T r)^T A (z - T r) / z^T A z (train_spd).
+
     python -m paper_1509_02468_gb300.train --images 200 --side 256 --out weights.npz
 """
 from __future__ import annotations
@@ -84,6 +88,51 @@ def train(net, pairs, epochs: int, batch: int, lr: float, seed: int = 0, log=Non
     return hist
 
 
+def make_random_pairs(seeds, side: int, per_image: int, sigma: float = SIGMA, tol: float = 1e-8,
+                      kmax_solve: int = 20000, seed: int = 0, device="cuda"):
+    """[(graph, r, z)]: per image, per_image residuals r ~ N(0, 1) on its grid (every
+    frequency present) and z solving (L + sigma I) z = r to tol by FP64 CG on the GPU."""
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    out = []
+    for s in seeds:
+        _, noisy = synth.polygon_image(side, side, s)
+        g32 = torch.as_tensor(noisy, device=device)
+        G = bf.bf_weights(g32, RADIUS, SIGMA_S, SIGMA_R)
+        G64 = bf.bf_weights(g32.double(), RADIUS, SIGMA_S, SIGMA_R)
+        for _ in range(per_image):
+            r = torch.randn(noisy.size, device=device, generator=gen)
+            z, info, _ = bf.cg_filter(G64, (r / sigma).double(), kmax_solve, shift=sigma, tol=tol)
+            out.append((G, r.contiguous(), z.float().contiguous()))
+    return out
+
+
+def spd_initial_kernel(half: int = 3, centre: float = 0.1, noise: float = 1e-2, seed: int = 0):
+    """A small start for K (T = D^-1/2 (I + K^T K) D^-1/2 is then close to Jacobi); K = 0
+    itself is a stationary point of the loss (T depends on K quadratically)."""
+    rng = np.random.default_rng(seed)
+    K = noise * rng.standard_normal((2 * half + 1, 2 * half + 1))
+    K[half, half] += centre
+    return K.astype(np.float32)
+
+
+def train_spd(spd, pairs, epochs: int, lr: float, sigma: float = SIGMA, log=None):
+    """Full-batch Adam on the A-norm loss of the SPD preconditioner (bf_spd_accumulate):
+    one step per epoch on the mean gradient over all pairs; returns the mean loss of every
+    epoch."""
+    hist = []
+    for ep in range(epochs):
+        spd.zero_grad()
+        for G, r, z in pairs:
+            spd.accumulate(G, sigma, r, z)
+        _, loss = spd.grad()
+        hist.append(loss / max(len(pairs), 1))
+        spd.adam(lr, 1.0 / max(len(pairs), 1))
+        if log and ep % 50 == 0:
+            log(f"epoch {ep}: mean A-norm loss {hist[-1]:.5f}")
+    return hist
+
+
 def mean_loss(net, pairs):
     tot = 0.0
     for G, r, z in pairs:
@@ -95,14 +144,14 @@ def mean_loss(net, pairs):
 
 
 def refined_cg(G32, G64, x0, sigma: float, tol: float, precond: str, net=None, inner_tol: float = 1e-3,
-               inner_kmax: int = 3000, outer_max: int = 30):
+               inner_kmax: int = 3000, outer_max: int = 30, spd=None):
     """(L + sigma I) x = sigma x0 to a true relative residual tol by the library's
     mixed-precision refinement (cg_refine: FP64 residuals on G64, FP32 flexible CG on G32 to
     inner_tol).  Returns (x, rel, inner iterations, outer steps); rel is NaN when an inner
     solve broke down."""
     try:
         x, info = bf.cg_refine(G64, G32, x0.double().contiguous(), sigma, tol, precond=precond, net=net,
-                               inner_tol=inner_tol, inner_kmax=inner_kmax, outer_max=outer_max)
+                               inner_tol=inner_tol, inner_kmax=inner_kmax, outer_max=outer_max, spd=spd)
     except bf.BFError:                          # breakdown or non-finite scalars: give up
         return x0.double(), float("nan"), 0, 0
     return x, info.rnorm / info.ref, info.iters, info.restarts
