@@ -73,3 +73,25 @@ def test_guided_graph_parameter_checks_need_no_gpu():
         p = P(**{**good, **change})
         assert lib.bf_guided_graph(ctypes.byref(p), fake_guide, ctypes.byref(out), None) == -1, change
         assert not out.value
+
+
+def test_spd_preconditioner_checks_need_no_gpu():
+    """bf_spd_create rejects a half-width outside 1..4 and NULL output with BF_EINVAL, and
+    the SPD entry points reject NULL arguments, before touching the device."""
+    from paper_1509_02468_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    for fn in ("bf_spd_create", "bf_spd_apply", "bf_spd_accumulate", "bf_spd_grad", "bf_spd_adam",
+               "bf_spd_zero_grad", "bf_spd_weights", "bf_spd_size"):
+        getattr(lib, fn).restype = ctypes.c_int
+    out = ctypes.c_void_p()
+    for half in (0, 5, -1):
+        assert lib.bf_spd_create(half, None, ctypes.byref(out)) == -1
+        assert not out.value
+    assert lib.bf_spd_create(3, None, None) == -1
+    assert lib.bf_spd_size(None) == 0
+    assert lib.bf_spd_apply(None, None, None, 1, 1, None, 1, None) == -1
+    assert lib.bf_spd_accumulate(None, None, ctypes.c_double(0.01), None, None, None) == -1
+    assert lib.bf_spd_grad(None, None, None, None) == -1
+    assert lib.bf_spd_adam(None, ctypes.c_float(1e-3), ctypes.c_float(1.0), None) == -1
+    assert lib.bf_spd_zero_grad(None, None) == -1
+    assert lib.bf_spd_weights(None, None) == -1
