@@ -9,7 +9,8 @@ on the host and resident on the device before the timed region; L2 (126 MB) is f
 writing a 256 MB buffer between timed steps, and each step is timed with CUDA events on
 the launching stream.
 
-Extra keys: `roofline` for the operator bf_apply in its HBM-bound form (L x on one column
+Extra keys: `without_weights` (the same step with the graph reused instead of recomputed
+for the step's image), `roofline` for the operator bf_apply in its HBM-bound form (L x on one column
 with stored FP32 weights on a 2048 x 2048 image, timed alone with an L2 flush before each
 launch), `apply_modes_2048` (the operator per weight mode and k in {1, 4, 16} against
 HBM), `cg_2048` (CG 50 on the 2048 x 2048 image against HBM), `roofline_apply16_512` (L X
@@ -297,6 +298,29 @@ def run_gpu(args):
                 "theta": last["theta"].cpu().numpy()}
     keep.clear()
     ms, value = job_rate(sum(times) / len(times), npix, world, dist, "cuda")
+    # the same step without recomputing the graph (bf_graph_update), outside the timed region
+    try:
+        def filters_only():
+            side.wait_stream(stream)
+            lob.wait_stream(stream)
+            bf.lobpcg_filter(Gs, X0, w["lob_iters"], want_X=False, sync=False, stream=lob)
+            bf.cg_filter(Gs, guide.view(-1), w["cg_iters"], out=x_cg, sync=False, stream=side)
+            stream.wait_stream(side)
+            stream.wait_stream(lob)
+        t_f = []
+        for i in range(3 + min(args.steps, 10)):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            filters_only()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                t_f.append(e0.elapsed_time(e1))
+        without_weights = {"ms_per_step": sum(t_f) / len(t_f), "value": npix / (sum(t_f) / len(t_f) * 1e-3) / 1e6,
+                           "unit": "Mpix/s", "note": "the step without bf_graph_update (graph reused)"}
+    except Exception as exc:                    # reported in the line, not fatal to it
+        without_weights = {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
     # ---- rooflines.  The operator (L X, k = 16, on-the-fly weights) on the step's image and
     # on a 2048 x 2048 image of the same generator (X and Y far larger than L2); the
@@ -403,6 +427,7 @@ def run_gpu(args):
                            "lobpcg_iters": w["lob_iters"], "weights": "on-the-fly fp32",
                            "l2": "flushed between steps (256 MB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
+                "without_weights": without_weights,
                 "roofline": roofline, "apply_modes_2048": apply_modes, "cg_2048": cg_2048,
                 "roofline_apply16_512": roofline_512, "roofline_2048": roofline_2048,
                 "roofline_dominant": roofline_rr, "cpu_baseline": cpu, "err": err,
