@@ -1,6 +1,7 @@
-"""The seeded input recipes (paper_1509_02468_gb300/synth.py) produce what the design notes
-state: the 1D signal's pieces and noise, the polygon image's range and noise, the block
-start, and the sizes of the 256-instance mixed batch.  CPU only."""
+"""The seeded input recipes (paper_1509_02468_gb300/synth.py) produce what their docstrings
+state: the 1D signal's 12 pieces of at least 16 samples and its noise, the polygon image's
+range and noise, the block start, and the sizes of the 256-instance mixed batch
+(36.7 M samples).  CPU only."""
 import numpy as np
 import pytest
 
