@@ -51,6 +51,22 @@ WORKLOAD = dict(name="image512_w7x7_cg50_lobpcg_k16x30", ny=512, nx=512, radius=
 L2_FLUSH_BYTES = 256 << 20
 
 
+def host_info():
+    """The host the CPU baseline ran on: logical cores and a CPU description."""
+    import platform
+    desc = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    desc = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": desc}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -218,7 +234,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"] + f"_sample{side}", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -412,7 +428,7 @@ def run_gpu(args):
             ref = dict(np.load(ref_path))
         err = step_errors(ref, step_out["x_cg"], step_out["y"], step_out["theta"])
         cpu = {"value": res["npix"] / res["times"][0] / 1e6, "unit": "Mpix/s", "cores": 1,
-               "kind": "oracle",
+               "kind": "oracle", "host": host_info(),
                "sample": "one full step (512x512: graph + CG 50 + LOBPCG k=16 x 30), FP64 "
                          "numpy/scipy, 1 thread"}
 
